@@ -1,0 +1,752 @@
+/*
+ * FUnc-SNE reference oracle: a plain, slow, double-precision CPU restatement
+ * of one iteration of the method (Lambert, Couplet, Verleysen, Lee,
+ * "FUnc-SNE", arXiv 2509.07681).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library. It shares no code,
+ * header, table or constant generator with the CUDA path: every constant
+ * used here is restated below from the written method description.
+ *
+ * Passages followed (paper sections / equations):
+ *   Eq. 1      HD conditional affinities p_{j|i}, symmetrisation p_ij.
+ *   Eq. 4      variable-tail LD kernel w_ij = (1 + |y_i - y_j|^2/alpha)^-alpha.
+ *   Eq. 5      gradient 4 sum_j (p_ij - q_ij) w_ij^{1/alpha} (y_i - y_j).
+ *   Eq. 6      split of the sum into HD neighbours, LD-but-not-HD neighbours,
+ *              and the rest (estimated by negative sampling, Section 2.2).
+ *   Section 3  joint HD/LD neighbour refinement from neighbours of neighbours
+ *              and cross-space proposals; new-neighbour flags; warm-restart
+ *              bandwidth recalibration; HD refinement with probability
+ *              0.05 + 0.95 E[N_new/N]; LD refinement every iteration;
+ *              separate attraction / repulsion scaling.
+ * Readings where the paper is silent (candidate counts, random-number
+ * mapping, tie-break, Jacobi update order, bisection details, Z estimator,
+ * smoothing rates, optimiser) are the builder's and are stated in the
+ * comments next to the code that implements them.
+ *
+ * Parity status: every function below is pinned by a CPU test against a
+ * closed form, brute force, finite differences or published known-answer
+ * vectors, except the whole-run trajectory (an approximation) which is
+ * compared by statistics only.
+ *
+ * Compile with -ffp-contract=off so that x86 and Arm hosts give identical
+ * results.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10, from Salmon, Moraes, Dror, Shaw, "Parallel random     */
+/* numbers: as easy as 1, 2, 3" (SC'11): 10 rounds of two 32x32->64     */
+/* multiplies, with a Weyl-sequence key schedule.                        */
+/* ------------------------------------------------------------------ */
+static const uint32_t PHILOX_MUL_A = 0xD2511F53u;
+static const uint32_t PHILOX_MUL_B = 0xCD9E8D57u;
+static const uint32_t PHILOX_WEYL_A = 0x9E3779B9u; /* golden ratio */
+static const uint32_t PHILOX_WEYL_B = 0xBB67AE85u; /* sqrt(3) - 1 */
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_WEYL_A;
+            k1 += PHILOX_WEYL_B;
+        }
+        uint64_t prod_a = (uint64_t)PHILOX_MUL_A * (uint64_t)x0;
+        uint64_t prod_b = (uint64_t)PHILOX_MUL_B * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(prod_b >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)prod_b;
+        uint32_t y2 = (uint32_t)(prod_a >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)prod_a;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Random-stream identifiers (builder's reading: one Philox counter per
+ * (iteration, point, purpose, slot), key = the 64-bit seed). */
+enum {
+    STREAM_COIN = 0,
+    STREAM_HD = 1,
+    STREAM_LD = 2,
+    STREAM_NEG = 3,
+    STREAM_MLP = 4,
+    STREAM_INSERT = 5,
+    STREAM_INIT_HD = 6,
+    STREAM_INIT_LD = 7,
+    STREAM_INIT_Y = 8,
+    STREAM_ZINIT = 9
+};
+
+/* Builder constants (the paper gives none of these). */
+#define CAND_HD 32             /* HD candidates per point and iteration     */
+#define CAND_LD 32             /* LD candidates per point and iteration     */
+#define HD_SLOTS_NN 16         /* HD slots 0..15: HD neighbour of neighbour */
+#define HD_SLOTS_LDNB 20       /* HD slots 16..19: LD neighbour             */
+#define HD_SLOTS_LDNN 24       /* HD slots 20..23: LD neighbour of neighbour*/
+                               /* HD slots 24..31: uniform random           */
+#define LD_SLOTS_NN 16         /* LD slots 0..15: LD neighbour of neighbour */
+#define LD_SLOTS_HDNB 24       /* LD slots 16..23: HD neighbour             */
+                               /* LD slots 24..31: uniform random           */
+#define GAMMA_E 0.1            /* smoothing of E[N_new/N]                   */
+#define GAMMA_Z 0.1            /* smoothing of the normalisation estimate   */
+#define INIT_Y_STD 1e-4        /* per-dimension std of the initial layout   */
+
+static void draw4(uint64_t seed, uint32_t t, uint32_t i, uint32_t stream, uint32_t slot,
+                  uint32_t out[4])
+{
+    uint32_t ctr[4] = {t, i, stream, slot};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    oracle_philox4x32_10(ctr, key, out);
+}
+
+/* uniform integer in [0, m): the high word of u * m (no modulo). */
+static int64_t map_index(uint32_t u, int64_t m)
+{
+    return (int64_t)(((uint64_t)u * (uint64_t)m) >> 32);
+}
+
+/* uniform point index in [0, N) minus {i}. */
+static int64_t map_other(uint32_t u, int64_t N, int64_t i)
+{
+    int64_t j = map_index(u, N - 1);
+    return j >= i ? j + 1 : j;
+}
+
+/* ------------------------------------------------------------------ */
+/* State (all arrays owned by the caller).                              */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int64_t N;
+    int32_t D, d, k_hd, k_ld, n_neg;
+    double alpha, perplexity;
+    uint64_t seed;
+    /* options */
+    double lr, momentum, att_ratio, rep_ratio, exaggeration;
+    int32_t exag_iters;   /* exaggeration applies while t < exag_iters     */
+    int32_t hd_mode;      /* 0 adaptive coin, 1 always refine, 2 never     */
+    int32_t neg_mode;     /* 0 Philox negatives, 1 exhaustive (pin mode)   */
+    /* state */
+    const double *X;      /* N x D                                          */
+    double *Y, *V;        /* N x d                                          */
+    int32_t *hd_idx;      /* N x k_hd, ordered by (d2, idx)                 */
+    double *hd_d2;        /* N x k_hd                                       */
+    int32_t *ld_idx;      /* N x k_ld                                       */
+    double *beta;         /* N: 1/(2 sigma_i^2)                              */
+    double *P;            /* N x k_hd: p_{j|i} aligned with hd_idx           */
+    double Zhat, E;
+    uint32_t t;
+} oracle_state;
+
+/* Squared Euclidean distance, the plain definition. */
+static double sqdist(const double *a, const double *b, int n)
+{
+    double s = 0.0;
+    for (int f = 0; f < n; ++f) {
+        double diff = a[f] - b[f];
+        s += diff * diff;
+    }
+    return s;
+}
+
+double oracle_sqdist(const double *a, const double *b, int n) { return sqdist(a, b, n); }
+
+/* Order on (distance, index): ascending distance, ties by smaller index. */
+typedef struct { double d2; int64_t idx; } entry;
+
+static int entry_cmp(const void *pa, const void *pb)
+{
+    const entry *a = (const entry *)pa, *b = (const entry *)pb;
+    if (a->d2 < b->d2) return -1;
+    if (a->d2 > b->d2) return 1;
+    if (a->idx < b->idx) return -1;
+    if (a->idx > b->idx) return 1;
+    return 0;
+}
+
+static int contains(const int32_t *list, int n, int64_t v)
+{
+    for (int a = 0; a < n; ++a)
+        if (list[a] == v) return 1;
+    return 0;
+}
+
+/*
+ * Top-k merge (Section 3, neighbour-set refinement): the new set is the k
+ * smallest (d2, idx) among the old set and the candidates. Candidates equal
+ * to i, already in the old set, or repeated among earlier candidates are
+ * dropped first. Returns 1 when at least one candidate entered the set.
+ */
+int oracle_topk_merge(int64_t i, int k, const int32_t *old_idx, const double *old_d2,
+                      int n_cand, const int64_t *cand_idx, const double *cand_d2,
+                      int32_t *new_idx, double *new_d2)
+{
+    entry *u = (entry *)malloc(sizeof(entry) * (size_t)(k + n_cand));
+    int n = 0;
+    for (int a = 0; a < k; ++a) {
+        u[n].d2 = old_d2[a];
+        u[n].idx = old_idx[a];
+        ++n;
+    }
+    for (int s = 0; s < n_cand; ++s) {
+        int64_t c = cand_idx[s];
+        if (c == i || contains(old_idx, k, c)) continue;
+        int seen = 0;
+        for (int r = 0; r < s; ++r)
+            if (cand_idx[r] == c) seen = 1;
+        if (seen) continue;
+        u[n].d2 = cand_d2[s];
+        u[n].idx = c;
+        ++n;
+    }
+    qsort(u, (size_t)n, sizeof(entry), entry_cmp);
+    int changed = 0;
+    for (int a = 0; a < k; ++a)
+        if (!contains(old_idx, k, u[a].idx)) changed = 1;
+    /* an unchanged set keeps its stored order (its p_{j|i} stay aligned) */
+    for (int a = 0; a < k; ++a) {
+        new_idx[a] = changed ? (int32_t)u[a].idx : old_idx[a];
+        new_d2[a] = changed ? u[a].d2 : old_d2[a];
+    }
+    free(u);
+    return changed;
+}
+
+/*
+ * HD candidates of point i at iteration t (Section 3: neighbours of
+ * neighbours, with the LD sets proposing candidates for the HD set).
+ * Slot s uses Philox counter (t, i, HD, s):
+ *   s in [0,16):  a = N_HD(i)[w0 * k_hd], c = N_HD(a)[w1 * k_hd]
+ *   s in [16,20): c = N_LD(i)[w0 * k_ld]
+ *   s in [20,24): a = N_LD(i)[w0 * k_ld], c = N_LD(a)[w1 * k_ld]
+ *   s in [24,32): c uniform over the other points (w0)
+ * where "w * m" denotes the high word of the 64-bit product.
+ */
+void oracle_hd_candidates(const oracle_state *st, int64_t i, int64_t *cand)
+{
+    for (int s = 0; s < CAND_HD; ++s) {
+        uint32_t w[4];
+        draw4(st->seed, st->t, (uint32_t)i, STREAM_HD, (uint32_t)s, w);
+        int64_t c;
+        if (s < HD_SLOTS_NN) {
+            int64_t a = st->hd_idx[i * st->k_hd + map_index(w[0], st->k_hd)];
+            c = st->hd_idx[a * st->k_hd + map_index(w[1], st->k_hd)];
+        } else if (s < HD_SLOTS_LDNB) {
+            c = st->ld_idx[i * st->k_ld + map_index(w[0], st->k_ld)];
+        } else if (s < HD_SLOTS_LDNN) {
+            int64_t a = st->ld_idx[i * st->k_ld + map_index(w[0], st->k_ld)];
+            c = st->ld_idx[a * st->k_ld + map_index(w[1], st->k_ld)];
+        } else {
+            c = map_other(w[0], st->N, i);
+        }
+        cand[s] = c;
+    }
+}
+
+/*
+ * LD candidates of point i at iteration t. Slot s uses counter (t, i, LD, s):
+ *   s in [0,16):  a = N_LD(i)[w0 * k_ld], c = N_LD(a)[w1 * k_ld]
+ *   s in [16,24): c = N_HD(i)[w0 * k_hd]   (HD set of iteration t)
+ *   s in [24,32): c uniform over the other points (w0)
+ */
+void oracle_ld_candidates(const oracle_state *st, int64_t i, int64_t *cand)
+{
+    for (int s = 0; s < CAND_LD; ++s) {
+        uint32_t w[4];
+        draw4(st->seed, st->t, (uint32_t)i, STREAM_LD, (uint32_t)s, w);
+        int64_t c;
+        if (s < LD_SLOTS_NN) {
+            int64_t a = st->ld_idx[i * st->k_ld + map_index(w[0], st->k_ld)];
+            c = st->ld_idx[a * st->k_ld + map_index(w[1], st->k_ld)];
+        } else if (s < LD_SLOTS_HDNB) {
+            c = st->hd_idx[i * st->k_hd + map_index(w[0], st->k_hd)];
+        } else {
+            c = map_other(w[0], st->N, i);
+        }
+        cand[s] = c;
+    }
+}
+
+/* Shannon entropy (natural log) of p_{.|i} for bandwidth beta = 1/(2 sigma^2),
+ * from Eq. 1 restricted to the k listed neighbours. Writes P when non-NULL. */
+double oracle_entropy(const double *d2, int k, double beta, double *P)
+{
+    double dmin = d2[0];
+    for (int a = 1; a < k; ++a)
+        if (d2[a] < dmin) dmin = d2[a];
+    double *e = (double *)malloc(sizeof(double) * (size_t)k);
+    double sum = 0.0;
+    for (int a = 0; a < k; ++a) {
+        e[a] = exp(-beta * (d2[a] - dmin));
+        sum += e[a];
+    }
+    double h = 0.0;
+    for (int a = 0; a < k; ++a) {
+        double p = e[a] / sum;
+        if (P) P[a] = p;
+        if (p > 0.0) h -= p * log(p);
+    }
+    free(e);
+    return h;
+}
+
+/*
+ * Perplexity calibration of sigma_i (Eq. 1): find beta with entropy equal
+ * to ln(perplexity). The entropy decreases in beta, so: start from beta0
+ * (the previous value: warm restart, Section 3) or, when beta0 <= 0, from
+ * 1 / mean(d2 - d2_min); double beta until the entropy drops below the
+ * target, then bisect, stopping when |H - ln perp| < tol or after maxit
+ * evaluations. When ln k <= ln perp no beta reaches the target and the
+ * uniform distribution (beta = 0) is returned.
+ * Returns the number of entropy evaluations.
+ */
+int oracle_bisect(const double *d2, int k, double perplexity, double beta0, double tol,
+                  int maxit, double *beta_out, double *P)
+{
+    double target = log(perplexity);
+    if (log((double)k) <= target) {
+        for (int a = 0; a < k; ++a) P[a] = 1.0 / k;
+        *beta_out = 0.0;
+        return 0;
+    }
+    double beta = beta0;
+    if (!(beta > 0.0)) {
+        double dmin = d2[0], mean = 0.0;
+        for (int a = 1; a < k; ++a)
+            if (d2[a] < dmin) dmin = d2[a];
+        for (int a = 0; a < k; ++a) mean += d2[a] - dmin;
+        mean /= k;
+        beta = mean > 0.0 ? 1.0 / mean : 1.0;
+    }
+    double lo = 0.0, hi = INFINITY;
+    int it = 0;
+    while (it < maxit) {
+        double h = oracle_entropy(d2, k, beta, NULL);
+        ++it;
+        if (fabs(h - target) < tol) break;
+        if (h > target) {
+            lo = beta;
+            beta = isinf(hi) ? 2.0 * beta : 0.5 * (lo + hi);
+        } else {
+            hi = beta;
+            beta = 0.5 * (lo + hi);
+        }
+    }
+    oracle_entropy(d2, k, beta, P);
+    *beta_out = beta;
+    return it;
+}
+
+/* Eq. 4: w = (1 + r2/alpha)^-alpha and its power w^{1/alpha} = 1/(1 + r2/alpha). */
+static double kernel_w(double r2, double alpha) { return pow(1.0 + r2 / alpha, -alpha); }
+static double kernel_w_inv_alpha(double r2, double alpha) { return 1.0 / (1.0 + r2 / alpha); }
+
+/* Initial neighbour list: k distinct other points. Slot l draws an offset
+ * o_l uniform in [0, N-1) from counter (0, i, stream, l); an offset already
+ * taken moves to the next free one (linear probing mod N-1). The neighbour
+ * is (i + 1 + o_l) mod N. */
+void oracle_initial_list(uint64_t seed, int64_t N, int64_t i, int k, uint32_t stream, int32_t *out)
+{
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    for (int l = 0; l < k; ++l) {
+        uint32_t w[4];
+        draw4(seed, 0u, (uint32_t)i, stream, (uint32_t)l, w);
+        int64_t o = map_index(w[0], N - 1);
+        for (;;) {
+            int taken = 0;
+            for (int m = 0; m < l; ++m)
+                if (off[m] == o) taken = 1;
+            if (!taken) break;
+            o = (o + 1) % (N - 1);
+        }
+        off[l] = o;
+        out[l] = (int32_t)((i + 1 + o) % N);
+    }
+    free(off);
+}
+
+/* Gaussian N(0,1) from two uniform words (Box-Muller). */
+static double gauss_from(uint32_t a, uint32_t b)
+{
+    double u1 = ((double)a + 0.5) * (1.0 / 4294967296.0);
+    double u2 = ((double)b + 0.5) * (1.0 / 4294967296.0);
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+/* Sorts one HD list of point i by (d2, idx) with distances recomputed. */
+static void sort_hd_list(oracle_state *st, int64_t i)
+{
+    int k = st->k_hd;
+    entry *u = (entry *)malloc(sizeof(entry) * (size_t)k);
+    for (int a = 0; a < k; ++a) {
+        int64_t j = st->hd_idx[i * k + a];
+        u[a].idx = j;
+        u[a].d2 = sqdist(st->X + i * st->D, st->X + j * st->D, st->D);
+    }
+    qsort(u, (size_t)k, sizeof(entry), entry_cmp);
+    for (int a = 0; a < k; ++a) {
+        st->hd_idx[i * k + a] = (int32_t)u[a].idx;
+        st->hd_d2[i * k + a] = u[a].d2;
+    }
+    free(u);
+}
+
+/*
+ * Repulsion, attraction and the normalisation estimate (Eq. 5 split as in
+ * Eq. 6), for the lists currently in hd_idx / ld_idx, with Y, P and Zhat of
+ * the state. A and R are N x d, zeroed here. Returns Z_t, the estimate of
+ * sum_{k != l} w_kl. In exhaustive mode the third term of Eq. 6 is summed
+ * over every other point with factor 1 instead of being sampled.
+ *
+ *   attraction: for j in N_HD(i), f = 4 (p_{j|i} / 2N) w^{1/alpha} (y_i - y_j)
+ *               is added to A_i and subtracted from A_j, which realises
+ *               p_ij = (p_{j|i} + p_{i|j}) / 2N with p_{i|j} = 0 when i is
+ *               not in N_HD(j);
+ *   repulsion:  for j in S_i = N_HD(i) u N_LD(i):
+ *               R_i += 4 (w_ij / Zhat) w^{1/alpha} (y_i - y_j);
+ *               negatives s < n_neg: j_s uniform over the other points from
+ *               counter (t, i, NEG, s); a draw inside S_i contributes 0;
+ *               the others are scaled by (N-1)/n_neg.
+ */
+double oracle_forces(const oracle_state *st, uint32_t t, uint32_t neg_stream, double zhat,
+                     double *A, double *R, double *z_per_point)
+{
+    int64_t N = st->N;
+    int d = st->d, kh = st->k_hd, kl = st->k_ld;
+    double alpha = st->alpha;
+    memset(A, 0, sizeof(double) * (size_t)(N * d));
+    memset(R, 0, sizeof(double) * (size_t)(N * d));
+    double ztotal = 0.0;
+    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)(kh + kl));
+    char *inS = NULL;
+    if (st->neg_mode == 1) inS = (char *)malloc((size_t)N);
+    for (int64_t i = 0; i < N; ++i) {
+        const double *yi = st->Y + i * d;
+        /* attraction over the HD list */
+        for (int a = 0; a < kh; ++a) {
+            int64_t j = st->hd_idx[i * kh + a];
+            const double *yj = st->Y + j * d;
+            double r2 = sqdist(yi, yj, d);
+            double coef = 4.0 * (st->P[i * kh + a] / (2.0 * (double)N)) * kernel_w_inv_alpha(r2, alpha);
+            for (int c = 0; c < d; ++c) {
+                double f = coef * (yi[c] - yj[c]);
+                A[i * d + c] += f;
+                A[j * d + c] -= f;
+            }
+        }
+        /* S_i = HD list, then LD entries not in the HD list */
+        int ns = 0;
+        for (int a = 0; a < kh; ++a) S[ns++] = st->hd_idx[i * kh + a];
+        for (int a = 0; a < kl; ++a) {
+            int32_t j = st->ld_idx[i * kl + a];
+            if (!contains(st->hd_idx + i * kh, kh, j)) S[ns++] = j;
+        }
+        double zi = 0.0;
+        for (int a = 0; a < ns; ++a) {
+            const double *yj = st->Y + (int64_t)S[a] * d;
+            double r2 = sqdist(yi, yj, d);
+            double w = kernel_w(r2, alpha);
+            double coef = 4.0 * (w / zhat) * kernel_w_inv_alpha(r2, alpha);
+            for (int c = 0; c < d; ++c) R[i * d + c] += coef * (yi[c] - yj[c]);
+            zi += w;
+        }
+        if (st->neg_mode == 1) {
+            memset(inS, 0, (size_t)N);
+            for (int a = 0; a < ns; ++a) inS[S[a]] = 1;
+            for (int64_t j = 0; j < N; ++j) {
+                if (j == i || inS[j]) continue;
+                const double *yj = st->Y + j * d;
+                double r2 = sqdist(yi, yj, d);
+                double w = kernel_w(r2, alpha);
+                double coef = 4.0 * (w / zhat) * kernel_w_inv_alpha(r2, alpha);
+                for (int c = 0; c < d; ++c) R[i * d + c] += coef * (yi[c] - yj[c]);
+                zi += w;
+            }
+        } else {
+            double scale = (double)(N - 1) / (double)st->n_neg;
+            for (int s = 0; s < st->n_neg; ++s) {
+                uint32_t w4[4];
+                draw4(st->seed, t, (uint32_t)i, neg_stream, (uint32_t)s, w4);
+                int64_t j = map_other(w4[0], N, i);
+                if (contains(S, ns, j)) continue;
+                const double *yj = st->Y + j * d;
+                double r2 = sqdist(yi, yj, d);
+                double w = kernel_w(r2, alpha);
+                double coef = scale * 4.0 * (w / zhat) * kernel_w_inv_alpha(r2, alpha);
+                for (int c = 0; c < d; ++c) R[i * d + c] += coef * (yi[c] - yj[c]);
+                zi += scale * w;
+            }
+        }
+        if (z_per_point) z_per_point[i] = zi;
+        ztotal += zi;
+    }
+    free(S);
+    free(inS);
+    return ztotal;
+}
+
+/*
+ * Initial state: random distinct HD and LD lists (HD lists sorted by
+ * (d2, idx)), Y0 = (X - mean) R with R_fc ~ N(0,1) from counter
+ * (0, f, INIT_Y, c), each LD dimension rescaled to std 1e-4 (a random linear
+ * projection, Section 3's jump-start idea), V = 0, every beta calibrated
+ * from a cold start, E = 1, t = 0, and Zhat = the Z estimate of this state
+ * with negatives from the ZINIT stream.
+ */
+void oracle_init(oracle_state *st, double bisect_tol, int bisect_maxit)
+{
+    int64_t N = st->N;
+    int D = st->D, d = st->d, kh = st->k_hd, kl = st->k_ld;
+    for (int64_t i = 0; i < N; ++i) {
+        oracle_initial_list(st->seed, N, i, kh, STREAM_INIT_HD, st->hd_idx + i * kh);
+        sort_hd_list(st, i);
+        oracle_initial_list(st->seed, N, i, kl, STREAM_INIT_LD, st->ld_idx + i * kl);
+    }
+    double *Rm = (double *)malloc(sizeof(double) * (size_t)(D * d));
+    for (int f = 0; f < D; ++f)
+        for (int c = 0; c < d; ++c) {
+            uint32_t w[4];
+            draw4(st->seed, 0u, (uint32_t)f, STREAM_INIT_Y, (uint32_t)c, w);
+            Rm[f * d + c] = gauss_from(w[0], w[1]);
+        }
+    double *mu = (double *)calloc((size_t)(D > 0 ? D : 1), sizeof(double));
+    for (int64_t i = 0; i < N; ++i)
+        for (int f = 0; f < D; ++f) mu[f] += st->X[i * D + f];
+    for (int f = 0; f < D; ++f) mu[f] /= (double)N;
+    for (int64_t i = 0; i < N; ++i)
+        for (int c = 0; c < d; ++c) {
+            double s = 0.0;
+            for (int f = 0; f < D; ++f) s += (st->X[i * D + f] - mu[f]) * Rm[f * d + c];
+            st->Y[i * d + c] = s;
+        }
+    for (int c = 0; c < d; ++c) {
+        double m = 0.0, v = 0.0;
+        for (int64_t i = 0; i < N; ++i) m += st->Y[i * d + c];
+        m /= (double)N;
+        for (int64_t i = 0; i < N; ++i) v += (st->Y[i * d + c] - m) * (st->Y[i * d + c] - m);
+        double sd = sqrt(v / (double)N);
+        double scale = sd > 0.0 ? INIT_Y_STD / sd : 1.0;
+        for (int64_t i = 0; i < N; ++i) st->Y[i * d + c] *= scale;
+    }
+    memset(st->V, 0, sizeof(double) * (size_t)(N * d));
+    for (int64_t i = 0; i < N; ++i)
+        oracle_bisect(st->hd_d2 + i * kh, kh, st->perplexity, 0.0, bisect_tol, bisect_maxit,
+                      st->beta + i, st->P + i * kh);
+    st->E = 1.0;
+    st->t = 0;
+    double *A = (double *)malloc(sizeof(double) * (size_t)(N * d));
+    double *R = (double *)malloc(sizeof(double) * (size_t)(N * d));
+    st->Zhat = 1.0;
+    st->Zhat = oracle_forces(st, 0u, STREAM_ZINIT, 1.0, A, R, NULL);
+    free(A);
+    free(R);
+    free(Rm);
+    free(mu);
+}
+
+/* Coin for HD refinement at iteration t: refine iff the uniform draw from
+ * counter (t, 0, COIN, 0) is below 0.05 + 0.95 E (Section 3). */
+int oracle_coin(const oracle_state *st)
+{
+    if (st->hd_mode == 1) return 1;
+    if (st->hd_mode == 2) return 0;
+    uint32_t w[4];
+    draw4(st->seed, st->t, 0u, STREAM_COIN, 0u, w);
+    double p = 0.05 + 0.95 * st->E;
+    double u = (double)w[0] * (1.0 / 4294967296.0);
+    return u < p;
+}
+
+/*
+ * One iteration (Jacobi: every point reads the state of iteration t and
+ * writes iteration t+1):
+ *   1. coin; if it fires, HD refinement of every point from the lists of t,
+ *      flags for points whose set changed, and warm-restart recalibration of
+ *      beta and P for flagged points;
+ *   2. LD refinement of every point from the lists of t and Y_t;
+ *   3. forces with the new lists, P and Y_t, Zhat_t;
+ *   4. g = att * exag * A - rep * R; V = momentum V - lr g; Y += V;
+ *      Zhat <- (1 - 0.1) Zhat + 0.1 Z_t; E <- (1 - 0.1) E + 0.1 N_new/N
+ *      when the coin fired; t <- t + 1.
+ * A_out / R_out (N x d) receive the forces of step 3; flags (N bytes) the
+ * new-neighbour flags; info[0] = coin, info[1] = N_new. z_out (N) receives
+ * the per-point Z terms when non-NULL.
+ */
+void oracle_step(oracle_state *st, double bisect_tol, int bisect_maxit, double *A_out,
+                 double *R_out, uint8_t *flags, int64_t *info, double *z_out)
+{
+    int64_t N = st->N;
+    int D = st->D, d = st->d, kh = st->k_hd, kl = st->k_ld;
+    int32_t *nh_idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(N * kh));
+    double *nh_d2 = (double *)malloc(sizeof(double) * (size_t)(N * kh));
+    int32_t *nl_idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(N * kl));
+    memcpy(nh_idx, st->hd_idx, sizeof(int32_t) * (size_t)(N * kh));
+    memcpy(nh_d2, st->hd_d2, sizeof(double) * (size_t)(N * kh));
+    memset(flags, 0, (size_t)N);
+
+    int fire = oracle_coin(st);
+    int64_t n_new = 0;
+    int64_t cand[CAND_HD > CAND_LD ? CAND_HD : CAND_LD];
+    double cd2[CAND_HD > CAND_LD ? CAND_HD : CAND_LD];
+    double *old_d2 = (double *)malloc(sizeof(double) * (size_t)(kh > kl ? kh : kl));
+    double *ld_new_d2 = (double *)malloc(sizeof(double) * (size_t)kl);
+    if (fire) {
+        for (int64_t i = 0; i < N; ++i) {
+            oracle_hd_candidates(st, i, cand);
+            for (int s = 0; s < CAND_HD; ++s)
+                cd2[s] = (cand[s] == i) ? 0.0 : sqdist(st->X + i * D, st->X + cand[s] * D, D);
+            for (int a = 0; a < kh; ++a)
+                old_d2[a] = sqdist(st->X + i * D, st->X + (int64_t)st->hd_idx[i * kh + a] * D, D);
+            flags[i] = (uint8_t)oracle_topk_merge(i, kh, st->hd_idx + i * kh, old_d2, CAND_HD,
+                                                  cand, cd2, nh_idx + i * kh, nh_d2 + i * kh);
+            n_new += flags[i];
+        }
+        for (int64_t i = 0; i < N; ++i)
+            if (flags[i])
+                oracle_bisect(nh_d2 + i * kh, kh, st->perplexity, st->beta[i], bisect_tol,
+                              bisect_maxit, st->beta + i, st->P + i * kh);
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        oracle_ld_candidates(st, i, cand);
+        for (int s = 0; s < CAND_LD; ++s)
+            cd2[s] = (cand[s] == i) ? 0.0 : sqdist(st->Y + i * d, st->Y + cand[s] * d, d);
+        for (int a = 0; a < kl; ++a)
+            old_d2[a] = sqdist(st->Y + i * d, st->Y + (int64_t)st->ld_idx[i * kl + a] * d, d);
+        oracle_topk_merge(i, kl, st->ld_idx + i * kl, old_d2, CAND_LD, cand, cd2,
+                          nl_idx + i * kl, ld_new_d2);
+    }
+    free(old_d2);
+    free(ld_new_d2);
+    /* install the lists of iteration t+1 before the forces */
+    memcpy(st->hd_idx, nh_idx, sizeof(int32_t) * (size_t)(N * kh));
+    memcpy(st->hd_d2, nh_d2, sizeof(double) * (size_t)(N * kh));
+    memcpy(st->ld_idx, nl_idx, sizeof(int32_t) * (size_t)(N * kl));
+    free(nh_idx);
+    free(nh_d2);
+    free(nl_idx);
+
+    double zt = oracle_forces(st, st->t, STREAM_NEG, st->Zhat, A_out, R_out, z_out);
+    double exag = (st->t < (uint32_t)st->exag_iters) ? st->exaggeration : 1.0;
+    for (int64_t e = 0; e < N * d; ++e) {
+        double g = st->att_ratio * exag * A_out[e] - st->rep_ratio * R_out[e];
+        st->V[e] = st->momentum * st->V[e] - st->lr * g;
+        st->Y[e] = st->Y[e] + st->V[e];
+    }
+    st->Zhat = (1.0 - GAMMA_Z) * st->Zhat + GAMMA_Z * zt;
+    if (fire) st->E = (1.0 - GAMMA_E) * st->E + GAMMA_E * ((double)n_new / (double)N);
+    st->t += 1;
+    info[0] = fire;
+    info[1] = n_new;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact (dense) references, for small N.                               */
+/* ------------------------------------------------------------------ */
+
+/* Dense symmetric P (N x N) from sparse lists: p_ij = (p_{j|i} + p_{i|j}) / 2N
+ * with p_{j|i} = 0 when j is not listed for i (Eq. 1). */
+void oracle_dense_p(const oracle_state *st, double *Pd)
+{
+    int64_t N = st->N;
+    int kh = st->k_hd;
+    memset(Pd, 0, sizeof(double) * (size_t)(N * N));
+    for (int64_t i = 0; i < N; ++i)
+        for (int a = 0; a < kh; ++a) {
+            int64_t j = st->hd_idx[i * kh + a];
+            double v = st->P[i * kh + a] / (2.0 * (double)N);
+            Pd[i * N + j] += v;
+            Pd[j * N + i] += v;
+        }
+}
+
+/* Z = sum_{k != l} w_kl (Eq. 4), exactly. */
+double oracle_exact_z(const double *Y, int64_t N, int d, double alpha)
+{
+    double z = 0.0;
+    for (int64_t k = 0; k < N; ++k)
+        for (int64_t l = 0; l < N; ++l)
+            if (k != l) z += kernel_w(sqdist(Y + k * d, Y + l * d, d), alpha);
+    return z;
+}
+
+/* KL(P || Q) = sum_{i != j} p_ij log(p_ij / q_ij) with q_ij = w_ij / Z
+ * (Section 2.2 and Eq. 4). Terms with p_ij = 0 contribute 0. */
+double oracle_kl(const double *Pd, const double *Y, int64_t N, int d, double alpha)
+{
+    double z = oracle_exact_z(Y, N, d, alpha);
+    double kl = 0.0;
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < N; ++j) {
+            if (i == j) continue;
+            double p = Pd[i * N + j];
+            if (p <= 0.0) continue;
+            double q = kernel_w(sqdist(Y + i * d, Y + j * d, d), alpha) / z;
+            kl += p * log(p / q);
+        }
+    return kl;
+}
+
+/* Eq. 5: dL/dy_i = 4 sum_j (p_ij - q_ij) w_ij^{1/alpha} (y_i - y_j). */
+void oracle_exact_grad(const double *Pd, const double *Y, int64_t N, int d, double alpha,
+                       double *G)
+{
+    double z = oracle_exact_z(Y, N, d, alpha);
+    memset(G, 0, sizeof(double) * (size_t)(N * d));
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < N; ++j) {
+            if (i == j) continue;
+            double r2 = sqdist(Y + i * d, Y + j * d, d);
+            double q = kernel_w(r2, alpha) / z;
+            double coef = 4.0 * (Pd[i * N + j] - q) * kernel_w_inv_alpha(r2, alpha);
+            for (int c = 0; c < d; ++c) G[i * d + c] += coef * (Y[i * d + c] - Y[j * d + c]);
+        }
+}
+
+/* Exact k nearest neighbours of every row of X by brute force, ordered by
+ * (d2, idx); self excluded. */
+void oracle_bruteforce_knn(const double *X, int64_t N, int D, int k, int32_t *idx, double *d2)
+{
+    entry *u = (entry *)malloc(sizeof(entry) * (size_t)N);
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t n = 0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            u[n].idx = j;
+            u[n].d2 = sqdist(X + i * D, X + j * D, D);
+            ++n;
+        }
+        qsort(u, (size_t)n, sizeof(entry), entry_cmp);
+        for (int a = 0; a < k; ++a) {
+            idx[i * k + a] = (int32_t)u[a].idx;
+            d2[i * k + a] = u[a].d2;
+        }
+    }
+    free(u);
+}
+
+/* Exact k nearest neighbours of a few query rows (indices q) in X. */
+void oracle_query_knn(const double *X, int64_t N, int D, const int64_t *q, int64_t nq, int k,
+                      int32_t *idx, double *d2)
+{
+    entry *u = (entry *)malloc(sizeof(entry) * (size_t)N);
+    for (int64_t a = 0; a < nq; ++a) {
+        int64_t i = q[a];
+        int64_t n = 0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            u[n].idx = j;
+            u[n].d2 = sqdist(X + i * D, X + j * D, D);
+            ++n;
+        }
+        qsort(u, (size_t)n, sizeof(entry), entry_cmp);
+        for (int b = 0; b < k; ++b) {
+            idx[a * k + b] = (int32_t)u[b].idx;
+            d2[a * k + b] = u[b].d2;
+        }
+    }
+    free(u);
+}

@@ -1,0 +1,305 @@
+"""ctypes wrapper of the FP64 CPU oracle (``funcsne_oracle.c``).
+
+Test infrastructure only (see the package docstring). All state arrays are
+numpy float64 / int32 arrays owned by :class:`OracleState`.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from .build import build_oracle
+
+__all__ = ["lib", "philox", "OracleState", "bisect", "entropy", "topk_merge",
+           "exact_z", "kl_divergence", "exact_grad", "bruteforce_knn", "query_knn",
+           "ORACLE_BISECT_TOL", "ORACLE_BISECT_MAXIT", "STREAMS", "CAND_HD", "CAND_LD"]
+
+ORACLE_BISECT_TOL = 1e-9
+ORACLE_BISECT_MAXIT = 200
+STREAMS = dict(COIN=0, HD=1, LD=2, NEG=3, MLP=4, INSERT=5, INIT_HD=6, INIT_LD=7,
+               INIT_Y=8, ZINIT=9)
+CAND_HD = 32
+CAND_LD = 32
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build_oracle())
+        _declare(_lib)
+    return _lib
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_lp = C.POINTER(C.c_int64)
+_up = C.POINTER(C.c_uint32)
+_bp = C.POINTER(C.c_uint8)
+
+
+class _State(C.Structure):
+    _fields_ = [("N", C.c_int64), ("D", C.c_int32), ("d", C.c_int32), ("k_hd", C.c_int32),
+                ("k_ld", C.c_int32), ("n_neg", C.c_int32), ("alpha", C.c_double),
+                ("perplexity", C.c_double), ("seed", C.c_uint64), ("lr", C.c_double),
+                ("momentum", C.c_double), ("att_ratio", C.c_double), ("rep_ratio", C.c_double),
+                ("exaggeration", C.c_double), ("exag_iters", C.c_int32), ("hd_mode", C.c_int32),
+                ("neg_mode", C.c_int32), ("X", _dp), ("Y", _dp), ("V", _dp), ("hd_idx", _ip),
+                ("hd_d2", _dp), ("ld_idx", _ip), ("beta", _dp), ("P", _dp), ("Zhat", C.c_double),
+                ("E", C.c_double), ("t", C.c_uint32)]
+
+
+def _declare(L):
+    sp = C.POINTER(_State)
+    L.oracle_philox4x32_10.argtypes = [_up, _up, _up]
+    L.oracle_philox4x32_10.restype = None
+    L.oracle_entropy.argtypes = [_dp, C.c_int, C.c_double, _dp]
+    L.oracle_entropy.restype = C.c_double
+    L.oracle_bisect.argtypes = [_dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp]
+    L.oracle_bisect.restype = C.c_int
+    L.oracle_topk_merge.argtypes = [C.c_int64, C.c_int, _ip, _dp, C.c_int, _lp, _dp, _ip, _dp]
+    L.oracle_topk_merge.restype = C.c_int
+    L.oracle_hd_candidates.argtypes = [sp, C.c_int64, _lp]
+    L.oracle_hd_candidates.restype = None
+    L.oracle_ld_candidates.argtypes = [sp, C.c_int64, _lp]
+    L.oracle_ld_candidates.restype = None
+    L.oracle_initial_list.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int, C.c_uint32, _ip]
+    L.oracle_initial_list.restype = None
+    L.oracle_forces.argtypes = [sp, C.c_uint32, C.c_uint32, C.c_double, _dp, _dp, _dp]
+    L.oracle_forces.restype = C.c_double
+    L.oracle_init.argtypes = [sp, C.c_double, C.c_int]
+    L.oracle_init.restype = None
+    L.oracle_coin.argtypes = [sp]
+    L.oracle_coin.restype = C.c_int
+    L.oracle_step.argtypes = [sp, C.c_double, C.c_int, _dp, _dp, _bp, _lp, _dp]
+    L.oracle_step.restype = None
+    L.oracle_dense_p.argtypes = [sp, _dp]
+    L.oracle_dense_p.restype = None
+    L.oracle_exact_z.argtypes = [_dp, C.c_int64, C.c_int, C.c_double]
+    L.oracle_exact_z.restype = C.c_double
+    L.oracle_kl.argtypes = [_dp, _dp, C.c_int64, C.c_int, C.c_double]
+    L.oracle_kl.restype = C.c_double
+    L.oracle_exact_grad.argtypes = [_dp, _dp, C.c_int64, C.c_int, C.c_double, _dp]
+    L.oracle_exact_grad.restype = None
+    L.oracle_bruteforce_knn.argtypes = [_dp, C.c_int64, C.c_int, C.c_int, _ip, _dp]
+    L.oracle_bruteforce_knn.restype = None
+    L.oracle_query_knn.argtypes = [_dp, C.c_int64, C.c_int, _lp, C.c_int64, C.c_int, _ip, _dp]
+    L.oracle_query_knn.restype = None
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def philox(ctr, key):
+    """Philox4x32-10 block: 4 counter words, 2 key words -> 4 output words."""
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox4x32_10(_p(c, _up), _p(k, _up), _p(out, _up))
+    return out
+
+
+def entropy(d2, beta):
+    d2 = _f64(d2)
+    P = np.zeros_like(d2)
+    h = lib().oracle_entropy(_p(d2, _dp), len(d2), float(beta), _p(P, _dp))
+    return h, P
+
+
+def bisect(d2, perplexity, beta0=0.0, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
+    """Returns (beta, P, evaluations)."""
+    d2 = _f64(d2)
+    P = np.zeros_like(d2)
+    b = C.c_double(0.0)
+    it = lib().oracle_bisect(_p(d2, _dp), len(d2), float(perplexity), float(beta0), float(tol),
+                             int(maxit), C.byref(b), _p(P, _dp))
+    return b.value, P, it
+
+
+def topk_merge(i, old_idx, old_d2, cand_idx, cand_d2):
+    """Returns (new_idx, new_d2, changed)."""
+    old_idx = np.ascontiguousarray(old_idx, dtype=np.int32)
+    old_d2 = _f64(old_d2)
+    cand_idx = np.ascontiguousarray(cand_idx, dtype=np.int64)
+    cand_d2 = _f64(cand_d2)
+    k = len(old_idx)
+    ni = np.zeros(k, dtype=np.int32)
+    nd = np.zeros(k, dtype=np.float64)
+    ch = lib().oracle_topk_merge(int(i), k, _p(old_idx, _ip), _p(old_d2, _dp), len(cand_idx),
+                                 _p(cand_idx, _lp), _p(cand_d2, _dp), _p(ni, _ip), _p(nd, _dp))
+    return ni, nd, bool(ch)
+
+
+def exact_z(Y, alpha):
+    Y = _f64(Y)
+    return lib().oracle_exact_z(_p(Y, _dp), Y.shape[0], Y.shape[1], float(alpha))
+
+
+def kl_divergence(Pd, Y, alpha):
+    Pd = _f64(Pd)
+    Y = _f64(Y)
+    return lib().oracle_kl(_p(Pd, _dp), _p(Y, _dp), Y.shape[0], Y.shape[1], float(alpha))
+
+
+def exact_grad(Pd, Y, alpha):
+    Pd = _f64(Pd)
+    Y = _f64(Y)
+    G = np.zeros_like(Y)
+    lib().oracle_exact_grad(_p(Pd, _dp), _p(Y, _dp), Y.shape[0], Y.shape[1], float(alpha),
+                            _p(G, _dp))
+    return G
+
+
+def bruteforce_knn(X, k):
+    X = _f64(X)
+    N = X.shape[0]
+    idx = np.zeros((N, k), dtype=np.int32)
+    d2 = np.zeros((N, k), dtype=np.float64)
+    lib().oracle_bruteforce_knn(_p(X, _dp), N, X.shape[1], k, _p(idx, _ip), _p(d2, _dp))
+    return idx, d2
+
+
+def query_knn(X, queries, k):
+    X = _f64(X)
+    q = np.ascontiguousarray(queries, dtype=np.int64)
+    idx = np.zeros((len(q), k), dtype=np.int32)
+    d2 = np.zeros((len(q), k), dtype=np.float64)
+    lib().oracle_query_knn(_p(X, _dp), X.shape[0], X.shape[1], _p(q, _lp), len(q), k,
+                           _p(idx, _ip), _p(d2, _dp))
+    return idx, d2
+
+
+class OracleState:
+    """The method's state held in FP64 numpy arrays, stepped by the C oracle."""
+
+    def __init__(self, X, d, k_hd, k_ld, n_neg, alpha, perplexity, seed=0, lr=None,
+                 momentum=0.8, att_ratio=1.0, rep_ratio=1.0, exaggeration=1.0, exag_iters=0,
+                 hd_mode=0, neg_mode=0, init=True):
+        self.X = _f64(X)
+        N, D = self.X.shape
+        self.N, self.D = N, D
+        self.Y = np.zeros((N, d))
+        self.V = np.zeros((N, d))
+        self.hd_idx = np.zeros((N, k_hd), dtype=np.int32)
+        self.hd_d2 = np.zeros((N, k_hd))
+        self.ld_idx = np.zeros((N, k_ld), dtype=np.int32)
+        self.beta = np.zeros(N)
+        self.P = np.zeros((N, k_hd))
+        if lr is None:
+            lr = max(N / 12.0, 200.0)
+        s = _State()
+        s.N, s.D, s.d, s.k_hd, s.k_ld, s.n_neg = N, D, d, k_hd, k_ld, n_neg
+        s.alpha, s.perplexity, s.seed = alpha, perplexity, seed
+        s.lr, s.momentum, s.att_ratio, s.rep_ratio = lr, momentum, att_ratio, rep_ratio
+        s.exaggeration, s.exag_iters, s.hd_mode, s.neg_mode = exaggeration, exag_iters, hd_mode, neg_mode
+        self._s = s
+        self._bind()
+        if init:
+            lib().oracle_init(C.byref(s), ORACLE_BISECT_TOL, ORACLE_BISECT_MAXIT)
+
+    def _bind(self):
+        s = self._s
+        s.X = _p(self.X, _dp)
+        s.Y = _p(self.Y, _dp)
+        s.V = _p(self.V, _dp)
+        s.hd_idx = _p(self.hd_idx, _ip)
+        s.hd_d2 = _p(self.hd_d2, _dp)
+        s.ld_idx = _p(self.ld_idx, _ip)
+        s.beta = _p(self.beta, _dp)
+        s.P = _p(self.P, _dp)
+
+    # scalar state and options
+    def __getattr__(self, name):
+        if name in ("Zhat", "E", "t", "lr", "momentum", "att_ratio", "rep_ratio", "exaggeration",
+                    "exag_iters", "hd_mode", "neg_mode", "alpha", "perplexity", "seed", "n_neg",
+                    "k_hd", "k_ld", "d"):
+            return getattr(self.__dict__["_s"], name)
+        raise AttributeError(name)
+
+    def set(self, **kw):
+        for k, v in kw.items():
+            setattr(self._s, k, v)
+
+    def load(self, Y=None, V=None, hd_idx=None, ld_idx=None, beta=None, P=None, Zhat=None,
+             E=None, t=None):
+        """Overwrite parts of the state (for example with the GPU's exported state).
+        HD distances are recomputed in FP64 from X; the list order is kept."""
+        if Y is not None:
+            self.Y[...] = Y
+        if V is not None:
+            self.V[...] = V
+        if hd_idx is not None:
+            self.hd_idx[...] = hd_idx
+        if ld_idx is not None:
+            self.ld_idx[...] = ld_idx
+        if beta is not None:
+            self.beta[...] = beta
+        if P is not None:
+            self.P[...] = P
+        if Zhat is not None:
+            self._s.Zhat = Zhat
+        if E is not None:
+            self._s.E = E
+        if t is not None:
+            self._s.t = t
+        diff = self.X[:, None, :] - self.X[self.hd_idx]
+        self.hd_d2[...] = np.einsum("nkd,nkd->nk", diff, diff)
+
+    def coin(self):
+        return bool(lib().oracle_coin(C.byref(self._s)))
+
+    def hd_candidates(self, i):
+        out = np.zeros(CAND_HD, dtype=np.int64)
+        lib().oracle_hd_candidates(C.byref(self._s), int(i), _p(out, _lp))
+        return out
+
+    def ld_candidates(self, i):
+        out = np.zeros(CAND_LD, dtype=np.int64)
+        lib().oracle_ld_candidates(C.byref(self._s), int(i), _p(out, _lp))
+        return out
+
+    def forces(self, zhat=None, t=None, stream=STREAMS["NEG"]):
+        """Returns (A, R, Z_t, z per point) for the current lists, P and Y."""
+        A = np.zeros_like(self.Y)
+        R = np.zeros_like(self.Y)
+        z = np.zeros(self.N)
+        zt = lib().oracle_forces(C.byref(self._s), self._s.t if t is None else t, stream,
+                                 self._s.Zhat if zhat is None else zhat, _p(A, _dp), _p(R, _dp),
+                                 _p(z, _dp))
+        return A, R, zt, z
+
+    def step(self, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
+        """One iteration. Returns dict(A, R, flags, coin, n_new, z)."""
+        A = np.zeros_like(self.Y)
+        R = np.zeros_like(self.Y)
+        flags = np.zeros(self.N, dtype=np.uint8)
+        info = np.zeros(2, dtype=np.int64)
+        z = np.zeros(self.N)
+        lib().oracle_step(C.byref(self._s), float(tol), int(maxit), _p(A, _dp), _p(R, _dp),
+                          _p(flags, _bp), _p(info, _lp), _p(z, _dp))
+        return dict(A=A, R=R, flags=flags, coin=bool(info[0]), n_new=int(info[1]), z=z)
+
+    def dense_p(self):
+        Pd = np.zeros((self.N, self.N))
+        lib().oracle_dense_p(C.byref(self._s), _p(Pd, _dp))
+        return Pd
+
+    def initial_list(self, i, k, stream):
+        out = np.zeros(k, dtype=np.int32)
+        lib().oracle_initial_list(self._s.seed, self.N, int(i), int(k), int(stream), _p(out, _ip))
+        return out
+
+    def copy(self):
+        o = OracleState.__new__(OracleState)
+        o.__dict__.update({k: (v.copy() if isinstance(v, np.ndarray) else v)
+                           for k, v in self.__dict__.items() if k != "_s"})
+        o._s = _State.from_buffer_copy(self._s)
+        o._bind()
+        return o

@@ -1,0 +1,333 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle:
+published known-answer vectors, closed forms, brute force, finite
+differences, conservation laws and limiting cases of the paper's equations.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_07681_gb300 import synth
+from paper_2509_07681_gb300.quality import recall, rnx_auc, rnx_curve
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ---------------------------------------------------------------- Philox
+def _kat_rows():
+    rows = []
+    with open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(x, 16) for x in line.split()]
+            rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,out", _kat_rows())
+def test_philox_known_answers(ctr, key, out):
+    assert O.philox(ctr, key).tolist() == out
+
+
+# ---------------------------------------------------------------- bisection (Eq. 1)
+def test_bisection_hits_target_entropy():
+    g = np.random.default_rng(1)
+    for _ in range(50):
+        k = int(g.integers(8, 65))
+        d2 = np.sort(g.exponential(3.0, size=k) + g.uniform(0, 5))
+        perp = float(g.uniform(2.0, k - 1.5))
+        beta, P, it = O.bisect(d2, perp)
+        # entropy evaluated independently of the oracle's routine
+        p = np.exp(-beta * (d2 - d2.min()))
+        p /= p.sum()
+        H = -(p * np.log(p)).sum()
+        assert abs(H - math.log(perp)) < 1e-6
+        assert abs(P.sum() - 1.0) < 1e-12
+        np.testing.assert_allclose(P, p, rtol=1e-9, atol=1e-15)
+
+
+def test_bisection_two_point_closed_form():
+    # two neighbours at distances 0 and c: p = 1/(1+exp(-beta c)), binary entropy
+    from scipy.optimize import brentq
+    c = 2.5
+    for perp in [1.2, 1.5, 1.9]:
+        beta, P, _ = O.bisect([0.0, c], perp)
+
+        def h(b):
+            e = math.exp(-b * c)
+            p1, p2 = 1.0 / (1.0 + e), e / (1.0 + e)
+            return -(p1 * math.log(p1) + p2 * math.log(p2)) - math.log(perp)
+        ref = brentq(h, 1e-12, 20.0, xtol=1e-14)
+        assert abs(beta - ref) < 1e-6 * max(1.0, ref)
+
+
+def test_bisection_degenerate_cases():
+    # equal distances: every beta gives H = ln k; a reachable target is impossible
+    # when perplexity >= k, which must give the uniform distribution.
+    beta, P, _ = O.bisect(np.full(16, 3.0), 30.0)
+    assert beta == 0.0 and np.allclose(P, 1 / 16)
+    beta, P, _ = O.bisect(np.linspace(0, 1, 16), 16.0)
+    assert beta == 0.0 and np.allclose(P, 1 / 16)
+    h, p = O.entropy(np.full(8, 1.0), 5.0)
+    assert abs(h - math.log(8)) < 1e-12
+
+
+def test_entropy_monotone_in_beta():
+    d2 = np.sort(np.random.default_rng(2).exponential(1.0, 32))
+    hs = [O.entropy(d2, b)[0] for b in np.geomspace(1e-3, 1e3, 40)]
+    assert all(a >= b - 1e-12 for a, b in zip(hs, hs[1:]))
+    assert abs(hs[0] - math.log(32)) < 1e-2
+
+
+def test_warm_start_agrees_with_cold_start():
+    d2 = np.sort(np.random.default_rng(3).exponential(2.0, 32))
+    b0, P0, _ = O.bisect(d2, 10.0)
+    b1, P1, _ = O.bisect(d2, 10.0, beta0=b0 * 3.7)
+    assert abs(b1 - b0) < 1e-6 * b0
+    np.testing.assert_allclose(P0, P1, rtol=1e-6)
+
+
+# ---------------------------------------------------------------- top-k merge
+def _lex_knn(X, i, k):
+    d2 = ((X - X[i]) ** 2).sum(1)
+    d2[i] = np.inf
+    order = np.lexsort((np.arange(len(X)), d2))
+    return order[:k], d2[order[:k]]
+
+
+@pytest.mark.parametrize("gen", ["gauss", "integer"])
+def test_merge_with_all_candidates_is_exact_knn(gen):
+    rng = np.random.default_rng(4)
+    N, D, k = 200, 7, 8
+    X = rng.standard_normal((N, D)) if gen == "gauss" else synth.integer_grid(N, D, high=3, seed=4)
+    X = X.astype(np.float64)
+    for i in range(0, N, 13):
+        old = rng.choice(np.delete(np.arange(N), i), size=k, replace=False).astype(np.int32)
+        old_d2 = ((X[old] - X[i]) ** 2).sum(1)
+        o = np.lexsort((old, old_d2))
+        old, old_d2 = old[o], old_d2[o]
+        cand = np.arange(N)
+        cand_d2 = ((X - X[i]) ** 2).sum(1)
+        ni, nd, ch = O.topk_merge(i, old, old_d2, cand, cand_d2)
+        ref_i, ref_d = _lex_knn(X, i, k)
+        assert ni.tolist() == ref_i.tolist()
+        np.testing.assert_array_equal(nd, ref_d)
+        assert ch == (set(ref_i.tolist()) != set(old.tolist()))
+
+
+def test_merge_drops_self_duplicates_and_keeps_order_when_unchanged():
+    old = np.array([5, 3, 9], dtype=np.int32)
+    od = np.array([1.0, 2.0, 3.0])
+    # candidates: self (0), a duplicate of an old entry, a repeated candidate, and far ones
+    ni, nd, ch = O.topk_merge(0, old, od, [0, 3, 7, 7, 8], [0.0, 0.5, 9.0, 9.0, 8.0])
+    assert ni.tolist() == [5, 3, 9] and not ch
+    ni, nd, ch = O.topk_merge(0, old, od, [7, 7, 2], [1.5, 1.5, 2.0])
+    # tie at d2=2.0 between old 3 and candidate 2: smaller index first
+    assert ni.tolist() == [5, 7, 2] and ch
+
+
+# ---------------------------------------------------------------- candidates
+def _state(N=300, D=10, d=2, kh=16, kl=8, nneg=8, alpha=1.0, perp=8.0, seed=5, **kw):
+    X = synth.blobs(n=N, dim=D, n_clusters=5, seed=seed)
+    return O.OracleState(X, d, kh, kl, nneg, alpha, perp, seed=seed, **kw)
+
+
+def test_initial_lists_distinct_and_valid():
+    st = _state()
+    for lists, k in [(st.hd_idx, st.k_hd), (st.ld_idx, st.k_ld)]:
+        for i in range(st.N):
+            row = lists[i]
+            assert len(set(row.tolist())) == k
+            assert i not in row
+            assert row.min() >= 0 and row.max() < st.N
+    # HD lists ordered by (d2, idx) with exact distances
+    for i in range(0, st.N, 17):
+        d2 = ((st.X[st.hd_idx[i]] - st.X[i]) ** 2).sum(1)
+        assert np.all(np.diff(d2) >= 0)
+    # tiny N: k = N - 1 forces every other point into the list
+    st2 = _state(N=17, kh=16, kl=16, perp=4.0)
+    for i in range(17):
+        assert sorted(st2.hd_idx[i].tolist()) == [j for j in range(17) if j != i]
+
+
+def test_candidates_come_from_their_sources():
+    st = _state()
+    for i in range(0, st.N, 7):
+        c = st.hd_candidates(i)
+        nn_hd = set(st.hd_idx[st.hd_idx[i]].ravel().tolist())
+        nn_ld = set(st.ld_idx[st.ld_idx[i]].ravel().tolist())
+        assert set(c[:16].tolist()) <= nn_hd
+        assert set(c[16:20].tolist()) <= set(st.ld_idx[i].tolist())
+        assert set(c[20:24].tolist()) <= nn_ld
+        assert all(0 <= x < st.N and x != i for x in c[24:])
+        c = st.ld_candidates(i)
+        assert set(c[:16].tolist()) <= nn_ld
+        assert set(c[16:24].tolist()) <= set(st.hd_idx[i].tolist())
+        assert all(0 <= x < st.N and x != i for x in c[24:])
+
+
+def test_random_candidates_are_uniform():
+    # chi-square over many iterations: the random slots cover the other points uniformly
+    st = _state(N=40, kh=8, kl=8)
+    counts = np.zeros(40)
+    for t in range(400):
+        st.set(t=t)
+        c = st.hd_candidates(3)
+        for x in c[24:]:
+            counts[x] += 1
+    assert counts[3] == 0
+    exp = counts.sum() / 39
+    chi2 = (((counts - exp) ** 2) / exp)[np.arange(40) != 3].sum()
+    assert chi2 < 80  # 38 dof: p ~ 1e-4
+
+
+# ---------------------------------------------------------------- gradient (Eq. 4-6)
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 3.0])
+def test_exact_gradient_matches_finite_differences(alpha):
+    st = _state(N=40, D=6, d=3, kh=8, kl=6, perp=5.0)
+    rng = np.random.default_rng(6)
+    Y = rng.standard_normal((40, 3))
+    Pd = st.dense_p()
+    G = O.exact_grad(Pd, Y, alpha)
+    h = 1e-6
+    for i in range(0, 40, 9):
+        for c in range(3):
+            Yp, Ym = Y.copy(), Y.copy()
+            Yp[i, c] += h
+            Ym[i, c] -= h
+            fd = (O.kl_divergence(Pd, Yp, alpha) - O.kl_divergence(Pd, Ym, alpha)) / (2 * h)
+            assert abs(fd - G[i, c]) <= 1e-6 * max(1.0, np.abs(G).max())
+
+
+def test_dense_p_symmetric_and_normalised():
+    st = _state()
+    Pd = st.dense_p()
+    np.testing.assert_allclose(Pd, Pd.T, rtol=0, atol=1e-18)
+    assert abs(Pd.sum() - 1.0) < 1e-12
+    assert np.all(np.diag(Pd) == 0)
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 2.0])
+def test_exhaustive_split_equals_exact_gradient(alpha):
+    """Eq. 6's three-term split, with the rest summed exhaustively and the exact Z,
+    must reproduce Eq. 5 over the sparse symmetrised P."""
+    st = _state(N=120, D=8, d=2, kh=12, kl=8, alpha=alpha, perp=6.0, neg_mode=1)
+    rng = np.random.default_rng(7)
+    st.Y[...] = rng.standard_normal(st.Y.shape)
+    z = O.exact_z(st.Y, alpha)
+    A, R, zt, _ = st.forces(zhat=z)
+    assert abs(zt - z) <= 1e-12 * z
+    G = O.exact_grad(st.dense_p(), st.Y, alpha)
+    np.testing.assert_allclose(A - R, G, rtol=0, atol=1e-12 * np.abs(G).max())
+    # momentum conservation: both parts sum to zero over points
+    assert np.abs(A.sum(0)).max() < 1e-12 * np.abs(A).max() * st.N
+    assert np.abs(G.sum(0)).max() < 1e-12 * np.abs(G).max() * st.N
+
+
+def test_alpha_one_is_tsne_gradient():
+    """alpha = 1 reduces Eq. 5 to the t-SNE gradient of Eq. 3."""
+    st = _state(N=60, D=5, d=2, kh=8, kl=6, perp=5.0)
+    Y = np.random.default_rng(8).standard_normal((60, 2))
+    Pd = st.dense_p()
+    G = O.exact_grad(Pd, Y, 1.0)
+    diff = Y[:, None, :] - Y[None, :, :]
+    r2 = (diff ** 2).sum(-1)
+    num = 1.0 / (1.0 + r2)
+    np.fill_diagonal(num, 0.0)
+    Q = num / num.sum()
+    G3 = 4.0 * (((Pd - Q) * num)[:, :, None] * diff).sum(1)
+    np.testing.assert_allclose(G, G3, rtol=1e-10, atol=1e-14)
+
+
+def test_large_alpha_is_gaussian_kernel_sne():
+    """alpha -> infinity: w -> exp(-r2) and w^{1/alpha} -> 1 (symmetric SNE)."""
+    st = _state(N=50, D=5, d=2, kh=8, kl=6, perp=5.0)
+    Y = 0.5 * np.random.default_rng(9).standard_normal((50, 2))
+    Pd = st.dense_p()
+    G = O.exact_grad(Pd, Y, 1e7)
+    diff = Y[:, None, :] - Y[None, :, :]
+    w = np.exp(-(diff ** 2).sum(-1))
+    np.fill_diagonal(w, 0.0)
+    Q = w / w.sum()
+    Gs = 4.0 * ((Pd - Q)[:, :, None] * diff).sum(1)
+    np.testing.assert_allclose(G, Gs, rtol=1e-4, atol=1e-6 * np.abs(Gs).max())
+
+
+def test_negative_sampling_is_unbiased():
+    """Averaged over independent Philox streams, the sampled repulsion and Z
+    approach the exhaustive values (Monte-Carlo, 4 sigma)."""
+    st = _state(N=80, D=6, d=2, kh=8, kl=6, nneg=4, perp=5.0)
+    st.Y[...] = np.random.default_rng(10).standard_normal(st.Y.shape)
+    ex = st.copy()
+    ex.set(neg_mode=1)
+    z = O.exact_z(st.Y, st.alpha)
+    A0, R0, z0, _ = ex.forces(zhat=z)
+    Rs, Zs = [], []
+    for t in range(3000):
+        _, R, zt, _ = st.forces(zhat=z, t=t)
+        Rs.append(R)
+        Zs.append(zt)
+    Rs = np.array(Rs)
+    Zs = np.array(Zs)
+    assert abs(Zs.mean() - z0) < 4 * Zs.std() / math.sqrt(len(Zs))
+    m = Rs.mean(0)
+    se = Rs.std(0) / math.sqrt(len(Rs)) + 1e-15
+    assert np.mean(np.abs(m - R0) < 4 * se) > 0.99
+
+
+# ---------------------------------------------------------------- step
+def test_step_invariants():
+    st = _state(N=300, hd_mode=1)
+    for _ in range(5):
+        old_hd = st.hd_idx.copy()
+        out = st.step()
+        assert out["coin"]
+        changed = np.array([set(a.tolist()) != set(b.tolist()) for a, b in zip(old_hd, st.hd_idx)])
+        np.testing.assert_array_equal(changed, out["flags"].astype(bool))
+        assert out["n_new"] == changed.sum()
+        for i in range(st.N):
+            assert len(set(st.hd_idx[i].tolist())) == st.k_hd and i not in st.hd_idx[i]
+            assert len(set(st.ld_idx[i].tolist())) == st.k_ld and i not in st.ld_idx[i]
+            assert abs(st.P[i].sum() - 1) < 1e-9
+        # HD distances never increase position-wise as a set: the k-th distance is monotone
+    assert st.t == 5
+
+
+def test_hd_kth_distance_never_increases():
+    st = _state(N=300, hd_mode=1)
+    kth = st.hd_d2[:, -1].copy()
+    for _ in range(5):
+        st.step()
+        assert np.all(st.hd_d2[:, -1] <= kth + 1e-12)
+        kth = st.hd_d2[:, -1].copy()
+
+
+def test_coin_probability_follows_smoothed_fraction():
+    st = _state(N=50)
+    st.set(E=0.0)
+    fired = 0
+    for t in range(4000):
+        st.set(t=t)
+        fired += st.coin()
+    assert abs(fired / 4000 - 0.05) < 0.012
+    st.set(E=1.0)
+    assert all(st.coin() for _ in range(3))
+
+
+def test_whole_run_finds_neighbours_and_structure():
+    """Approximate method: statistics only. A short run on Gaussian blobs must
+    reach high HD-KNN recall and an embedding that keeps the clusters
+    (R_NX at the cluster scale) and part of the local structure."""
+    X = synth.blobs(n=600, dim=20, n_clusters=6, seed=11)
+    st = O.OracleState(X, 2, 16, 8, 8, 1.0, 10.0, seed=11, exaggeration=4.0, exag_iters=100)
+    for _ in range(300):
+        st.step()
+    exact, _ = O.bruteforce_knn(X, 128)
+    assert recall(st.hd_idx, exact[:, :16]) > 0.99
+    ld_exact, _ = O.bruteforce_knn(st.Y, 128)
+    r = rnx_curve(ld_exact, exact, len(X))
+    assert r[99] > 0.6
+    assert rnx_auc(ld_exact, exact, len(X), kmax=16) > 0.15
