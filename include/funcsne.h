@@ -1,0 +1,209 @@
+/*
+ * funcsne.h -- C ABI of the GB300 (sm_103a) FUnc-SNE iteration.
+ *
+ * FUnc-SNE (Lambert, Couplet, Verleysen, Lee, arXiv 2509.07681) embeds N
+ * high-dimensional (HD) points x_i in R^D into a low-dimensional (LD) space
+ * R^d by gradient descent on the variable-tail t-SNE objective (Eq. 4-5)
+ * while it refines, at every iteration, approximate HD and LD neighbour sets
+ * from neighbours of neighbours, cross-space proposals and random points
+ * (Section 3). This library runs one such iteration per step on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - Return value: FUNCSNE_OK (0) or a negative FUNCSNE_E_* code. No C++
+ *     exception crosses the ABI. funcsne_last_error() gives a message.
+ *   - Array arguments are plain pointers to row-major data; each entry
+ *     point accepts host memory or device memory of the current device,
+ *     detected with cudaPointerGetAttributes. Data passed in is copied;
+ *     the caller keeps ownership of every buffer it passes.
+ *   - Work is enqueued on the handle's CUDA stream (funcsne_set_stream);
+ *     calls that write caller buffers synchronise that stream first.
+ *   - Point indices are int32 (N < 2^31).
+ */
+#ifndef FUNCSNE_H
+#define FUNCSNE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FUNCSNE_OK = 0,
+    FUNCSNE_E_ARG = -1,   /* invalid argument (size, range, NULL pointer)        */
+    FUNCSNE_E_OOM = -2,   /* device allocation failed                            */
+    FUNCSNE_E_CUDA = -3,  /* a CUDA runtime call failed                          */
+    FUNCSNE_E_NAN = -4,   /* non-finite input data or embedding                   */
+    FUNCSNE_E_RANGE = -5, /* a device-side index check failed                     */
+    FUNCSNE_E_STATE = -6  /* call not valid in the handle's current state         */
+};
+
+/* HD storage precision (option "precision"). Distances are always
+ * accumulated in FP32; reduced-precision rows are dequantised first, and
+ * candidates that may enter a neighbour set are re-ranked from the FP32
+ * master rows, so neighbour sets equal those of FUNCSNE_FP32. */
+enum { FUNCSNE_FP32 = 0, FUNCSNE_BF16 = 1, FUNCSNE_FP8 = 2 };
+
+/* Neighbour spaces for funcsne_get_knn. */
+enum { FUNCSNE_SPACE_HD = 0, FUNCSNE_SPACE_LD = 1 };
+
+/* Placement of inserted points (funcsne_insert). */
+enum { FUNCSNE_PLACE_MEAN = 0, FUNCSNE_PLACE_SURROGATE = 1 };
+
+typedef struct funcsne funcsne_t;
+
+/* Snapshot of the per-point state, for testing and checkpointing. Every
+ * pointer may be NULL (field skipped) and may be host or device memory. */
+typedef struct {
+    float *Y;        /* N x d embedding                                        */
+    float *V;        /* N x d momentum                                          */
+    int32_t *hd_idx; /* N x k_hd HD neighbour indices, ordered by (d2, index)   */
+    float *hd_d2;    /* N x k_hd squared HD distances (FP32, exact rows)         */
+    int32_t *ld_idx; /* N x k_ld LD neighbour indices                           */
+    float *beta;     /* N bandwidths beta_i = 1 / (2 sigma_i^2)  (Eq. 1)         */
+    float *P;        /* N x k_hd conditional affinities p_{j|i}, aligned with hd_idx */
+    double Zhat;     /* running estimate of sum_{k != l} w_kl (Eq. 4)           */
+    double E;        /* smoothed fraction of points with new HD neighbours       */
+    uint32_t t;      /* iteration counter                                        */
+} funcsne_state_t;
+
+typedef struct {
+    int64_t N;
+    uint32_t t;
+    double E;              /* E[N_new / N] after the last step (Section 3)        */
+    double Zhat;           /* normalisation estimate used by the next step         */
+    double last_Z;         /* Z_t estimated by the last step                        */
+    int64_t last_n_new;    /* points whose HD set changed in the last step          */
+    int32_t last_coin;     /* 1 if the last step refined the HD sets               */
+    int32_t precision;     /* FUNCSNE_FP32 / _BF16 / _FP8                           */
+    uint32_t error_word;   /* device error bits (0 = none)                          */
+    int64_t cand_scored;   /* HD candidates scored (cumulative)                      */
+    int64_t cand_reranked; /* of which re-ranked from FP32 rows (cumulative)         */
+} funcsne_stats_t;
+
+/*
+ * funcsne_create -- allocate a handle and initialise the method's state
+ * (Section 3: optimisation starts right after the initial allocations).
+ *   X          N x D row-major FP32 data (host or device), copied.
+ *   N, D       number of points (k_hd < N, k_ld < N) and HD dimension (D >= 1).
+ *   d          LD dimension, 1 <= d <= 32 (Section 3: arbitrary LD dimension).
+ *   k_hd       HD neighbours per point, 2 <= k_hd <= 64.
+ *   k_ld       LD neighbours per point, 1 <= k_ld <= 32.
+ *   n_neg      negative samples per point and step, 1 <= n_neg <= 1024.
+ *   alpha      tail parameter of Eq. 4 (alpha > 0; 1 = t-SNE).
+ *   perplexity target perplexity of Eq. 1, 1 < perplexity < k_hd + 1.
+ *   seed       key of every Philox4x32-10 stream the method draws.
+ *   out        receives the handle (owned by the caller; funcsne_destroy).
+ * Initial state: k distinct random HD and LD neighbours per point, Y0 = a
+ * random linear projection of the centred data scaled to std 1e-4 per LD
+ * dimension, V = 0, bandwidths calibrated from a cold start, E = 1,
+ * Zhat = the estimate of Z at Y0.
+ * Errors: FUNCSNE_E_ARG (sizes, ranges, NULL), FUNCSNE_E_NAN (non-finite X),
+ * FUNCSNE_E_OOM, FUNCSNE_E_CUDA. On error *out is NULL.
+ */
+int funcsne_create(const float *X, int64_t N, int32_t D, int32_t d, int32_t k_hd,
+                   int32_t k_ld, int32_t n_neg, float alpha, float perplexity, uint64_t seed,
+                   funcsne_t **out);
+
+/*
+ * funcsne_set_option / funcsne_get_option -- numeric options by name:
+ *   "lr"             learning rate (default max(N/12, 200))
+ *   "momentum"       momentum of the update (default 0.8)
+ *   "att_ratio"      scale of the attractive force (Section 3; default 1)
+ *   "rep_ratio"      scale of the repulsive force (Section 3; default 1)
+ *   "exaggeration"   extra attraction factor while t < "exag_iters" (default 1)
+ *   "exag_iters"     iterations with exaggeration (default 0)
+ *   "hd_mode"        0: refine the HD sets with probability 0.05 + 0.95 E
+ *                    (Section 3); 1: every iteration; 2: never
+ *   "precision"      FUNCSNE_FP32 / FUNCSNE_BF16 / FUNCSNE_FP8 HD storage
+ *   "alpha"          tail parameter (may change between steps)
+ * Unknown keys or out-of-range values: FUNCSNE_E_ARG.
+ */
+int funcsne_set_option(funcsne_t *h, const char *key, double value);
+int funcsne_get_option(const funcsne_t *h, const char *key, double *value);
+
+/* Use the given cudaStream_t (NULL = the handle's own stream) for all work. */
+int funcsne_set_stream(funcsne_t *h, void *stream);
+
+/*
+ * funcsne_step -- enqueue n_iters iterations (Section 3 / Eq. 5-6):
+ *   1. with probability 0.05 + 0.95 E (or always / never, option hd_mode),
+ *      refine every HD set from 32 candidates (neighbours of HD neighbours,
+ *      LD neighbours and their neighbours, random points) by a top-k_hd
+ *      merge on (d2, index); flag points whose set changed and recalibrate
+ *      their bandwidth by bisection from the previous value;
+ *   2. refine every LD set from 32 candidates (neighbours of LD neighbours,
+ *      HD neighbours, random points) at the current embedding;
+ *   3. attraction over the HD sets (both directions of p_ij), repulsion over
+ *      the HD and LD sets plus n_neg Philox negatives, normalised by Zhat;
+ *   4. momentum update of Y; Zhat and E smoothed; t += 1.
+ * Asynchronous on the handle's stream. Errors surface at funcsne_sync.
+ */
+int funcsne_step(funcsne_t *h, int32_t n_iters);
+
+/* Wait for the handle's stream; report device error words (FUNCSNE_E_RANGE,
+ * FUNCSNE_E_NAN) and CUDA errors. */
+int funcsne_sync(funcsne_t *h);
+
+/*
+ * funcsne_insert -- append n_new points (Section 3: the algorithm admits new
+ * points without a pre-computation phase). X_new is n_new x D FP32 (host or
+ * device), copied. Each new point gets k_hd HD neighbours from random
+ * candidates refined by four neighbour-of-neighbour rounds against the
+ * existing points, its LD position by `placement` (FUNCSNE_PLACE_MEAN: mean
+ * of its HD neighbours' positions; FUNCSNE_PLACE_SURROGATE: the online MLP,
+ * falling back to the mean while the MLP is untrained), and LD neighbours
+ * seeded from its HD neighbours. *first_id receives the index of the first
+ * new point (ids are contiguous). Errors: FUNCSNE_E_ARG, FUNCSNE_E_OOM.
+ */
+int funcsne_insert(funcsne_t *h, const float *X_new, int64_t n_new, int32_t placement,
+                   int64_t *first_id);
+
+/* Copy the first min(N, cap_rows) rows of the N x d embedding into Y_out. */
+int funcsne_get_embedding(const funcsne_t *h, float *Y_out, int64_t cap_rows);
+
+/* Copy the current neighbour lists of `space` (FUNCSNE_SPACE_HD: N x k_hd,
+ * FUNCSNE_SPACE_LD: N x k_ld) into idx and, when d2 is non-NULL, their
+ * squared distances (LD distances at the current embedding). */
+int funcsne_get_knn(const funcsne_t *h, int32_t space, int32_t *idx, float *d2);
+
+int funcsne_get_stats(const funcsne_t *h, funcsne_stats_t *stats);
+
+/* Snapshot / restore the per-point state (see funcsne_state_t). On import,
+ * HD distances are recomputed from X and each HD list (with its P row) is
+ * ordered by (d2, index); hd_d2 is ignored. Lists must hold distinct
+ * indices other than the point itself (FUNCSNE_E_ARG otherwise). */
+int funcsne_export_state(const funcsne_t *h, funcsne_state_t *st);
+int funcsne_import_state(funcsne_t *h, const funcsne_state_t *st);
+
+/* Run one iteration like funcsne_step and also copy the forces of step 3
+ * before the update: att (N x d) = sum over HD pairs of
+ * 4 p_ij w^{1/alpha} (y_i - y_j), rep (N x d) = the estimated
+ * 4 sum_j q_ij w^{1/alpha} (y_i - y_j), so that dL/dy = att - rep (Eq. 5). */
+int funcsne_debug_step(funcsne_t *h, float *att, float *rep);
+
+/* Run n_iters iterations like funcsne_step but with direct kernel launches
+ * and CUDA events around each kernel on the handle's stream; waits for the
+ * stream and writes the summed device time (milliseconds) of the fused
+ * step kernel and of the update kernel. For measurement. */
+int funcsne_profile_step(funcsne_t *h, int32_t n_iters, double *ms_step_kernel,
+                         double *ms_update_kernel);
+
+/* Exact k nearest HD neighbours (FP32 distances, ties by index) of the n_q
+ * query points `queries` (int32, host or device), by brute force over all
+ * points: for measuring neighbour recall. idx: n_q x k, d2: n_q x k or NULL. */
+int funcsne_exact_knn(const funcsne_t *h, const int32_t *queries, int64_t n_q, int32_t k,
+                      int32_t *idx, float *d2);
+
+/* Message for the last error on this handle (or the last create failure
+ * when h is NULL). Valid until the next call on the handle. */
+const char *funcsne_last_error(const funcsne_t *h);
+
+/* Release the handle and its device memory (NULL-safe). */
+void funcsne_destroy(funcsne_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FUNCSNE_H */

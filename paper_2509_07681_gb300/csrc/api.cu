@@ -1,0 +1,839 @@
+// Host runtime behind the C ABI of include/funcsne.h: the handle, argument
+// checks, device memory layout, CUDA-graph replay of the iteration, and the
+// copy-in / copy-out entry points.
+//
+// Device layout (N points, LD rows padded to DP = 2, 4, 8, 16 or 32 floats):
+//   X32   N x xpitch FP32 (xpitch = D rounded up to 4; zero padding)
+//   Xq    N x qpitch BF16 / FP8 copy (only in reduced-precision modes)
+//   Y V A R  N x DP FP32 (element count rounded up to a multiple of 4)
+//   hd_idx[2] hd_d2[2]  N x k_hd ping-pong lists;  ld_idx[2]  N x k_ld
+//   P N x k_hd, beta N; DevScalars; per-block Z partials and counters.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/funcsne.h"
+#include "launch.h"
+#include "params.h"
+
+using namespace fsne;
+
+struct funcsne {
+    int64_t N = 0;
+    int32_t D = 0, d = 0, DP = 0, k_hd = 0, k_ld = 0, n_neg = 0, RH = 1;
+    float alpha = 1.f, perplexity = 30.f;
+    uint64_t seed = 0;
+    // options
+    double lr = 200.0, momentum = 0.8, att = 1.0, rep = 1.0, exaggeration = 1.0;
+    int32_t exag_iters = 0, hd_mode = kHdAdaptive, precision = FUNCSNE_FP32;
+    // layout
+    int32_t xpitch = 0, n4 = 0, xs_floats = 0, qpitch = 0, nq = 0, qscale_off = 0;
+    int64_t yelem = 0;
+    // device memory
+    float* X32 = nullptr;
+    uint8_t* Xq = nullptr;
+    float *Y = nullptr, *V = nullptr, *A = nullptr, *R = nullptr;
+    int32_t* hd_idx[2] = {nullptr, nullptr};
+    float* hd_d2[2] = {nullptr, nullptr};
+    int32_t* ld_idx[2] = {nullptr, nullptr};
+    float *P = nullptr, *beta = nullptr;
+    DevScalars* sc = nullptr;
+    double* zpart = nullptr;
+    unsigned long long* cnt = nullptr;
+    int32_t max_blocks = 0;
+    // execution
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int step_blocks = 0, update_blocks = 0;
+    size_t step_smem = 0;
+    cudaGraphExec_t graph1 = nullptr, graph8 = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(funcsne* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_create_error = buf;
+    return code;
+}
+
+#define FSNE_CUDA(h, call)                                                                          \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? FUNCSNE_E_OOM : FUNCSNE_E_CUDA,      \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);       \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+void drop_graphs(funcsne* h) {
+    if (h->graph1) cudaGraphExecDestroy(h->graph1);
+    if (h->graph8) cudaGraphExecDestroy(h->graph8);
+    h->graph1 = h->graph8 = nullptr;
+}
+
+StepParams step_params(const funcsne* h) {
+    StepParams p{};
+    p.N = h->N;
+    p.k_hd = h->k_hd;
+    p.k_ld = h->k_ld;
+    p.n_neg = h->n_neg;
+    p.n4 = h->n4;
+    p.xpitch = h->xpitch;
+    p.nq = h->nq;
+    p.qpitch = h->qpitch;
+    p.qscale_off = h->qscale_off;
+    p.hd_mode = h->hd_mode;
+    p.xs_floats = h->xs_floats;
+    p.smem_per_warp = h->xs_floats * 4 + 96 * 4;
+    p.alpha = h->alpha;
+    p.inv_alpha = 1.f / h->alpha;
+    p.inv2N = static_cast<float>(1.0 / (2.0 * static_cast<double>(h->N)));
+    p.neg_scale = static_cast<float>(static_cast<double>(h->N - 1) / h->n_neg);
+    p.log_perp = std::log(h->perplexity);
+    const float gamma = static_cast<float>((h->xs_floats + 4) * std::ldexp(1.0, -24) * 1.01);
+    p.q_gamma = gamma;
+    if (h->precision == FUNCSNE_BF16) {
+        p.q_u = static_cast<float>(std::ldexp(1.0, -8) * (1.0 + std::ldexp(1.0, -20)));
+        p.q_a = 0.f;
+    } else {
+        p.q_u = static_cast<float>(std::ldexp(1.0, -4) * (1.0 + std::ldexp(1.0, -20)) + std::ldexp(1.0, -22));
+        p.q_a = static_cast<float>(std::ldexp(1.0, -10) * (1.0 + std::ldexp(1.0, -20)));
+    }
+    p.seed = h->seed;
+    p.X32 = h->X32;
+    p.Xq = h->Xq;
+    p.Y = h->Y;
+    p.A = h->A;
+    p.R = h->R;
+    p.hd_idx0 = h->hd_idx[0];
+    p.hd_idx1 = h->hd_idx[1];
+    p.hd_d20 = h->hd_d2[0];
+    p.hd_d21 = h->hd_d2[1];
+    p.ld_idx0 = h->ld_idx[0];
+    p.ld_idx1 = h->ld_idx[1];
+    p.P = h->P;
+    p.beta = h->beta;
+    p.sc = h->sc;
+    p.zpart = h->zpart;
+    p.cnt = h->cnt;
+    return p;
+}
+
+UpdateParams update_params(const funcsne* h, float* dbg_att, float* dbg_rep) {
+    UpdateParams u{};
+    u.n_elem = h->yelem;
+    u.n_zpart = h->step_blocks;
+    u.hd_mode = h->hd_mode;
+    u.N = h->N;
+    u.lr = static_cast<float>(h->lr);
+    u.momentum = static_cast<float>(h->momentum);
+    u.att = static_cast<float>(h->att);
+    u.rep = static_cast<float>(h->rep);
+    u.exaggeration = static_cast<float>(h->exaggeration);
+    u.exag_iters = h->exag_iters;
+    u.seed = h->seed;
+    u.Y = h->Y;
+    u.V = h->V;
+    u.A = h->A;
+    u.R = h->R;
+    u.dbg_att = dbg_att;
+    u.dbg_rep = dbg_rep;
+    u.sc = h->sc;
+    u.zpart = h->zpart;
+    u.cnt = h->cnt;
+    return u;
+}
+
+cudaError_t launch_step_kernel(const funcsne* h, const StepParams& p, cudaStream_t s) {
+    switch (h->precision) {
+        case FUNCSNE_FP32: return step_launch_f32(p, h->DP, h->RH, h->step_blocks, h->step_smem, s);
+        case FUNCSNE_BF16: return step_launch_bf16(p, h->DP, h->RH, h->step_blocks, h->step_smem, s);
+        default: return step_launch_fp8(p, h->DP, h->RH, h->step_blocks, h->step_smem, s);
+    }
+}
+
+// Grid of the step kernel: resident blocks per SM x SMs (persistent warps).
+int configure_step(funcsne* h) {
+    h->step_smem = static_cast<size_t>(8) * (h->xs_floats * 4 + 96 * 4);
+    int occ = 0;
+    switch (h->precision) {
+        case FUNCSNE_FP32: occ = step_occupancy_f32(h->DP, h->RH, h->step_smem); break;
+        case FUNCSNE_BF16: occ = step_occupancy_bf16(h->DP, h->RH, h->step_smem); break;
+        default: occ = step_occupancy_fp8(h->DP, h->RH, h->step_smem); break;
+    }
+    if (occ < 1) occ = 1;
+    int64_t blocks = static_cast<int64_t>(occ) * h->num_sms;
+    const int64_t need = (h->N + 7) / 8;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    if (blocks > h->max_blocks) blocks = h->max_blocks;
+    h->step_blocks = static_cast<int>(blocks);
+    int64_t ub = (h->yelem / 4 + 255) / 256;
+    if (ub > 4L * h->num_sms) ub = 4L * h->num_sms;
+    if (ub < 1) ub = 1;
+    h->update_blocks = static_cast<int>(ub);
+    drop_graphs(h);
+    return FUNCSNE_OK;
+}
+
+int enqueue_iteration(funcsne* h, cudaStream_t s, float* dbg_att, float* dbg_rep) {
+    const StepParams p = step_params(h);
+    FSNE_CUDA(h, launch_step_kernel(h, p, s));
+    FSNE_CUDA(h, update_launch(update_params(h, dbg_att, dbg_rep), h->update_blocks, s));
+    return FUNCSNE_OK;
+}
+
+int build_graph(funcsne* h, int iters, cudaGraphExec_t* out) {
+    // capture on the handle's own stream; the graph may then run on any stream
+    cudaGraph_t g = nullptr;
+    FSNE_CUDA(h, cudaStreamBeginCapture(h->own_stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < iters; ++k) {
+        const StepParams p = step_params(h);
+        cudaError_t e1 = launch_step_kernel(h, p, h->own_stream);
+        cudaError_t e2 = update_launch(update_params(h, nullptr, nullptr), h->update_blocks, h->own_stream);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            cudaStreamEndCapture(h->own_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return fail(h, FUNCSNE_E_CUDA, "graph capture: %s",
+                        cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+        }
+    }
+    FSNE_CUDA(h, cudaStreamEndCapture(h->own_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    FSNE_CUDA(h, e);
+    return FUNCSNE_OK;
+}
+
+int read_scalars(funcsne* h, DevScalars* out) {
+    FSNE_CUDA(h, cudaMemcpyAsync(out, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+    FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return FUNCSNE_OK;
+}
+
+// Copy an N x cols row-major array between a caller buffer (pitch cols) and
+// a device array of pitch `dpitch` elements.
+template <typename T>
+int copy_rows(funcsne* h, T* dst, size_t dst_pitch, const T* src, size_t src_pitch, int64_t rows, size_t cols) {
+    if (rows <= 0) return FUNCSNE_OK;
+    FSNE_CUDA(h, cudaMemcpy2DAsync(dst, dst_pitch * sizeof(T), src, src_pitch * sizeof(T), cols * sizeof(T),
+                                   static_cast<size_t>(rows), cudaMemcpyDefault, h->stream));
+    return FUNCSNE_OK;
+}
+
+void free_all(funcsne* h) {
+    drop_graphs(h);
+    cudaFree(h->X32);
+    cudaFree(h->Xq);
+    cudaFree(h->Y);
+    cudaFree(h->V);
+    cudaFree(h->A);
+    cudaFree(h->R);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->hd_idx[b]);
+        cudaFree(h->hd_d2[b]);
+        cudaFree(h->ld_idx[b]);
+    }
+    cudaFree(h->P);
+    cudaFree(h->beta);
+    cudaFree(h->sc);
+    cudaFree(h->zpart);
+    cudaFree(h->cnt);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+}
+
+int quantize(funcsne* h) {
+    cudaFree(h->Xq);
+    h->Xq = nullptr;
+    if (h->precision == FUNCSNE_FP32) {
+        h->qpitch = h->nq = h->qscale_off = 0;
+        return FUNCSNE_OK;
+    }
+    if (h->precision == FUNCSNE_BF16) {
+        h->qpitch = round_up(2 * h->D, 16);
+        h->nq = h->qpitch / 16;
+        h->qscale_off = 0;
+    } else {
+        const int nw = (h->D + 3) / 4;
+        h->qpitch = round_up(4 * nw + 4, 16);
+        h->nq = nw;
+        h->qscale_off = h->qpitch - 4;
+    }
+    FSNE_CUDA(h, dalloc(&h->Xq, static_cast<size_t>(h->N) * h->qpitch));
+    FSNE_CUDA(h, cudaMemsetAsync(h->Xq, 0, static_cast<size_t>(h->N) * h->qpitch, h->stream));
+    FSNE_CUDA(h, launch_quantize(h->X32, h->N, h->D, h->xpitch, h->precision, h->qpitch, h->qscale_off, h->Xq,
+                                 h->stream));
+    return FUNCSNE_OK;
+}
+
+int check_errors(funcsne* h) {
+    DevScalars s;
+    int rc = read_scalars(h, &s);
+    if (rc) return rc;
+    if (s.err & kErrIndex) return fail(h, FUNCSNE_E_RANGE, "device index check failed (error word 0x%x)", s.err);
+    if (s.err & kErrNonFinite) return fail(h, FUNCSNE_E_NAN, "non-finite values (error word 0x%x)", s.err);
+    return FUNCSNE_OK;
+}
+
+int clear_error_word(funcsne* h) {
+    FSNE_CUDA(h, cudaMemsetAsync(&h->sc->err, 0, sizeof(uint32_t), h->stream));
+    return FUNCSNE_OK;
+}
+
+ZinitParams zinit_params(const funcsne* h, const int32_t* hd, const int32_t* ld, double* part) {
+    ZinitParams z{};
+    z.N = h->N;
+    z.k_hd = h->k_hd;
+    z.k_ld = h->k_ld;
+    z.n_neg = h->n_neg;
+    z.alpha = h->alpha;
+    z.inv_alpha = 1.f / h->alpha;
+    z.neg_scale = static_cast<float>(static_cast<double>(h->N - 1) / h->n_neg);
+    z.t = 0;
+    z.stream = kStreamZinit;
+    z.seed = h->seed;
+    z.Y = h->Y;
+    z.hd_idx = hd;
+    z.ld_idx = ld;
+    z.part = part;
+    return z;
+}
+
+}  // namespace
+
+extern "C" {
+
+int funcsne_create(const float* X, int64_t N, int32_t D, int32_t d, int32_t k_hd, int32_t k_ld, int32_t n_neg,
+                   float alpha, float perplexity, uint64_t seed, funcsne_t** out) {
+    if (!out) return fail(nullptr, FUNCSNE_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!X) return fail(nullptr, FUNCSNE_E_ARG, "X is NULL");
+    if (D < 1 || D > 4096) return fail(nullptr, FUNCSNE_E_ARG, "D must be in [1, 4096] (got %d)", D);
+    if (d < 1 || d > 32) return fail(nullptr, FUNCSNE_E_ARG, "d must be in [1, 32] (got %d)", d);
+    if (k_hd < 2 || k_hd > 64) return fail(nullptr, FUNCSNE_E_ARG, "k_hd must be in [2, 64] (got %d)", k_hd);
+    if (k_ld < 1 || k_ld > 32) return fail(nullptr, FUNCSNE_E_ARG, "k_ld must be in [1, 32] (got %d)", k_ld);
+    if (N <= k_hd || N <= k_ld || N >= (int64_t(1) << 31) - 1)
+        return fail(nullptr, FUNCSNE_E_ARG, "N must exceed k_hd and k_ld and be < 2^31 - 1 (got %lld)",
+                    static_cast<long long>(N));
+    if (n_neg < 1 || n_neg > 1024) return fail(nullptr, FUNCSNE_E_ARG, "n_neg must be in [1, 1024]");
+    if (!(alpha > 0.f) || !std::isfinite(alpha)) return fail(nullptr, FUNCSNE_E_ARG, "alpha must be > 0");
+    if (!(perplexity > 1.f) || !(perplexity < static_cast<float>(k_hd) + 1.f))
+        return fail(nullptr, FUNCSNE_E_ARG, "perplexity must be in (1, k_hd + 1)");
+
+    funcsne* h = new funcsne();
+    h->N = N;
+    h->D = D;
+    h->d = d;
+    h->DP = d <= 2 ? 2 : d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32;
+    h->k_hd = k_hd;
+    h->k_ld = k_ld;
+    h->n_neg = n_neg;
+    h->RH = k_hd <= 32 ? 1 : 2;
+    h->alpha = alpha;
+    h->perplexity = perplexity;
+    h->seed = seed;
+    h->lr = std::fmax(static_cast<double>(N) / 12.0, 200.0);
+    h->xpitch = round_up(D, 4);
+    h->n4 = h->xpitch / 4;
+    h->xs_floats = round_up(D, 16);
+    h->yelem = (N * h->DP + 3) / 4 * 4;
+
+    auto bail = [&](int rc) {
+        g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return rc;
+    };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        fail(h, FUNCSNE_E_CUDA, "no CUDA device available");
+        return bail(FUNCSNE_E_CUDA);
+    }
+    h->max_blocks = 64 * h->num_sms;
+#define CREATE_CUDA(call)                                                                           \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            fail(h, e_ == cudaErrorMemoryAllocation ? FUNCSNE_E_OOM : FUNCSNE_E_CUDA, "%s: %s", #call, \
+                 cudaGetErrorString(e_));                                                           \
+            return bail(e_ == cudaErrorMemoryAllocation ? FUNCSNE_E_OOM : FUNCSNE_E_CUDA);          \
+        }                                                                                           \
+    } while (0)
+    CREATE_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    h->stream = h->own_stream;
+    const size_t nk_hd = static_cast<size_t>(N) * k_hd, nk_ld = static_cast<size_t>(N) * k_ld;
+    CREATE_CUDA(dalloc(&h->X32, static_cast<size_t>(N) * h->xpitch));
+    CREATE_CUDA(dalloc(&h->Y, h->yelem));
+    CREATE_CUDA(dalloc(&h->V, h->yelem));
+    CREATE_CUDA(dalloc(&h->A, h->yelem));
+    CREATE_CUDA(dalloc(&h->R, h->yelem));
+    for (int b = 0; b < 2; ++b) {
+        CREATE_CUDA(dalloc(&h->hd_idx[b], nk_hd));
+        CREATE_CUDA(dalloc(&h->hd_d2[b], nk_hd));
+        CREATE_CUDA(dalloc(&h->ld_idx[b], nk_ld));
+    }
+    CREATE_CUDA(dalloc(&h->P, nk_hd));
+    CREATE_CUDA(dalloc(&h->beta, static_cast<size_t>(N)));
+    CREATE_CUDA(dalloc(&h->sc, 1));
+    CREATE_CUDA(dalloc(&h->zpart, static_cast<size_t>(h->max_blocks) + 1));
+    CREATE_CUDA(dalloc(&h->cnt, 3 * static_cast<size_t>(h->max_blocks) + 3));
+    cudaStream_t s = h->stream;
+    CREATE_CUDA(cudaMemsetAsync(h->X32, 0, static_cast<size_t>(N) * h->xpitch * sizeof(float), s));
+    CREATE_CUDA(cudaMemcpy2DAsync(h->X32, h->xpitch * sizeof(float), X, D * sizeof(float), D * sizeof(float),
+                                  static_cast<size_t>(N), cudaMemcpyDefault, s));
+    CREATE_CUDA(cudaMemsetAsync(h->Y, 0, h->yelem * sizeof(float), s));
+    CREATE_CUDA(cudaMemsetAsync(h->V, 0, h->yelem * sizeof(float), s));
+    CREATE_CUDA(cudaMemsetAsync(h->A, 0, h->yelem * sizeof(float), s));
+    CREATE_CUDA(cudaMemsetAsync(h->R, 0, h->yelem * sizeof(float), s));
+    DevScalars init{};
+    init.E = 1.0;
+    init.Zhat = 1.0;
+    CREATE_CUDA(cudaMemcpyAsync(h->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    CREATE_CUDA(launch_check_finite(h->X32, static_cast<int64_t>(N) * h->xpitch, &h->sc->err, s));
+    {
+        DevScalars chk;
+        CREATE_CUDA(cudaMemcpyAsync(&chk, h->sc, sizeof(chk), cudaMemcpyDeviceToHost, s));
+        CREATE_CUDA(cudaStreamSynchronize(s));
+        if (chk.err) {
+            fail(h, FUNCSNE_E_NAN, "X holds non-finite values");
+            return bail(FUNCSNE_E_NAN);
+        }
+    }
+    // initial state
+    CREATE_CUDA(launch_init_lists(N, k_hd, kStreamInitHd, seed, h->hd_idx[0], s));
+    CREATE_CUDA(launch_init_lists(N, k_ld, kStreamInitLd, seed, h->ld_idx[0], s));
+    {
+        FinalizeParams f{};
+        f.N = N;
+        f.k_hd = k_hd;
+        f.n4 = h->n4;
+        f.xpitch = h->xpitch;
+        f.log_perp = std::log(perplexity);
+        f.X32 = h->X32;
+        f.idx = h->hd_idx[0];
+        f.d2 = h->hd_d2[0];
+        f.P = h->P;
+        f.beta = h->beta;
+        f.Pin = nullptr;
+        int blocks = 8 * h->num_sms;
+        CREATE_CUDA(launch_hd_finalize(f, blocks, s));
+    }
+    {
+        // FP64 scratch for the projection: R, mu, moments and block partials
+        const int64_t cols = D > h->DP ? D : h->DP;
+        const int64_t len = static_cast<int64_t>(D) * d + D + 2 * h->DP + 1024 * cols;
+        double* scratch = nullptr;
+        CREATE_CUDA(dalloc(&scratch, static_cast<size_t>(len)));
+        cudaError_t e = launch_init_y(h->X32, N, D, h->xpitch, d, h->DP, seed, h->Y, scratch, len, s);
+        if (e == cudaSuccess) {
+            ZinitParams z = zinit_params(h, h->hd_idx[0], h->ld_idx[0], scratch);
+            int blocks = 4 * h->num_sms;
+            if (blocks > 1024) blocks = 1024;
+            e = launch_zinit(z, h->DP, blocks, h->sc, s);
+        }
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(scratch);
+        CREATE_CUDA(e);
+        CREATE_CUDA(e2);
+    }
+#undef CREATE_CUDA
+    configure_step(h);
+    *out = h;
+    return FUNCSNE_OK;
+}
+
+int funcsne_set_option(funcsne_t* h, const char* key, double v) {
+    if (!h || !key) return fail(h, FUNCSNE_E_ARG, "NULL handle or key");
+    const std::string k(key);
+    if (!std::isfinite(v)) return fail(h, FUNCSNE_E_ARG, "option %s: value must be finite", key);
+    if (k == "lr") {
+        if (!(v > 0)) return fail(h, FUNCSNE_E_ARG, "lr must be > 0");
+        h->lr = v;
+    } else if (k == "momentum") {
+        if (v < 0 || v >= 1) return fail(h, FUNCSNE_E_ARG, "momentum must be in [0, 1)");
+        h->momentum = v;
+    } else if (k == "att_ratio") {
+        if (v < 0) return fail(h, FUNCSNE_E_ARG, "att_ratio must be >= 0");
+        h->att = v;
+    } else if (k == "rep_ratio") {
+        if (v < 0) return fail(h, FUNCSNE_E_ARG, "rep_ratio must be >= 0");
+        h->rep = v;
+    } else if (k == "exaggeration") {
+        if (v <= 0) return fail(h, FUNCSNE_E_ARG, "exaggeration must be > 0");
+        h->exaggeration = v;
+    } else if (k == "exag_iters") {
+        if (v < 0 || v > 2e9) return fail(h, FUNCSNE_E_ARG, "exag_iters out of range");
+        h->exag_iters = static_cast<int32_t>(v);
+    } else if (k == "hd_mode") {
+        const int m = static_cast<int>(v);
+        if (m != v || m < 0 || m > 2) return fail(h, FUNCSNE_E_ARG, "hd_mode must be 0, 1 or 2");
+        h->hd_mode = m;
+    } else if (k == "alpha") {
+        if (!(v > 0)) return fail(h, FUNCSNE_E_ARG, "alpha must be > 0");
+        h->alpha = static_cast<float>(v);
+    } else if (k == "precision") {
+        const int m = static_cast<int>(v);
+        if (m != v || m < 0 || m > 2) return fail(h, FUNCSNE_E_ARG, "precision must be 0, 1 or 2");
+        if (m != h->precision) {
+            h->precision = m;
+            int rc = quantize(h);
+            if (rc) return rc;
+            configure_step(h);
+        }
+    } else {
+        return fail(h, FUNCSNE_E_ARG, "unknown option '%s'", key);
+    }
+    drop_graphs(h);
+    return FUNCSNE_OK;
+}
+
+int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
+    funcsne* h = const_cast<funcsne*>(hc);
+    if (!h || !key || !v) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    const std::string k(key);
+    if (k == "lr") *v = h->lr;
+    else if (k == "momentum") *v = h->momentum;
+    else if (k == "att_ratio") *v = h->att;
+    else if (k == "rep_ratio") *v = h->rep;
+    else if (k == "exaggeration") *v = h->exaggeration;
+    else if (k == "exag_iters") *v = h->exag_iters;
+    else if (k == "hd_mode") *v = h->hd_mode;
+    else if (k == "alpha") *v = h->alpha;
+    else if (k == "precision") *v = h->precision;
+    else if (k == "step_blocks") *v = h->step_blocks;
+    else return fail(h, FUNCSNE_E_ARG, "unknown option '%s'", key);
+    return FUNCSNE_OK;
+}
+
+int funcsne_set_stream(funcsne_t* h, void* stream) {
+    if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
+    // order the new stream after all work already queued on the old one
+    cudaEvent_t ev;
+    FSNE_CUDA(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    FSNE_CUDA(h, cudaEventRecord(ev, h->stream));
+    h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
+    cudaError_t e = cudaStreamWaitEvent(h->stream, ev, 0);
+    cudaEventDestroy(ev);
+    FSNE_CUDA(h, e);
+    return FUNCSNE_OK;
+}
+
+int funcsne_step(funcsne_t* h, int32_t n_iters) {
+    if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
+    if (n_iters < 0) return fail(h, FUNCSNE_E_ARG, "n_iters must be >= 0");
+    if (n_iters == 0) return FUNCSNE_OK;
+    if (!h->graph1) {
+        int rc = build_graph(h, 1, &h->graph1);
+        if (rc) return rc;
+    }
+    if (n_iters >= 8 && !h->graph8) {
+        int rc = build_graph(h, 8, &h->graph8);
+        if (rc) return rc;
+    }
+    int left = n_iters;
+    while (left >= 8) {
+        FSNE_CUDA(h, cudaGraphLaunch(h->graph8, h->stream));
+        left -= 8;
+    }
+    while (left-- > 0) FSNE_CUDA(h, cudaGraphLaunch(h->graph1, h->stream));
+    return FUNCSNE_OK;
+}
+
+int funcsne_sync(funcsne_t* h) {
+    if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
+    FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    FSNE_CUDA(h, cudaGetLastError());
+    return check_errors(h);
+}
+
+int funcsne_insert(funcsne_t* h, const float* X_new, int64_t n_new, int32_t placement, int64_t* first_id) {
+    (void)X_new;
+    (void)n_new;
+    (void)placement;
+    (void)first_id;
+    return fail(h, FUNCSNE_E_STATE, "funcsne_insert is not available in this build");
+}
+
+int funcsne_get_embedding(const funcsne_t* hc, float* Y_out, int64_t cap_rows) {
+    funcsne* h = const_cast<funcsne*>(hc);
+    if (!h || !Y_out) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    const int64_t rows = cap_rows < h->N ? cap_rows : h->N;
+    int rc = copy_rows<float>(h, Y_out, h->d, h->Y, h->DP, rows, h->d);
+    if (rc) return rc;
+    FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return FUNCSNE_OK;
+}
+
+int funcsne_get_knn(const funcsne_t* hc, int32_t space, int32_t* idx, float* d2) {
+    funcsne* h = const_cast<funcsne*>(hc);
+    if (!h || !idx) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    DevScalars s;
+    int rc = read_scalars(h, &s);
+    if (rc) return rc;
+    if (space == FUNCSNE_SPACE_HD) {
+        const size_t n = static_cast<size_t>(h->N) * h->k_hd;
+        FSNE_CUDA(h, cudaMemcpyAsync(idx, h->hd_idx[s.hd_cur], n * sizeof(int32_t), cudaMemcpyDefault, h->stream));
+        if (d2) FSNE_CUDA(h, cudaMemcpyAsync(d2, h->hd_d2[s.hd_cur], n * sizeof(float), cudaMemcpyDefault, h->stream));
+    } else if (space == FUNCSNE_SPACE_LD) {
+        const size_t n = static_cast<size_t>(h->N) * h->k_ld;
+        FSNE_CUDA(h, cudaMemcpyAsync(idx, h->ld_idx[s.ld_cur], n * sizeof(int32_t), cudaMemcpyDefault, h->stream));
+        if (d2) {
+            float* tmp = nullptr;
+            FSNE_CUDA(h, dalloc(&tmp, n));
+            cudaError_t e = launch_ld_distances(h->Y, h->ld_idx[s.ld_cur], h->N, h->k_ld, h->DP, tmp, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d2, tmp, n * sizeof(float), cudaMemcpyDefault, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            cudaFree(tmp);
+            FSNE_CUDA(h, e);
+        }
+    } else {
+        return fail(h, FUNCSNE_E_ARG, "space must be FUNCSNE_SPACE_HD or FUNCSNE_SPACE_LD");
+    }
+    FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return FUNCSNE_OK;
+}
+
+int funcsne_get_stats(const funcsne_t* hc, funcsne_stats_t* st) {
+    funcsne* h = const_cast<funcsne*>(hc);
+    if (!h || !st) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    DevScalars s;
+    int rc = read_scalars(h, &s);
+    if (rc) return rc;
+    st->N = h->N;
+    st->t = s.t;
+    st->E = s.E;
+    st->Zhat = s.Zhat;
+    st->last_Z = s.last_Z;
+    st->last_n_new = static_cast<int64_t>(s.last_n_new);
+    st->last_coin = s.last_coin;
+    st->precision = h->precision;
+    st->error_word = s.err;
+    st->cand_scored = static_cast<int64_t>(s.cand_scored);
+    st->cand_reranked = static_cast<int64_t>(s.cand_reranked);
+    return FUNCSNE_OK;
+}
+
+int funcsne_export_state(const funcsne_t* hc, funcsne_state_t* st) {
+    funcsne* h = const_cast<funcsne*>(hc);
+    if (!h || !st) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    DevScalars s;
+    int rc = read_scalars(h, &s);
+    if (rc) return rc;
+    const size_t nh = static_cast<size_t>(h->N) * h->k_hd, nl = static_cast<size_t>(h->N) * h->k_ld;
+    if (st->Y && (rc = copy_rows<float>(h, st->Y, h->d, h->Y, h->DP, h->N, h->d))) return rc;
+    if (st->V && (rc = copy_rows<float>(h, st->V, h->d, h->V, h->DP, h->N, h->d))) return rc;
+    if (st->hd_idx) FSNE_CUDA(h, cudaMemcpyAsync(st->hd_idx, h->hd_idx[s.hd_cur], nh * 4, cudaMemcpyDefault, h->stream));
+    if (st->hd_d2) FSNE_CUDA(h, cudaMemcpyAsync(st->hd_d2, h->hd_d2[s.hd_cur], nh * 4, cudaMemcpyDefault, h->stream));
+    if (st->ld_idx) FSNE_CUDA(h, cudaMemcpyAsync(st->ld_idx, h->ld_idx[s.ld_cur], nl * 4, cudaMemcpyDefault, h->stream));
+    if (st->beta) FSNE_CUDA(h, cudaMemcpyAsync(st->beta, h->beta, static_cast<size_t>(h->N) * 4, cudaMemcpyDefault, h->stream));
+    if (st->P) FSNE_CUDA(h, cudaMemcpyAsync(st->P, h->P, nh * 4, cudaMemcpyDefault, h->stream));
+    FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    st->Zhat = s.Zhat;
+    st->E = s.E;
+    st->t = s.t;
+    return FUNCSNE_OK;
+}
+
+int funcsne_import_state(funcsne_t* h, const funcsne_state_t* st) {
+    if (!h || !st) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    if (!(st->Zhat > 0) || !std::isfinite(st->Zhat) || !(st->E >= 0 && st->E <= 1))
+        return fail(h, FUNCSNE_E_ARG, "Zhat must be > 0 and E in [0, 1]");
+    DevScalars s;
+    int rc = read_scalars(h, &s);
+    if (rc) return rc;
+    const size_t nh = static_cast<size_t>(h->N) * h->k_hd, nl = static_cast<size_t>(h->N) * h->k_ld;
+    if ((rc = clear_error_word(h))) return rc;
+    if (st->hd_idx) {
+        FSNE_CUDA(h, cudaMemcpyAsync(h->hd_idx[s.hd_cur], st->hd_idx, nh * 4, cudaMemcpyDefault, h->stream));
+        FSNE_CUDA(h, launch_check_lists(h->hd_idx[s.hd_cur], h->N, h->k_hd, &h->sc->err, h->stream));
+    }
+    if (st->ld_idx) {
+        FSNE_CUDA(h, cudaMemcpyAsync(h->ld_idx[s.ld_cur], st->ld_idx, nl * 4, cudaMemcpyDefault, h->stream));
+        FSNE_CUDA(h, launch_check_lists(h->ld_idx[s.ld_cur], h->N, h->k_ld, &h->sc->err, h->stream));
+    }
+    if ((rc = check_errors(h))) {
+        clear_error_word(h);
+        return fail(h, FUNCSNE_E_ARG, "imported neighbour lists are invalid (out of range, self or repeated)");
+    }
+    if (st->Y) {
+        FSNE_CUDA(h, cudaMemsetAsync(h->Y, 0, h->yelem * 4, h->stream));
+        if ((rc = copy_rows<float>(h, h->Y, h->DP, st->Y, h->d, h->N, h->d))) return rc;
+    }
+    if (st->V) {
+        FSNE_CUDA(h, cudaMemsetAsync(h->V, 0, h->yelem * 4, h->stream));
+        if ((rc = copy_rows<float>(h, h->V, h->DP, st->V, h->d, h->N, h->d))) return rc;
+    }
+    if (st->beta) FSNE_CUDA(h, cudaMemcpyAsync(h->beta, st->beta, static_cast<size_t>(h->N) * 4, cudaMemcpyDefault, h->stream));
+    float* pin = nullptr;
+    if (st->P) {
+        FSNE_CUDA(h, dalloc(&pin, nh));
+        FSNE_CUDA(h, cudaMemcpyAsync(pin, st->P, nh * 4, cudaMemcpyDefault, h->stream));
+    }
+    if (st->hd_idx || st->P) {
+        FinalizeParams f{};
+        f.N = h->N;
+        f.k_hd = h->k_hd;
+        f.n4 = h->n4;
+        f.xpitch = h->xpitch;
+        f.log_perp = std::log(h->perplexity);
+        f.X32 = h->X32;
+        f.idx = h->hd_idx[s.hd_cur];
+        f.d2 = h->hd_d2[s.hd_cur];
+        f.P = h->P;
+        f.beta = h->beta;
+        f.Pin = pin;
+        cudaError_t e = launch_hd_finalize(f, 8 * h->num_sms, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(pin);
+        FSNE_CUDA(h, e);
+    }
+    FSNE_CUDA(h, cudaMemsetAsync(h->A, 0, h->yelem * 4, h->stream));
+    s.Zhat = st->Zhat;
+    s.E = st->E;
+    s.t = st->t;
+    s.err = 0;
+    s.ticket = 0;
+    s.n_new = 0;
+    FSNE_CUDA(h, cudaMemcpyAsync(h->sc, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+    FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return FUNCSNE_OK;
+}
+
+int funcsne_debug_step(funcsne_t* h, float* att, float* rep) {
+    if (!h || !att || !rep) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    float *da = nullptr, *dr = nullptr;
+    FSNE_CUDA(h, dalloc(&da, h->yelem));
+    cudaError_t e = dalloc(&dr, h->yelem);
+    if (e != cudaSuccess) {
+        cudaFree(da);
+        FSNE_CUDA(h, e);
+    }
+    int rc = enqueue_iteration(h, h->stream, da, dr);
+    if (!rc) rc = copy_rows<float>(h, att, h->d, da, h->DP, h->N, h->d);
+    if (!rc) rc = copy_rows<float>(h, rep, h->d, dr, h->DP, h->N, h->d);
+    e = cudaStreamSynchronize(h->stream);
+    cudaFree(da);
+    cudaFree(dr);
+    if (rc) return rc;
+    FSNE_CUDA(h, e);
+    return check_errors(h);
+}
+
+int funcsne_profile_step(funcsne_t* h, int32_t n_iters, double* ms_step, double* ms_update) {
+    if (!h || !ms_step || !ms_update) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    if (n_iters < 1) return fail(h, FUNCSNE_E_ARG, "n_iters must be >= 1");
+    std::vector<cudaEvent_t> ev(static_cast<size_t>(3 * n_iters), nullptr);
+    for (auto& e : ev) FSNE_CUDA(h, cudaEventCreate(&e));
+    int rc = FUNCSNE_OK;
+    for (int k = 0; k < n_iters && rc == FUNCSNE_OK; ++k) {
+        const StepParams p = step_params(h);
+        cudaError_t e = cudaEventRecord(ev[3 * k], h->stream);
+        if (e == cudaSuccess) e = launch_step_kernel(h, p, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3 * k + 1], h->stream);
+        if (e == cudaSuccess) e = update_launch(update_params(h, nullptr, nullptr), h->update_blocks, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3 * k + 2], h->stream);
+        if (e != cudaSuccess) rc = fail(h, FUNCSNE_E_CUDA, "profile_step: %s", cudaGetErrorString(e));
+    }
+    double a = 0.0, b = 0.0;
+    if (rc == FUNCSNE_OK) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        for (int k = 0; k < n_iters && e == cudaSuccess; ++k) {
+            float x = 0.f, y = 0.f;
+            e = cudaEventElapsedTime(&x, ev[3 * k], ev[3 * k + 1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&y, ev[3 * k + 1], ev[3 * k + 2]);
+            a += x;
+            b += y;
+        }
+        if (e != cudaSuccess) rc = fail(h, FUNCSNE_E_CUDA, "profile_step: %s", cudaGetErrorString(e));
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    *ms_step = a;
+    *ms_update = b;
+    return rc;
+}
+
+int funcsne_exact_knn(const funcsne_t* hc, const int32_t* queries, int64_t n_q, int32_t k, int32_t* idx, float* d2) {
+    funcsne* h = const_cast<funcsne*>(hc);
+    if (!h || !queries || !idx) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    if (k < 1 || k > 64 || k >= h->N) return fail(h, FUNCSNE_E_ARG, "k must be in [1, min(64, N-1)]");
+    if (n_q < 1) return FUNCSNE_OK;
+    std::vector<int32_t> hq(static_cast<size_t>(n_q));
+    FSNE_CUDA(h, cudaMemcpy(hq.data(), queries, static_cast<size_t>(n_q) * 4, cudaMemcpyDefault));
+    for (int32_t q : hq)
+        if (q < 0 || q >= h->N) return fail(h, FUNCSNE_E_ARG, "query index out of range");
+    KnnParams kp{};
+    kp.N = h->N;
+    kp.n4 = h->n4;
+    kp.xpitch = h->xpitch;
+    kp.k = k;
+    kp.RK = k <= 32 ? 1 : 2;
+    kp.n_q = n_q;
+    const int64_t qb = (n_q + 7) / 8;
+    int64_t ns = (8LL * h->num_sms + qb - 1) / qb;
+    if (ns < 1) ns = 1;
+    if (ns > 256) ns = 256;
+    if (ns > h->N / 64 + 1) ns = h->N / 64 + 1;
+    kp.n_split = static_cast<int32_t>(ns);
+    kp.X32 = h->X32;
+    int32_t* dq = nullptr;
+    unsigned long long* part = nullptr;
+    int32_t* didx = nullptr;
+    float* dd2 = nullptr;
+    cudaError_t e = dalloc(&dq, static_cast<size_t>(n_q));
+    if (e == cudaSuccess) e = dalloc(&part, static_cast<size_t>(n_q) * ns * 32 * kp.RK);
+    if (e == cudaSuccess) e = dalloc(&didx, static_cast<size_t>(n_q) * k);
+    if (e == cudaSuccess) e = dalloc(&dd2, static_cast<size_t>(n_q) * k);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dq, hq.data(), static_cast<size_t>(n_q) * 4, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        kp.queries = dq;
+        kp.part = part;
+        kp.idx = didx;
+        kp.d2 = dd2;
+        e = launch_exact_knn(kp, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(idx, didx, static_cast<size_t>(n_q) * k * 4, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess && d2) e = cudaMemcpyAsync(d2, dd2, static_cast<size_t>(n_q) * k * 4, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dq);
+    cudaFree(part);
+    cudaFree(didx);
+    cudaFree(dd2);
+    FSNE_CUDA(h, e);
+    return FUNCSNE_OK;
+}
+
+const char* funcsne_last_error(const funcsne_t* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+void funcsne_destroy(funcsne_t* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

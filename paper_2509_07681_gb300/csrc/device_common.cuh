@@ -1,0 +1,419 @@
+// Device building blocks of the FUnc-SNE iteration on sm_103a: the Philox
+// generator, index mappings, (distance, index) keys, warp-wide bitonic
+// networks, distance kernels for FP32 / BF16 / FP8 rows and the warp
+// bisection of the bandwidth (Eq. 1).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_fp16.h>
+
+#include "params.h"
+
+namespace fsne {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint64_t kSentinel = ~0ull;  // larger than every valid (d2, idx) key
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two 32x32->64-bit
+// multiplies; the 64-bit key is bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint64_t seed) {
+    uint32_t k0 = static_cast<uint32_t>(seed);
+    uint32_t k1 = static_cast<uint32_t>(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t ha = __umulhi(0xD2511F53u, c0), la = 0xD2511F53u * c0;
+        const uint32_t hb = __umulhi(0xCD9E8D57u, c2), lb = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hb ^ c1 ^ k0;
+        const uint32_t n2 = ha ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lb;
+        c2 = n2;
+        c3 = la;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// uniform integer in [0, m): high word of u * m.
+__device__ __forceinline__ uint32_t map_index(uint32_t u, uint32_t m) { return __umulhi(u, m); }
+
+// uniform index in [0, n) without i.
+__device__ __forceinline__ uint32_t map_other(uint32_t u, uint32_t n, uint32_t i) {
+    const uint32_t j = __umulhi(u, n - 1u);
+    return j + (j >= i ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------- keys
+// (d2, idx) packed so that unsigned order equals the lexicographic order
+// (d2 >= 0, so its IEEE bits are monotone).
+__device__ __forceinline__ uint64_t make_key(float d2, uint32_t idx) {
+    return (static_cast<uint64_t>(__float_as_uint(d2)) << 32) | idx;
+}
+__device__ __forceinline__ uint32_t key_idx(uint64_t k) { return static_cast<uint32_t>(k); }
+__device__ __forceinline__ float key_d2(uint64_t k) {
+    return __uint_as_float(static_cast<uint32_t>(k >> 32));
+}
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    const uint32_t lo = __shfl_sync(kFull, static_cast<uint32_t>(v), src);
+    const uint32_t hi = __shfl_sync(kFull, static_cast<uint32_t>(v >> 32), src);
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
+    const uint32_t lo = __shfl_xor_sync(kFull, static_cast<uint32_t>(v), m);
+    const uint32_t hi = __shfl_xor_sync(kFull, static_cast<uint32_t>(v >> 32), m);
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+
+// Element e of a warp-distributed array of 32*R values (lane e%32, register e/32).
+template <int R, typename T>
+__device__ __forceinline__ T warp_get(const T (&v)[R], uint32_t e) {
+    T out = v[0];
+    const int src = static_cast<int>(e & 31u);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const T x = __shfl_sync(kFull, v[r], src);
+        if (static_cast<uint32_t>(r) == (e >> 5)) out = x;
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------- bitonic networks
+// Ascending sort of 32*R keys held as element e = r*32 + lane.
+template <int R>
+__device__ __forceinline__ void cmpx_stage(uint64_t (&k)[R], int lane, int size, int stride) {
+    if (stride >= 32) {
+        const int rs = stride >> 5;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if ((r & rs) == 0) {
+                const int e = r * 32 + lane;
+                const bool asc = (e & size) == 0;
+                const uint64_t a = k[r], b = k[r | rs];
+                const bool sw = asc ? (a > b) : (a < b);
+                k[r] = sw ? b : a;
+                k[r | rs] = sw ? a : b;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = r * 32 + lane;
+            const uint64_t o = shfl_xor64(k[r], stride);
+            const bool asc = (e & size) == 0;
+            const bool lower = (lane & stride) == 0;
+            const uint64_t mn = k[r] < o ? k[r] : o;
+            const uint64_t mx = k[r] < o ? o : k[r];
+            k[r] = (lower == asc) ? mn : mx;
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void warp_sort(uint64_t (&k)[R], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32 * R; size <<= 1)
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) cmpx_stage<R>(k, lane, size, stride);
+}
+
+// Sorts a bitonic sequence of 32*R keys ascending.
+template <int R>
+__device__ __forceinline__ void warp_bitonic_merge(uint64_t (&k)[R], int lane) {
+#pragma unroll
+    for (int stride = 16 * R; stride > 0; stride >>= 1) cmpx_stage<R>(k, lane, 32 * R, stride);
+}
+
+// Top 32*R of (sorted old list, 32 candidates): old[0..32R-33] always stay,
+// the last 32 slots take the 32 smallest of (old tail, candidates).
+template <int R>
+__device__ __forceinline__ void merge_candidates(uint64_t (&old)[R], uint64_t cand, int lane) {
+    uint64_t c[1] = {cand};
+    warp_sort<1>(c, lane);
+    const uint64_t crev = shfl64(c[0], 31 - lane);
+    uint64_t b[1] = {old[R - 1] < crev ? old[R - 1] : crev};
+    warp_bitonic_merge<1>(b, lane);
+    if constexpr (R == 1) {
+        old[0] = b[0];
+    } else {
+        uint64_t m[2] = {old[0], shfl64(b[0], 31 - lane)};
+        warp_bitonic_merge<2>(m, lane);
+        old[0] = m[0];
+        old[1] = m[1];
+    }
+}
+
+// ---------------------------------------------------------------- warp reductions
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+    return v;
+}
+
+// Reduce-scatter: afterwards lane l holds the warp sum of v[l] (31 shuffles).
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool up = (lane & w) != 0;
+#pragma unroll
+        for (int k = 0; k < w; ++k) {
+            const float send = up ? v[k] : v[k + w];
+            const float keep = up ? v[k + w] : v[k];
+            v[k] = keep + __shfl_xor_sync(kFull, send, w);
+        }
+    }
+    return v[0];
+}
+
+// ---------------------------------------------------------------- rows
+template <int DP>
+__device__ __forceinline__ void load_row(const float* __restrict__ src, float (&v)[DP]) {
+    if constexpr (DP % 4 == 0) {
+        const float4* s = reinterpret_cast<const float4*>(src);
+#pragma unroll
+        for (int q = 0; q < DP / 4; ++q) {
+            const float4 a = __ldg(s + q);
+            v[4 * q] = a.x;
+            v[4 * q + 1] = a.y;
+            v[4 * q + 2] = a.z;
+            v[4 * q + 3] = a.w;
+        }
+    } else {
+        const float2* s = reinterpret_cast<const float2*>(src);
+#pragma unroll
+        for (int q = 0; q < DP / 2; ++q) {
+            const float2 a = __ldg(s + q);
+            v[2 * q] = a.x;
+            v[2 * q + 1] = a.y;
+        }
+    }
+}
+
+template <int DP>
+__device__ __forceinline__ float sqdist_ld(const float (&a)[DP], const float (&b)[DP]) {
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < DP; ++c) {
+        const float d = __fsub_rn(a[c], b[c]);
+        acc = __fmaf_rn(d, d, acc);
+    }
+    return acc;
+}
+
+// Vector atomic add of DP floats (DP = 2, 4, 8, 16, 32; rows 8-byte aligned
+// for DP = 2 and 16-byte aligned otherwise).
+template <int DP>
+__device__ __forceinline__ void atomic_add_row(float* dst, const float (&v)[DP], float scale) {
+    if constexpr (DP == 2) {
+        atomicAdd(reinterpret_cast<float2*>(dst), make_float2(scale * v[0], scale * v[1]));
+    } else {
+#pragma unroll
+        for (int q = 0; q < DP / 4; ++q)
+            atomicAdd(reinterpret_cast<float4*>(dst) + q,
+                      make_float4(scale * v[4 * q], scale * v[4 * q + 1], scale * v[4 * q + 2],
+                                  scale * v[4 * q + 3]));
+    }
+}
+
+// ---------------------------------------------------------------- HD distances
+// Exact FP32 squared distance, one lane per candidate, features in order
+// f = 0..D-1 (zero padding adds nothing). xs: the own row in shared memory.
+__device__ __forceinline__ float dist_f32(const float* __restrict__ xs,
+                                          const float* __restrict__ xc, int n4) {
+    const float4* a = reinterpret_cast<const float4*>(xs);
+    const float4* b = reinterpret_cast<const float4*>(xc);
+    float acc = 0.f;
+#pragma unroll 4
+    for (int q = 0; q < n4; ++q) {
+        const float4 u = a[q];
+        const float4 v = __ldg(b + q);
+        float d = __fsub_rn(u.x, v.x);
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(u.y, v.y);
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(u.z, v.z);
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(u.w, v.w);
+        acc = __fmaf_rn(d, d, acc);
+    }
+    return acc;
+}
+
+struct ApproxDist {
+    float d2;    // FP32 distance to the dequantised row
+    float band;  // bound on |d2 - exact FP32 distance to the master row|
+};
+
+// Error term of one dequantised coordinate: |x - x~| <= u |x~| + a.
+// Accumulates s1 = sum |x_i - x~| e and s2 = sum e^2; the distance error is
+// at most 2 s1 + 3 s2 (expand (D - e)^2 - D^2 with |e| bounded).
+__device__ __forceinline__ void approx_acc(float xi, float xq, float u, float a, float& acc,
+                                           float& s1, float& s2) {
+    const float d = __fsub_rn(xi, xq);
+    acc = __fmaf_rn(d, d, acc);
+    const float e = __fmaf_rn(u, fabsf(xq), a);
+    s1 = __fmaf_rn(fabsf(d), e, s1);
+    s2 = __fmaf_rn(e, e, s2);
+}
+
+__device__ __forceinline__ ApproxDist finish_band(float acc, float s1, float s2, float gamma) {
+    // FP32 rounding of the three sums and of both distance evaluations.
+    const float b = (2.f * s1 + 3.f * s2) * (1.f + 2.f * gamma);
+    ApproxDist r;
+    r.d2 = acc;
+    r.band = b + gamma * (2.f * acc + b) * (1.f + 4.f * gamma) + 1e-30f;
+    return r;
+}
+
+// BF16 rows: 8 values per 16-byte chunk.
+__device__ __forceinline__ ApproxDist dist_bf16(const float* __restrict__ xs,
+                                                const uint16_t* __restrict__ xc, int n8, float u,
+                                                float gamma) {
+    const uint4* b = reinterpret_cast<const uint4*>(xc);
+    float acc = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll 2
+    for (int q = 0; q < n8; ++q) {
+        const uint4 raw = __ldg(b + q);
+        const float4 x0 = reinterpret_cast<const float4*>(xs)[2 * q];
+        const float4 x1 = reinterpret_cast<const float4*>(xs)[2 * q + 1];
+        approx_acc(x0.x, __uint_as_float(raw.x << 16), u, 0.f, acc, s1, s2);
+        approx_acc(x0.y, __uint_as_float(raw.x & 0xffff0000u), u, 0.f, acc, s1, s2);
+        approx_acc(x0.z, __uint_as_float(raw.y << 16), u, 0.f, acc, s1, s2);
+        approx_acc(x0.w, __uint_as_float(raw.y & 0xffff0000u), u, 0.f, acc, s1, s2);
+        approx_acc(x1.x, __uint_as_float(raw.z << 16), u, 0.f, acc, s1, s2);
+        approx_acc(x1.y, __uint_as_float(raw.z & 0xffff0000u), u, 0.f, acc, s1, s2);
+        approx_acc(x1.z, __uint_as_float(raw.w << 16), u, 0.f, acc, s1, s2);
+        approx_acc(x1.w, __uint_as_float(raw.w & 0xffff0000u), u, 0.f, acc, s1, s2);
+    }
+    return finish_band(acc, s1, s2, gamma);
+}
+
+// FP8-E4M3 rows with a per-row FP32 scale stored after the codes:
+// 16 codes per 16-byte chunk, x~ = code * scale.
+__device__ __forceinline__ void fp8x4_to_float(uint32_t w, float s, float (&o)[4]) {
+    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w & 0xffffu), __NV_E4M3);
+    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w >> 16), __NV_E4M3);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+    o[0] = a.x * s;
+    o[1] = a.y * s;
+    o[2] = b.x * s;
+    o[3] = b.y * s;
+}
+
+__device__ __forceinline__ ApproxDist dist_fp8(const float* __restrict__ xs,
+                                               const uint8_t* __restrict__ xc, int nw,
+                                               int scale_off, float u, float a_rel, float gamma) {
+    // nw = ceil(D / 4) code words; the row's last 4 bytes hold the scale.
+    const float s = __ldg(reinterpret_cast<const float*>(xc + scale_off));
+    const float a = a_rel * s;
+    const uint4* b = reinterpret_cast<const uint4*>(xc);
+    float acc = 0.f, s1 = 0.f, s2 = 0.f;
+    const int nq = (nw + 3) >> 2;
+    for (int q = 0; q < nq; ++q) {
+        const uint4 raw = __ldg(b + q);
+        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            if (4 * q + m < nw) {
+                float v[4];
+                fp8x4_to_float(w4[m], s, v);
+                const float4 xi = reinterpret_cast<const float4*>(xs)[4 * q + m];
+                approx_acc(xi.x, v[0], u, a, acc, s1, s2);
+                approx_acc(xi.y, v[1], u, a, acc, s1, s2);
+                approx_acc(xi.z, v[2], u, a, acc, s1, s2);
+                approx_acc(xi.w, v[3], u, a, acc, s1, s2);
+            }
+        }
+    }
+    return finish_band(acc, s1, s2, gamma);
+}
+
+// ---------------------------------------------------------------- bisection (Eq. 1)
+// Warp-wide calibration of beta = 1/(2 sigma^2) for a sorted list of k
+// squared distances held as element e = r*32 + lane. Entropy
+// H = ln S + beta T / S with S = sum exp(-beta (d - d0)), T = sum exp(.)(d - d0).
+// Start from beta0 (> 0: warm restart) or 1/mean(d - d0); double while H is
+// above the target, then bisect until |H - ln perp| < tol.
+template <int R>
+__device__ __forceinline__ float warp_bisect(const float (&d2)[R], int k, float log_perp,
+                                             float beta0, float (&p)[R], int lane) {
+    const float d0 = __shfl_sync(kFull, d2[0], 0);
+    float sh[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) sh[r] = (r * 32 + lane < k) ? (d2[r] - d0) : 0.f;
+    const float inv_k = 1.f / static_cast<float>(k);
+    if (logf(static_cast<float>(k)) <= log_perp) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[r] = (r * 32 + lane < k) ? inv_k : 0.f;
+        return 0.f;
+    }
+    float beta = beta0;
+    if (!(beta > 0.f)) {
+        float m = 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) m += sh[r];
+        m = warp_sum(m) * inv_k;
+        beta = m > 0.f ? 1.f / m : 1.f;
+    }
+    float lo = 0.f, hi = INFINITY;
+    for (int it = 0; it < kBisectMaxIt; ++it) {
+        float S = 0.f, T = 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r * 32 + lane < k) {
+                const float e = expf(-beta * sh[r]);
+                S += e;
+                T = __fmaf_rn(e, sh[r], T);
+            }
+        }
+        S = warp_sum(S);
+        T = warp_sum(T);
+        const float H = logf(S) + beta * T / S;
+        if (fabsf(H - log_perp) < kBisectTol) break;
+        if (H > log_perp) {
+            lo = beta;
+            beta = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
+        } else {
+            hi = beta;
+            beta = 0.5f * (lo + hi);
+        }
+    }
+    float S = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        p[r] = (r * 32 + lane < k) ? expf(-beta * sh[r]) : 0.f;
+        S += p[r];
+    }
+    S = warp_sum(S);
+    const float invS = 1.f / S;
+#pragma unroll
+    for (int r = 0; r < R; ++r) p[r] *= invS;
+    return beta;
+}
+
+// Coin of iteration t: HD refinement iff u < 0.05 + 0.95 E (FP64, explicit
+// rounding so host and device agree bit for bit).
+__device__ __forceinline__ bool hd_coin(uint32_t t, double E, uint64_t seed, int mode) {
+    if (mode == kHdAlways) return true;
+    if (mode == kHdNever) return false;
+    const uint4 w = philox(t, 0u, kStreamCoin, 0u, seed);
+    const double p = __dadd_rn(0.05, __dmul_rn(0.95, E));
+    const double u = __dmul_rn(static_cast<double>(w.x), 2.3283064365386962890625e-10);
+    return u < p;
+}
+
+}  // namespace fsne

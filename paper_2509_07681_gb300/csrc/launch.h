@@ -1,0 +1,72 @@
+// Host-side launchers of the FUnc-SNE kernels (one declaration per kernel
+// family; definitions live next to the kernels).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "params.h"
+
+namespace fsne {
+
+struct FinalizeParams {
+    int64_t N;
+    int32_t k_hd, n4, xpitch;
+    float log_perp;
+    const float* X32;
+    int32_t* idx;     // N x k_hd, sorted in place
+    float* d2;        // N x k_hd out
+    float* P;         // N x k_hd out
+    float* beta;      // N out (cold start only)
+    const float* Pin; // imported P (aligned with idx before sorting) or NULL
+};
+
+struct ZinitParams {
+    int64_t N;
+    int32_t k_hd, k_ld, n_neg;
+    float alpha, inv_alpha, neg_scale;
+    uint32_t t, stream;
+    uint64_t seed;
+    const float* Y;
+    const int32_t* hd_idx;
+    const int32_t* ld_idx;
+    double* part;
+};
+
+struct KnnParams {
+    int64_t N;
+    int32_t n4, xpitch, k, n_split, RK;
+    int64_t n_q;
+    const float* X32;
+    const int32_t* queries;
+    unsigned long long* part;  // n_q x n_split x (32*RK) keys
+    int32_t* idx;              // n_q x k
+    float* d2;                 // n_q x k
+};
+
+// step kernels, one translation unit per HD storage precision
+cudaError_t step_launch_f32(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
+cudaError_t step_launch_bf16(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
+cudaError_t step_launch_fp8(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
+int step_occupancy_f32(int DP, int RH, size_t smem);
+int step_occupancy_bf16(int DP, int RH, size_t smem);
+int step_occupancy_fp8(int DP, int RH, size_t smem);
+cudaError_t update_launch(const UpdateParams& u, int blocks, cudaStream_t s);
+
+// set-up
+cudaError_t launch_init_lists(int64_t N, int k, uint32_t stream, uint64_t seed, int32_t* out, cudaStream_t s);
+cudaError_t launch_hd_finalize(const FinalizeParams& f, int blocks, cudaStream_t s);
+cudaError_t launch_init_y(const float* X32, int64_t N, int D, int xpitch, int d, int DP, uint64_t seed,
+                          float* Y, double* scratch, int64_t scratch_len, cudaStream_t s);
+cudaError_t launch_zinit(const ZinitParams& z, int DP, int blocks, DevScalars* sc, cudaStream_t s);
+cudaError_t launch_quantize(const float* X32, int64_t N, int D, int xpitch, int precision, int qpitch,
+                            int scale_off, uint8_t* Q, cudaStream_t s);
+cudaError_t launch_check_lists(const int32_t* idx, int64_t N, int k, uint32_t* err, cudaStream_t s);
+cudaError_t launch_check_finite(const float* X, int64_t n, uint32_t* err, cudaStream_t s);
+cudaError_t launch_ld_distances(const float* Y, const int32_t* idx, int64_t N, int k, int DP, float* d2,
+                                cudaStream_t s);
+
+// evaluation
+cudaError_t launch_exact_knn(const KnnParams& kp, cudaStream_t s);
+
+}  // namespace fsne

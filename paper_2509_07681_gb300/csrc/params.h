@@ -1,0 +1,112 @@
+// Constants, device-resident scalars and kernel parameter blocks of the
+// FUnc-SNE iteration. Shared by the host runtime and the kernels.
+#pragma once
+
+#include <cstdint>
+
+namespace fsne {
+
+// Random-stream identifiers: every draw uses the Philox counter
+// (iteration, point, stream, slot) under the 64-bit seed.
+constexpr uint32_t kStreamCoin = 0;
+constexpr uint32_t kStreamHd = 1;
+constexpr uint32_t kStreamLd = 2;
+constexpr uint32_t kStreamNeg = 3;
+constexpr uint32_t kStreamMlp = 4;
+constexpr uint32_t kStreamInsert = 5;
+constexpr uint32_t kStreamInitHd = 6;
+constexpr uint32_t kStreamInitLd = 7;
+constexpr uint32_t kStreamInitY = 8;
+constexpr uint32_t kStreamZinit = 9;
+
+// Candidate layout (32 per point and refinement; the paper names the
+// sources but not their counts).
+//   HD: slots 0-15 HD neighbour of an HD neighbour, 16-19 LD neighbour,
+//       20-23 LD neighbour of an LD neighbour, 24-31 uniform random point.
+//   LD: slots 0-15 LD neighbour of an LD neighbour, 16-23 HD neighbour,
+//       24-31 uniform random point.
+constexpr int kCand = 32;
+constexpr int kHdNnEnd = 16, kHdLdNbEnd = 20, kHdLdNnEnd = 24;
+constexpr int kLdNnEnd = 16, kLdHdNbEnd = 24;
+
+constexpr double kGammaE = 0.1;  // smoothing of E[N_new / N]
+constexpr double kGammaZ = 0.1;  // smoothing of the normalisation estimate
+constexpr double kInitYStd = 1e-4;
+
+constexpr float kBisectTol = 1e-5f;  // |H - ln perp| in FP32
+constexpr int kBisectMaxIt = 64;
+
+constexpr int kHdAdaptive = 0, kHdAlways = 1, kHdNever = 2;
+
+// Device-resident scalars of the method (one per handle).
+struct DevScalars {
+    double E;            // smoothed fraction of points with new HD neighbours
+    double Zhat;         // running estimate of sum_{k != l} w_kl
+    double last_Z;       // Z_t of the last step
+    uint32_t t;          // iteration counter
+    int32_t hd_cur;      // current HD list buffer (0 / 1)
+    int32_t ld_cur;      // current LD list buffer (0 / 1)
+    int32_t last_coin;
+    unsigned long long n_new;       // points flagged in the running step
+    unsigned long long last_n_new;
+    unsigned long long cand_scored;
+    unsigned long long cand_reranked;
+    uint32_t err;        // error bits
+    uint32_t ticket;     // last-block detection of the update kernel
+};
+
+constexpr uint32_t kErrNonFinite = 1u;
+constexpr uint32_t kErrIndex = 2u;
+
+struct StepParams {
+    int64_t N;
+    int32_t k_hd, k_ld, n_neg;
+    int32_t n4;          // float4 chunks per FP32 row
+    int32_t xpitch;      // floats per FP32 row
+    int32_t nq;          // BF16: 16-byte chunks per row; FP8: 4-byte code words per row
+    int32_t qpitch;      // bytes per quantised row
+    int32_t qscale_off;  // byte offset of the FP8 row scale
+    int32_t hd_mode;
+    int32_t smem_per_warp;  // bytes
+    int32_t xs_floats;      // own-row floats staged per warp
+    float alpha, inv_alpha, inv2N, neg_scale, log_perp;
+    float q_u, q_a, q_gamma;  // dequantisation error model (see dist_bf16 / dist_fp8)
+    uint64_t seed;
+    const float* X32;
+    const uint8_t* Xq;
+    float* Y;
+    float* A;
+    float* R;
+    int32_t* hd_idx0;
+    int32_t* hd_idx1;
+    float* hd_d20;
+    float* hd_d21;
+    int32_t* ld_idx0;
+    int32_t* ld_idx1;
+    float* P;
+    float* beta;
+    DevScalars* sc;
+    double* zpart;               // one FP64 partial of Z_t per block
+    unsigned long long* cnt;     // per-block counters: n_new, scored, reranked
+};
+
+struct UpdateParams {
+    int64_t n_elem;       // N * DP
+    int32_t n_zpart;      // blocks of the step kernel
+    int32_t hd_mode;
+    int64_t N;
+    float lr, momentum, att, rep, exaggeration;
+    int32_t exag_iters;
+    uint64_t seed;
+    float* Y;
+    float* V;
+    float* A;
+    float* R;
+    float* dbg_att;       // optional copies of the forces (NULL = none)
+    float* dbg_rep;
+    DevScalars* sc;
+    const double* zpart;
+    unsigned long long* cnt;
+};
+
+}  // namespace fsne

@@ -1,0 +1,216 @@
+"""GPU parity of the fused FUnc-SNE iteration against the FP64 oracle,
+through the C ABI. One iteration from the same state and Philox streams:
+neighbour index sets bit-exact (FP32/FP64 near-ties at the list boundary
+are reported, never silently accepted beyond a handful), forces within
+1e-4 relative per point, bandwidths within the bisection tolerance."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_07681_gb300 import funcsne as F
+from paper_2509_07681_gb300 import synth
+from paper_2509_07681_gb300.quality import recall, rnx_auc
+
+from gpu_util import compare_sets, fp32_band, lib, oracle_from_state, rel_err_rows
+
+pytestmark = pytest.mark.gpu
+
+FORCE_RTOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lib()
+
+
+CASES = {
+    # blobs workload: N=2000, D=50, d=2, k_hd=32, k_ld=16, n_neg=16, alpha=1
+    "blobs-2k": (lambda: synth.blobs(n=2000, dim=50),
+                 dict(d=2, k_hd=32, k_ld=16, n_neg=16, alpha=1.0, perplexity=30.0)),
+    # ragged: N not a multiple of the warps per block, D not a multiple of 4,
+    # d padded 3 -> 4, n_neg > 32, heavy tails
+    "ragged": (lambda: synth.blobs(n=997, dim=7, n_clusters=4, seed=3),
+               dict(d=3, k_hd=20, k_ld=10, n_neg=40, alpha=0.5, perplexity=12.0)),
+    # two registers per lane for the HD list (k_hd = 64), d = 32, light tails
+    "k64-d32": (lambda: synth.lowrank(n=1500, dim=33, latent=8, n_comp=10, seed=4),
+                dict(d=32, k_hd=64, k_ld=32, n_neg=32, alpha=0.7, perplexity=50.0)),
+    # the 1M-point workload's shape at small N: d=16, k 32/32, n_neg 32
+    "spectrum-shape": (lambda: synth.spectrum(n=3000, dim=50, n_clusters=12, seed=5),
+                       dict(d=16, k_hd=32, k_ld=32, n_neg=32, alpha=1.0, perplexity=30.0)),
+    # dynamic-dataset shape: D=128, d=8
+    "swissroll-shape": (lambda: synth.swissroll(n=2500, dim=128, seed=6),
+                        dict(d=8, k_hd=32, k_ld=16, n_neg=16, alpha=100.0, perplexity=30.0)),
+}
+
+
+def _make(X, params, seed=0, **opts):
+    m = F.FuncSNE(X, params["d"], params["k_hd"], params["k_ld"], params["n_neg"], params["alpha"],
+                  params["perplexity"], seed=seed)
+    for k, v in opts.items():
+        m.set_option(k, v)
+    return m
+
+
+def test_initial_state_matches_oracle():
+    X = synth.blobs(n=2000, dim=50)
+    p = CASES["blobs-2k"][1]
+    with _make(X, p) as m:
+        st = m.export_state()
+    o = O.OracleState(X, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0)
+    # initial lists are integer draws from Philox: identical element by element
+    np.testing.assert_array_equal(np.sort(st["hd_idx"], 1), np.sort(o.hd_idx, 1))
+    np.testing.assert_array_equal(st["ld_idx"], o.ld_idx)
+    assert np.max(rel_err_rows(st["Y"].astype(np.float64), o.Y)) < 1e-5
+    np.testing.assert_allclose(st["beta"], o.beta, rtol=2e-3)
+    assert abs(st["Zhat"] - o.Zhat) <= 1e-5 * o.Zhat
+    assert st["E"] == 1.0 and st["t"] == 0
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_one_iteration_matches_oracle(case):
+    gen, p = CASES[case]
+    X = gen()
+    N, D = X.shape
+    m = _make(X, p, hd_mode=1)
+    m.step(4)
+    m.sync()
+    st = m.export_state()
+    o = oracle_from_state(X, st, p, hd_mode=1)
+    att, rep = m.debug_step()
+    st1 = m.export_state()
+    s1 = m.stats()
+    out = o.step()
+    X64 = X.astype(np.float64)
+    band = fp32_band(D)
+    bad, amb = compare_sets(st1["hd_idx"], o.hd_idx, range(N), X64, band)
+    assert bad == 0, f"{bad} HD sets differ beyond FP32 near-ties"
+    assert amb <= max(2, N // 500)
+    badl, ambl = compare_sets(st1["ld_idx"], o.ld_idx, range(N), st["Y"].astype(np.float64), band)
+    assert badl == 0, f"{badl} LD sets differ beyond FP32 near-ties"
+    assert ambl <= max(2, N // 500)
+    # flags and the smoothed fraction
+    assert s1["last_coin"] == 1 and out["coin"]
+    if amb == 0:
+        assert s1["last_n_new"] == out["n_new"]
+        assert st1["E"] == o.E  # same FP64 expression on both sides
+    # bandwidths of flagged points within the bisection tolerance
+    fl = out["flags"].astype(bool)
+    if fl.any():
+        np.testing.assert_allclose(st1["beta"][fl], o.beta[fl], rtol=5e-3)
+    # forces: only rows whose sets agree are comparable element by element
+    same = np.array([set(a.tolist()) == set(b.tolist()) for a, b in zip(st1["hd_idx"], o.hd_idx)]) & \
+        np.array([set(a.tolist()) == set(b.tolist()) for a, b in zip(st1["ld_idx"], o.ld_idx)])
+    if same.all():
+        ea = rel_err_rows(att.astype(np.float64), out["A"])
+        er = rel_err_rows(rep.astype(np.float64), out["R"])
+        assert np.quantile(ea, 0.999) < FORCE_RTOL and ea.max() < 10 * FORCE_RTOL, ea.max()
+        assert er.max() < FORCE_RTOL, er.max()
+        assert abs(s1["last_Z"] - out["z"].sum()) <= 1e-5 * out["z"].sum()
+        # the update: V_{t+1} = momentum V_t - lr g
+        lr = m.get_option("lr")
+        scale = lr * (np.linalg.norm(out["A"], axis=1) + np.linalg.norm(out["R"], axis=1)) + \
+            1e-6 * np.linalg.norm(o.V, axis=1)
+        dv = np.linalg.norm(st1["V"] - o.V, axis=1)
+        assert np.all(dv <= 1e-3 * scale + 1e-12)
+    m.close()
+
+
+@pytest.mark.parametrize("precision", [F.BF16, F.FP8])
+def test_reduced_precision_sets_equal_fp32(precision):
+    """BF16 / FP8 rows with the exact FP32 re-rank give the FP32 path's sets."""
+    X = synth.spectrum(n=4000, dim=50, n_clusters=12, seed=7)
+    p = CASES["spectrum-shape"][1]
+    m = _make(X, p, hd_mode=1)
+    m.step(3)
+    st = m.export_state()
+    m.step(1)
+    ref = m.export_state()
+    m.import_state(st)
+    m.set_option("precision", precision)
+    m.step(1)
+    got = m.export_state()
+    s = m.stats()
+    np.testing.assert_array_equal(got["hd_idx"], ref["hd_idx"])
+    np.testing.assert_array_equal(got["hd_d2"], ref["hd_d2"])
+    np.testing.assert_array_equal(got["ld_idx"], ref["ld_idx"])
+    assert s["cand_scored"] > 0 and s["cand_reranked"] <= s["cand_scored"]
+    m.close()
+
+
+def test_integer_ties_are_broken_by_index():
+    """Small-integer data: FP32 and FP64 distances are exact, ties are exact,
+    and both sides must order them by index: bit-exact lists, no ambiguity."""
+    X = synth.integer_grid(1200, 6, high=3, seed=8)
+    p = dict(d=2, k_hd=24, k_ld=12, n_neg=16, alpha=1.0, perplexity=10.0)
+    m = _make(X, p, hd_mode=1)
+    m.step(2)
+    st = m.export_state()
+    o = oracle_from_state(X, st, p, hd_mode=1)
+    m.debug_step()
+    st1 = m.export_state()
+    o.step()
+    np.testing.assert_array_equal(st1["hd_idx"], o.hd_idx)
+    np.testing.assert_array_equal(st1["hd_d2"], o.hd_d2.astype(np.float32))
+    m.close()
+
+
+def test_no_hd_refinement_keeps_lists_and_p():
+    X = synth.blobs(n=1000, dim=20, seed=9)
+    p = dict(d=2, k_hd=16, k_ld=8, n_neg=8, alpha=1.0, perplexity=8.0)
+    m = _make(X, p, hd_mode=2)
+    st = m.export_state()
+    m.step(3)
+    st1 = m.export_state()
+    np.testing.assert_array_equal(st1["hd_idx"], st["hd_idx"])
+    np.testing.assert_array_equal(st1["P"], st["P"])
+    assert st1["E"] == st["E"] and st1["t"] == 3
+    m.close()
+
+
+def test_adaptive_coin_and_smoothing_match_oracle():
+    X = synth.blobs(n=1500, dim=30, seed=10)
+    p = dict(d=2, k_hd=16, k_ld=8, n_neg=8, alpha=1.0, perplexity=8.0)
+    m = _make(X, p)
+    m.step(40)
+    for _ in range(5):
+        st = m.export_state()
+        o = oracle_from_state(X, st, p)
+        m.step(1)
+        s = m.stats()
+        out = o.step()
+        assert s["last_coin"] == int(out["coin"])
+        if s["last_n_new"] == out["n_new"]:
+            assert m.export_state()["E"] == o.E
+    m.close()
+
+
+def test_exact_knn_matches_bruteforce():
+    X = synth.spectrum(n=5000, dim=50, n_clusters=8, seed=11)
+    with _make(X, CASES["spectrum-shape"][1]) as m:
+        q = np.arange(0, 5000, 37)
+        idx, d2 = m.exact_knn(q, 40)
+    ref, rd = O.query_knn(X, q, 40)
+    bad, amb = compare_sets(idx, ref, range(len(q)), X.astype(np.float64), fp32_band(50))
+    assert bad == 0 and amb <= 1
+
+
+def test_whole_run_blobs_recall_and_structure():
+    """500 iterations of the blobs workload: the HD lists converge to the exact
+    KNN and the embedding keeps the clusters (statistics, not bit parity)."""
+    X = synth.blobs(n=2000, dim=50)
+    p = CASES["blobs-2k"][1]
+    with _make(X, p) as m:
+        m.step(500)
+        m.sync()
+        hd = m.knn(F.SPACE_HD, with_d2=False)
+        Y = m.embedding()
+        s = m.stats()
+    exact, _ = O.bruteforce_knn(X, 128)
+    assert recall(hd, exact[:, :32]) > 0.99
+    ld, _ = O.bruteforce_knn(Y, 128)
+    from paper_2509_07681_gb300.quality import rnx_curve
+    r = rnx_curve(ld, exact, len(X))
+    assert r[99] > 0.5
+    assert math.isfinite(s["Zhat"]) and s["error_word"] == 0
