@@ -195,6 +195,39 @@ int funcsne_profile_step(funcsne_t *h, int32_t n_iters, double *ms_step_kernel,
 int funcsne_exact_knn(const funcsne_t *h, const int32_t *queries, int64_t n_q, int32_t k,
                       int32_t *idx, float *d2);
 
+/*
+ * funcsne_exact_knn_noalloc -- the brute-force exact KNN of funcsne_exact_knn
+ * for callers that cannot allocate device memory at the time of the call
+ * (for example code running under another framework's caching allocator,
+ * or a latency-critical path that must not incur the implicit
+ * synchronisation of cudaMalloc). The paper has no counterpart; this is a
+ * deployment convenience of this library. It allocates nothing: the
+ * kernels' scratch (query indices and partial top-k lists) lives in a 4 MiB
+ * file-scope device array that every GPU loading the library keeps until
+ * the process exits. No handle is needed.
+ *   X        device pointer, N rows of D FP32 features with row pitch ldx
+ *            floats (ldx % 4 == 0, ldx >= D rounded up to 4, ldx <= 4096),
+ *            16-byte aligned; columns D .. ceil(D/4)*4 - 1 must be zero.
+ *   queries  HOST array of n_q point indices in [0, N) (read before return).
+ *   k        neighbours per query, 1 <= k <= min(64, N - 1).
+ *   idx, d2  DEVICE outputs, n_q x k int32 and FP32 (d2 may be NULL); ordered
+ *            by (d2, index), the query point itself excluded.
+ *   stream   cudaStream_t to run on (NULL = legacy default stream); the
+ *            call is asynchronous on it.
+ * Limits: the scratch holds n_q x (4 + 256 x ceil(k/32)) bytes plus
+ * alignment, so n_q is at most about 16,000 for k <= 32 and about 8,000 for
+ * k <= 64; larger n_q returns FUNCSNE_E_ARG (split the queries).
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (other streams
+ * or other host threads) race on it and must be serialised by the caller.
+ * Errors: FUNCSNE_E_ARG (message via funcsne_last_error(NULL)),
+ * FUNCSNE_E_CUDA.
+ */
+int funcsne_exact_knn_noalloc(const float *X, int64_t N, int32_t D, int32_t ldx,
+                              const int32_t *queries, int64_t n_q, int32_t k, int32_t *idx,
+                              float *d2, void *stream);
+
 /* Message for the last error on this handle (or the last create failure
  * when h is NULL). Valid until the next call on the handle. */
 const char *funcsne_last_error(const funcsne_t *h);

@@ -324,6 +324,11 @@ ZinitParams zinit_params(const funcsne* h, const int32_t* hd, const int32_t* ld,
 
 }  // namespace
 
+namespace fsne {
+// Message for funcsne_last_error(NULL) from entry points that have no handle.
+void set_global_error(const char* msg) { g_create_error = msg; }
+}  // namespace fsne
+
 extern "C" {
 
 int funcsne_create(const float* X, int64_t N, int32_t D, int32_t d, int32_t k_hd, int32_t k_ld, int32_t n_neg,

@@ -65,6 +65,8 @@ ABI_FUNCTIONS = {
     "funcsne_debug_step": (C.c_int, [_h, _vp, _vp]),
     "funcsne_profile_step": (C.c_int, [_h, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "funcsne_exact_knn": (C.c_int, [_h, _vp, C.c_int64, C.c_int32, _vp, _vp]),
+    "funcsne_exact_knn_noalloc": (C.c_int, [_vp, C.c_int64, C.c_int32, C.c_int32, _vp, C.c_int64, C.c_int32,
+                                            _vp, _vp, _vp]),
     "funcsne_last_error": (C.c_char_p, [_h]),
     "funcsne_destroy": (None, [_h]),
 }
@@ -212,6 +214,16 @@ def funcsne_exact_knn(h, queries, k, idx, d2=None):
     pi, k1 = _ptr(idx)
     pd, k2 = _ptr(d2)
     _check(load().funcsne_exact_knn(h, pq, len(queries), k, pi, pd), h)
+    return idx, d2
+
+
+def funcsne_exact_knn_noalloc(X, N, D, ldx, queries, k, idx, d2=None, stream=None):
+    """X, idx, d2: device arrays; queries: host int32 array. No device allocation."""
+    px, k0 = _ptr(X)
+    q = np.ascontiguousarray(queries, dtype=np.int32)
+    pi, k1 = _ptr(idx)
+    pd, k2 = _ptr(d2)
+    _check(load().funcsne_exact_knn_noalloc(px, N, D, ldx, q.ctypes.data, len(q), k, pi, pd, stream), None)
     return idx, d2
 
 
