@@ -338,6 +338,28 @@ def run_reference(args, rank, world):
     return line
 
 
+def run_profile_case(args):
+    """A short, fixed sequence of launches for ncu: create the workload at N
+    (default 1M), then for each precision `warmup` + `steps` iterations with
+    HD refinement every iteration. Prints one line per precision."""
+    from paper_2509_07681_gb300 import funcsne as F
+    from paper_2509_07681_gb300 import synth
+    from paper_2509_07681_gb300.build import build
+
+    build()
+    X, p = synth.make(WORKLOAD, n=args.n)
+    m = F.FuncSNE(X, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0)
+    m.set_option("hd_mode", 1)
+    for name in args.precisions.split(","):
+        m.set_option("precision", {"fp32": F.FP32, "bf16": F.BF16, "fp8": F.FP8}[name])
+        m.profile_step(args.warmup)
+        a, b = m.profile_step(args.steps)
+        m.sync()
+        print(f"{name}: N={X.shape[0]} step_kernel {a / args.steps:.4f} ms update {b / args.steps:.4f} ms",
+              flush=True)
+    m.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,7 +368,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=None, help="override N (default: the workload's 1,000,000)")
     ap.add_argument("--cpu-sample", type=int, default=20000, help="points in the CPU oracle sample")
+    ap.add_argument("--mode", choices=["bench", "ncu"], default="bench",
+                    help="ncu: the short fixed launch sequence used for profiling")
+    ap.add_argument("--precisions", default="fp32,bf16,fp8", help="precisions of --mode ncu")
     args = ap.parse_args()
+    if args.mode == "ncu":
+        run_profile_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     rank = _env_int("RANK", 0)

@@ -71,8 +71,7 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
  * (iteration, point, purpose, slot), key = the 64-bit seed). */
 enum {
     STREAM_COIN = 0,
-    STREAM_HD = 1,
-    STREAM_LD = 2,
+    STREAM_REFINE = 1, /* words 0-1: HD candidate of the slot, words 2-3: LD candidate */
     STREAM_NEG = 3,
     STREAM_MLP = 4,
     STREAM_INSERT = 5,
@@ -95,6 +94,9 @@ enum {
 #define GAMMA_E 0.1            /* smoothing of E[N_new/N]                   */
 #define GAMMA_Z 0.1            /* smoothing of the normalisation estimate   */
 #define INIT_Y_STD 1e-4        /* per-dimension std of the initial layout   */
+#define INSERT_ROUNDS 4        /* neighbour-of-neighbour rounds per insertion */
+#define INSERT_SLOTS_NN 24     /* insertion slots 0..23: neighbour of neighbour */
+                               /* insertion slots 24..31: random existing point */
 
 static void draw4(uint64_t seed, uint32_t t, uint32_t i, uint32_t stream, uint32_t slot,
                   uint32_t out[4])
@@ -219,7 +221,7 @@ int oracle_topk_merge(int64_t i, int k, const int32_t *old_idx, const double *ol
 /*
  * HD candidates of point i at iteration t (Section 3: neighbours of
  * neighbours, with the LD sets proposing candidates for the HD set).
- * Slot s uses Philox counter (t, i, HD, s):
+ * Slot s uses words w0, w1 of the Philox block at counter (t, i, REFINE, s):
  *   s in [0,16):  a = N_HD(i)[w0 * k_hd], c = N_HD(a)[w1 * k_hd]
  *   s in [16,20): c = N_LD(i)[w0 * k_ld]
  *   s in [20,24): a = N_LD(i)[w0 * k_ld], c = N_LD(a)[w1 * k_ld]
@@ -230,7 +232,7 @@ void oracle_hd_candidates(const oracle_state *st, int64_t i, int64_t *cand)
 {
     for (int s = 0; s < CAND_HD; ++s) {
         uint32_t w[4];
-        draw4(st->seed, st->t, (uint32_t)i, STREAM_HD, (uint32_t)s, w);
+        draw4(st->seed, st->t, (uint32_t)i, STREAM_REFINE, (uint32_t)s, w);
         int64_t c;
         if (s < HD_SLOTS_NN) {
             int64_t a = st->hd_idx[i * st->k_hd + map_index(w[0], st->k_hd)];
@@ -248,24 +250,25 @@ void oracle_hd_candidates(const oracle_state *st, int64_t i, int64_t *cand)
 }
 
 /*
- * LD candidates of point i at iteration t. Slot s uses counter (t, i, LD, s):
- *   s in [0,16):  a = N_LD(i)[w0 * k_ld], c = N_LD(a)[w1 * k_ld]
- *   s in [16,24): c = N_HD(i)[w0 * k_hd]   (HD set of iteration t)
- *   s in [24,32): c uniform over the other points (w0)
+ * LD candidates of point i at iteration t. Slot s uses words w2, w3 of the
+ * Philox block at counter (t, i, REFINE, s) (the HD slot s uses w0, w1):
+ *   s in [0,16):  a = N_LD(i)[w2 * k_ld], c = N_LD(a)[w3 * k_ld]
+ *   s in [16,24): c = N_HD(i)[w2 * k_hd]   (HD set of iteration t)
+ *   s in [24,32): c uniform over the other points (w2)
  */
 void oracle_ld_candidates(const oracle_state *st, int64_t i, int64_t *cand)
 {
     for (int s = 0; s < CAND_LD; ++s) {
         uint32_t w[4];
-        draw4(st->seed, st->t, (uint32_t)i, STREAM_LD, (uint32_t)s, w);
+        draw4(st->seed, st->t, (uint32_t)i, STREAM_REFINE, (uint32_t)s, w);
         int64_t c;
         if (s < LD_SLOTS_NN) {
-            int64_t a = st->ld_idx[i * st->k_ld + map_index(w[0], st->k_ld)];
-            c = st->ld_idx[a * st->k_ld + map_index(w[1], st->k_ld)];
+            int64_t a = st->ld_idx[i * st->k_ld + map_index(w[2], st->k_ld)];
+            c = st->ld_idx[a * st->k_ld + map_index(w[3], st->k_ld)];
         } else if (s < LD_SLOTS_HDNB) {
-            c = st->hd_idx[i * st->k_hd + map_index(w[0], st->k_hd)];
+            c = st->hd_idx[i * st->k_hd + map_index(w[2], st->k_hd)];
         } else {
-            c = map_other(w[0], st->N, i);
+            c = map_other(w[2], st->N, i);
         }
         cand[s] = c;
     }
@@ -749,4 +752,117 @@ void oracle_query_knn(const double *X, int64_t N, int D, const int64_t *q, int64
         }
     }
     free(u);
+}
+
+/* ------------------------------------------------------------------ */
+/* Insertion of new points (Section 3: points can be added on the fly;  */
+/* the builder's reading of how a new point enters the state).          */
+/* ------------------------------------------------------------------ */
+
+/* Mean placement of a new point: the average LD position of its HD
+ * neighbours (all of them existing points). */
+static void place_mean(oracle_state *st, int64_t i)
+{
+    int d = st->d, kh = st->k_hd;
+    for (int c = 0; c < d; ++c) {
+        double s = 0.0;
+        for (int a = 0; a < kh; ++a) s += st->Y[(int64_t)st->hd_idx[i * kh + a] * d + c];
+        st->Y[i * d + c] = s / kh;
+    }
+}
+
+/*
+ * Insert the rows n_old .. st->N - 1 (their X rows already in place, every
+ * other array already sized for st->N) at iteration t = st->t:
+ *   1. HD list: k_hd distinct existing points, slot l drawing an offset in
+ *      [0, n_old) from counter (t, i, INSERT, l), linear probing mod n_old;
+ *      ordered by (d2, idx);
+ *   2. INSERT_ROUNDS rounds of 32 candidates, round r slot s from counter
+ *      (t, i, INSERT, 64 + 32 r + s): slots 0..23 a = list(i)[w0 * k_hd],
+ *      c = list(a)[w1 * k_hd] (a is an existing point, its list of
+ *      iteration t); slots 24..31 a uniform existing point; top-k merge;
+ *   3. cold-start bisection for beta and P;
+ *   4. Y = mean of the HD neighbours' Y (placement 0); V = 0;
+ *   5. LD list = the first k_ld HD neighbours, completed (when k_ld > k_hd)
+ *      by distinct random existing points from counter (t, i, INSERT, 256 + l);
+ *   6. Zhat scaled by the ratio of ordered pair counts, E = max(E, n_new/N).
+ * Placement 1 (a learned map) is handled by the caller, which overwrites Y.
+ */
+void oracle_insert(oracle_state *st, int64_t n_old, double bisect_tol, int bisect_maxit)
+{
+    int64_t N = st->N;
+    int D = st->D, kh = st->k_hd, kl = st->k_ld;
+    int64_t cand[CAND_HD];
+    double cd2[CAND_HD];
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)kh);
+    double *ld2 = (double *)malloc(sizeof(double) * (size_t)kh);
+    int32_t *nl = (int32_t *)malloc(sizeof(int32_t) * (size_t)kh);
+    double *nd2 = (double *)malloc(sizeof(double) * (size_t)kh);
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(kh > kl ? kh : kl));
+    for (int64_t i = n_old; i < N; ++i) {
+        for (int l = 0; l < kh; ++l) {
+            uint32_t w[4];
+            draw4(st->seed, st->t, (uint32_t)i, STREAM_INSERT, (uint32_t)l, w);
+            int64_t o = map_index(w[0], n_old);
+            for (;;) {
+                int taken = 0;
+                for (int m = 0; m < l; ++m)
+                    if (off[m] == o) taken = 1;
+                if (!taken) break;
+                o = (o + 1) % n_old;
+            }
+            off[l] = o;
+            st->hd_idx[i * kh + l] = (int32_t)o;
+        }
+        sort_hd_list(st, i);
+        for (int r = 0; r < INSERT_ROUNDS; ++r) {
+            for (int a = 0; a < kh; ++a) {
+                list[a] = st->hd_idx[i * kh + a];
+                ld2[a] = st->hd_d2[i * kh + a];
+            }
+            for (int s = 0; s < CAND_HD; ++s) {
+                uint32_t w[4];
+                draw4(st->seed, st->t, (uint32_t)i, STREAM_INSERT, (uint32_t)(64 + 32 * r + s), w);
+                int64_t c;
+                if (s < INSERT_SLOTS_NN) {
+                    int64_t a = list[map_index(w[0], kh)];
+                    c = st->hd_idx[a * kh + map_index(w[1], kh)];
+                } else {
+                    c = map_index(w[0], n_old);
+                }
+                cand[s] = c;
+                cd2[s] = sqdist(st->X + i * D, st->X + c * D, D);
+            }
+            oracle_topk_merge(i, kh, list, ld2, CAND_HD, cand, cd2, nl, nd2);
+            for (int a = 0; a < kh; ++a) {
+                st->hd_idx[i * kh + a] = nl[a];
+                st->hd_d2[i * kh + a] = nd2[a];
+            }
+        }
+        oracle_bisect(st->hd_d2 + i * kh, kh, st->perplexity, 0.0, bisect_tol, bisect_maxit,
+                      st->beta + i, st->P + i * kh);
+        place_mean(st, i);
+        for (int c = 0; c < st->d; ++c) st->V[i * st->d + c] = 0.0;
+        int m = kl < kh ? kl : kh;
+        for (int a = 0; a < m; ++a) st->ld_idx[i * kl + a] = st->hd_idx[i * kh + a];
+        for (int l = m; l < kl; ++l) {
+            uint32_t w[4];
+            draw4(st->seed, st->t, (uint32_t)i, STREAM_INSERT, (uint32_t)(256 + l), w);
+            int64_t o = map_index(w[0], n_old);
+            for (;;) {
+                if (!contains(st->ld_idx + i * kl, l, o)) break;
+                o = (o + 1) % n_old;
+            }
+            st->ld_idx[i * kl + l] = (int32_t)o;
+        }
+    }
+    double ratio = ((double)N * (double)(N - 1)) / ((double)n_old * (double)(n_old - 1));
+    st->Zhat = st->Zhat * ratio;
+    double frac = (double)(N - n_old) / (double)N;
+    if (frac > st->E) st->E = frac;
+    free(list);
+    free(ld2);
+    free(nl);
+    free(nd2);
+    free(off);
 }

@@ -17,7 +17,7 @@ __all__ = ["lib", "philox", "OracleState", "bisect", "entropy", "topk_merge",
 
 ORACLE_BISECT_TOL = 1e-9
 ORACLE_BISECT_MAXIT = 200
-STREAMS = dict(COIN=0, HD=1, LD=2, NEG=3, MLP=4, INSERT=5, INIT_HD=6, INIT_LD=7,
+STREAMS = dict(COIN=0, REFINE=1, NEG=3, MLP=4, INSERT=5, INIT_HD=6, INIT_LD=7,
                INIT_Y=8, ZINIT=9)
 CAND_HD = 32
 CAND_LD = 32
@@ -87,6 +87,8 @@ def _declare(L):
     L.oracle_bruteforce_knn.restype = None
     L.oracle_query_knn.argtypes = [_dp, C.c_int64, C.c_int, _lp, C.c_int64, C.c_int, _ip, _dp]
     L.oracle_query_knn.restype = None
+    L.oracle_insert.argtypes = [sp, C.c_int64, C.c_double, C.c_int]
+    L.oracle_insert.restype = None
 
 
 def _p(a, t):
@@ -285,6 +287,26 @@ class OracleState:
         lib().oracle_step(C.byref(self._s), float(tol), int(maxit), _p(A, _dp), _p(R, _dp),
                           _p(flags, _bp), _p(info, _lp), _p(z, _dp))
         return dict(A=A, R=R, flags=flags, coin=bool(info[0]), n_new=int(info[1]), z=z)
+
+    def insert(self, X_new, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
+        """Append the rows of X_new (mean placement). Returns the first new index."""
+        X_new = _f64(X_new)
+        n_old, n_new = self.N, X_new.shape[0]
+        N = n_old + n_new
+
+        def grow(a, fill=0):
+            out = np.full((N,) + a.shape[1:], fill, dtype=a.dtype)
+            out[:n_old] = a
+            return out
+        self.X = np.concatenate([self.X, X_new], axis=0)
+        self.Y, self.V = grow(self.Y), grow(self.V)
+        self.hd_idx, self.hd_d2, self.ld_idx = grow(self.hd_idx), grow(self.hd_d2), grow(self.ld_idx)
+        self.beta, self.P = grow(self.beta), grow(self.P)
+        self.N = N
+        self._s.N = N
+        self._bind()
+        lib().oracle_insert(C.byref(self._s), n_old, float(tol), int(maxit))
+        return n_old
 
     def dense_p(self):
         Pd = np.zeros((self.N, self.N))

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/funcsne.h"
@@ -23,6 +24,7 @@ using namespace fsne;
 
 struct funcsne {
     int64_t N = 0;
+    int64_t cap = 0;  // rows allocated (N <= cap; rows beyond N are zero)
     int32_t D = 0, d = 0, DP = 0, k_hd = 0, k_ld = 0, n_neg = 0, RH = 1;
     float alpha = 1.f, perplexity = 30.f;
     uint64_t seed = 0;
@@ -107,7 +109,7 @@ StepParams step_params(const funcsne* h) {
     p.qscale_off = h->qscale_off;
     p.hd_mode = h->hd_mode;
     p.xs_floats = h->xs_floats;
-    p.smem_per_warp = h->xs_floats * 4 + 96 * 4;
+    p.smem_per_warp = h->xs_floats * 4 + kHashSlots * 4;
     p.alpha = h->alpha;
     p.inv_alpha = 1.f / h->alpha;
     p.inv2N = static_cast<float>(1.0 / (2.0 * static_cast<double>(h->N)));
@@ -177,7 +179,7 @@ cudaError_t launch_step_kernel(const funcsne* h, const StepParams& p, cudaStream
 
 // Grid of the step kernel: resident blocks per SM x SMs (persistent warps).
 int configure_step(funcsne* h) {
-    h->step_smem = static_cast<size_t>(8) * (h->xs_floats * 4 + 96 * 4);
+    h->step_smem = static_cast<size_t>(8) * (h->xs_floats * 4 + kHashSlots * 4);
     int occ = 0;
     switch (h->precision) {
         case FUNCSNE_FP32: occ = step_occupancy_f32(h->DP, h->RH, h->step_smem); break;
@@ -322,6 +324,54 @@ ZinitParams zinit_params(const funcsne* h, const int32_t* hd, const int32_t* ld,
     return z;
 }
 
+// Reallocate every per-point array for new_cap rows (N rows kept, the rest zero).
+int grow(funcsne* h, int64_t new_cap) {
+    const int64_t N = h->N;
+    auto move = [&](auto** p, size_t row_elems) -> int {
+        using T = std::remove_pointer_t<std::remove_reference_t<decltype(*p)>>;
+        T* q = nullptr;
+        FSNE_CUDA(h, dalloc(&q, static_cast<size_t>(new_cap) * row_elems));
+        FSNE_CUDA(h, cudaMemsetAsync(q, 0, static_cast<size_t>(new_cap) * row_elems * sizeof(T), h->stream));
+        if (*p) {
+            FSNE_CUDA(h, cudaMemcpyAsync(q, *p, static_cast<size_t>(N) * row_elems * sizeof(T), cudaMemcpyDeviceToDevice,
+                                         h->stream));
+            FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+            cudaFree(*p);
+        }
+        *p = q;
+        return FUNCSNE_OK;
+    };
+    int rc;
+    if ((rc = move(&h->X32, h->xpitch))) return rc;
+    if (h->Xq && (rc = move(&h->Xq, h->qpitch))) return rc;
+    // LD rows: DP floats each, plus one spare row so that the element count
+    // rounded up to a multiple of 4 stays inside the allocation
+    const int64_t spare = new_cap + 1;
+    auto move_rows = [&](float** p) -> int {
+        float* q = nullptr;
+        FSNE_CUDA(h, dalloc(&q, static_cast<size_t>(spare) * h->DP));
+        FSNE_CUDA(h, cudaMemsetAsync(q, 0, static_cast<size_t>(spare) * h->DP * sizeof(float), h->stream));
+        FSNE_CUDA(h, cudaMemcpyAsync(q, *p, static_cast<size_t>(h->yelem) * sizeof(float), cudaMemcpyDeviceToDevice,
+                                     h->stream));
+        FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+        cudaFree(*p);
+        *p = q;
+        return FUNCSNE_OK;
+    };
+    if ((rc = move_rows(&h->Y)) || (rc = move_rows(&h->V)) || (rc = move_rows(&h->A)) || (rc = move_rows(&h->R)))
+        return rc;
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = move(&h->hd_idx[b], h->k_hd))) return rc;
+        if ((rc = move(&h->hd_d2[b], h->k_hd))) return rc;
+        if ((rc = move(&h->ld_idx[b], h->k_ld))) return rc;
+    }
+    if ((rc = move(&h->P, h->k_hd))) return rc;
+    if ((rc = move(&h->beta, 1))) return rc;
+    h->cap = new_cap;
+    drop_graphs(h);
+    return FUNCSNE_OK;
+}
+
 }  // namespace
 
 namespace fsne {
@@ -365,6 +415,7 @@ int funcsne_create(const float* X, int64_t N, int32_t D, int32_t d, int32_t k_hd
     h->n4 = h->xpitch / 4;
     h->xs_floats = round_up(D, 16);
     h->yelem = (N * h->DP + 3) / 4 * 4;
+    h->cap = N;
 
     auto bail = [&](int rc) {
         g_create_error = h->err;
@@ -575,11 +626,71 @@ int funcsne_sync(funcsne_t* h) {
 }
 
 int funcsne_insert(funcsne_t* h, const float* X_new, int64_t n_new, int32_t placement, int64_t* first_id) {
-    (void)X_new;
-    (void)n_new;
-    (void)placement;
-    (void)first_id;
-    return fail(h, FUNCSNE_E_STATE, "funcsne_insert is not available in this build");
+    if (!h || !X_new || !first_id) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    if (n_new < 1) return fail(h, FUNCSNE_E_ARG, "n_new must be >= 1");
+    if (placement != FUNCSNE_PLACE_MEAN && placement != FUNCSNE_PLACE_SURROGATE)
+        return fail(h, FUNCSNE_E_ARG, "placement must be FUNCSNE_PLACE_MEAN or FUNCSNE_PLACE_SURROGATE");
+    const int64_t n_old = h->N, N2 = h->N + n_new;
+    if (N2 >= (int64_t(1) << 31) - 1) return fail(h, FUNCSNE_E_ARG, "N + n_new must stay below 2^31 - 1");
+    DevScalars s;
+    int rc = read_scalars(h, &s);
+    if (rc) return rc;
+    if (N2 > h->cap) {
+        int64_t nc = h->cap + h->cap / 2;
+        if (nc < N2) nc = N2;
+        if ((rc = grow(h, nc))) return rc;
+    }
+    float* xdst = h->X32 + n_old * h->xpitch;
+    FSNE_CUDA(h, cudaMemcpy2DAsync(xdst, h->xpitch * sizeof(float), X_new, h->D * sizeof(float),
+                                   h->D * sizeof(float), static_cast<size_t>(n_new), cudaMemcpyDefault, h->stream));
+    FSNE_CUDA(h, launch_check_finite(xdst, n_new * h->xpitch, &h->sc->err, h->stream));
+    {
+        DevScalars chk;
+        if ((rc = read_scalars(h, &chk))) return rc;
+        if (chk.err & kErrNonFinite) {
+            FSNE_CUDA(h, cudaMemsetAsync(xdst, 0, static_cast<size_t>(n_new) * h->xpitch * sizeof(float), h->stream));
+            clear_error_word(h);
+            return fail(h, FUNCSNE_E_NAN, "X_new holds non-finite values");
+        }
+    }
+    if (h->precision != FUNCSNE_FP32)
+        FSNE_CUDA(h, launch_quantize(xdst, n_new, h->D, h->xpitch, h->precision, h->qpitch, h->qscale_off,
+                                     h->Xq + n_old * h->qpitch, h->stream));
+    InsertParams q{};
+    q.N = N2;
+    q.n_old = n_old;
+    q.k_hd = h->k_hd;
+    q.k_ld = h->k_ld;
+    q.n4 = h->n4;
+    q.xpitch = h->xpitch;
+    q.log_perp = std::log(h->perplexity);
+    q.t = s.t;
+    q.seed = h->seed;
+    q.X32 = h->X32;
+    q.Y = h->Y;
+    q.V = h->V;
+    q.A = h->A;
+    q.R = h->R;
+    q.hd_idx = h->hd_idx[s.hd_cur];
+    q.hd_d2 = h->hd_d2[s.hd_cur];
+    q.ld_idx = h->ld_idx[s.ld_cur];
+    q.P = h->P;
+    q.beta = h->beta;
+    FSNE_CUDA(h, launch_insert(q, h->DP, h->stream));
+    // the scalars of the grown state: Zhat scaled by the ordered pair count,
+    // inserted points count as points with new neighbours
+    s.Zhat *= (static_cast<double>(N2) * static_cast<double>(N2 - 1)) /
+              (static_cast<double>(n_old) * static_cast<double>(n_old - 1));
+    const double frac = static_cast<double>(n_new) / static_cast<double>(N2);
+    if (frac > s.E) s.E = frac;
+    FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->Zhat, &s.Zhat, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->E, &s.E, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->N = N2;
+    h->yelem = (N2 * h->DP + 3) / 4 * 4;
+    configure_step(h);
+    *first_id = n_old;
+    return FUNCSNE_OK;
 }
 
 int funcsne_get_embedding(const funcsne_t* hc, float* Y_out, int64_t cap_rows) {

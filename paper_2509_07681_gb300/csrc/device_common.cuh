@@ -163,19 +163,22 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// Reduce-scatter: afterwards lane l holds the warp sum of v[l] (31 shuffles).
-__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
+// Reduce-scatter of v[OFF .. OFF+32): afterwards lane l holds the warp sum
+// of v[OFF + l] (31 shuffles).
+template <int OFF = 0, int N>
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[N], int lane) {
+    static_assert(OFF + 32 <= N, "reduce-scatter window out of range");
 #pragma unroll
     for (int w = 16; w >= 1; w >>= 1) {
         const bool up = (lane & w) != 0;
 #pragma unroll
         for (int k = 0; k < w; ++k) {
-            const float send = up ? v[k] : v[k + w];
-            const float keep = up ? v[k + w] : v[k];
-            v[k] = keep + __shfl_xor_sync(kFull, send, w);
+            const float send = up ? v[OFF + k] : v[OFF + k + w];
+            const float keep = up ? v[OFF + k + w] : v[OFF + k];
+            v[OFF + k] = keep + __shfl_xor_sync(kFull, send, w);
         }
     }
-    return v[0];
+    return v[OFF];
 }
 
 // ---------------------------------------------------------------- rows
@@ -342,12 +345,50 @@ __device__ __forceinline__ ApproxDist dist_fp8(const float* __restrict__ xs,
     return finish_band(acc, s1, s2, gamma);
 }
 
+// ---------------------------------------------------------------- warp hash sets
+// Open-addressing set of point indices in shared memory (256 slots, linear
+// probing, EMPTY = 0xffffffff). At most 96 entries are ever inserted, so an
+// empty slot always exists and every probe sequence ends.
+constexpr uint32_t kHashEmpty = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t hash_slot(uint32_t x) { return (x * 2654435761u) >> 24; }
+
+__device__ __forceinline__ void hset_clear(uint32_t* tab, int lane) {
+    const uint4 e = make_uint4(kHashEmpty, kHashEmpty, kHashEmpty, kHashEmpty);
+    reinterpret_cast<uint4*>(tab)[lane] = e;
+    reinterpret_cast<uint4*>(tab)[lane + 32] = e;
+}
+
+__device__ __forceinline__ void hset_insert(uint32_t* tab, uint32_t x) {
+    uint32_t h = hash_slot(x);
+    for (int probe = 0; probe < kHashSlots; ++probe) {
+        const uint32_t prev = atomicCAS(tab + h, kHashEmpty, x);
+        if (prev == kHashEmpty || prev == x) return;
+        h = (h + 1u) & (kHashSlots - 1);
+    }
+}
+
+__device__ __forceinline__ bool hset_has(const uint32_t* tab, uint32_t x) {
+    uint32_t h = hash_slot(x);
+    for (int probe = 0; probe < kHashSlots; ++probe) {
+        const uint32_t v = tab[h];
+        if (v == x) return true;
+        if (v == kHashEmpty) return false;
+        h = (h + 1u) & (kHashSlots - 1);
+    }
+    return false;
+}
+
 // ---------------------------------------------------------------- bisection (Eq. 1)
 // Warp-wide calibration of beta = 1/(2 sigma^2) for a sorted list of k
-// squared distances held as element e = r*32 + lane. Entropy
-// H = ln S + beta T / S with S = sum exp(-beta (d - d0)), T = sum exp(.)(d - d0).
-// Start from beta0 (> 0: warm restart) or 1/mean(d - d0); double while H is
-// above the target, then bisect until |H - ln perp| < tol.
+// squared distances held as element e = r*32 + lane. With sh = d - d0,
+// S = sum exp(-beta sh), U = sum exp(.) sh, V = sum exp(.) sh^2:
+// H = ln S + beta U/S and dH/dbeta = -beta (V/S - (U/S)^2) < 0.
+// Start from beta0 (> 0: warm restart) or 1/mean(sh); keep a bracket
+// [lo, hi] on the root of H = ln perp; take the Newton step when it stays
+// inside the bracket, else double (no upper bound yet) or halve the bracket;
+// stop when |H - ln perp| < tol. The oracle reaches the same tolerance by
+// plain bisection.
 template <int R>
 __device__ __forceinline__ float warp_bisect(const float (&d2)[R], int k, float log_perp,
                                              float beta0, float (&p)[R], int lane) {
@@ -369,33 +410,45 @@ __device__ __forceinline__ float warp_bisect(const float (&d2)[R], int k, float 
         m = warp_sum(m) * inv_k;
         beta = m > 0.f ? 1.f / m : 1.f;
     }
+    constexpr float kLog2e = 1.4426950408889634f;
     float lo = 0.f, hi = INFINITY;
     for (int it = 0; it < kBisectMaxIt; ++it) {
-        float S = 0.f, T = 0.f;
+        float S = 0.f, U = 0.f, V = 0.f;
+        const float nb = -beta * kLog2e;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (r * 32 + lane < k) {
-                const float e = expf(-beta * sh[r]);
+                const float e = exp2f(nb * sh[r]);
                 S += e;
-                T = __fmaf_rn(e, sh[r], T);
+                const float es = e * sh[r];
+                U += es;
+                V = __fmaf_rn(es, sh[r], V);
             }
         }
-        S = warp_sum(S);
-        T = warp_sum(T);
-        const float H = logf(S) + beta * T / S;
-        if (fabsf(H - log_perp) < kBisectTol) break;
-        if (H > log_perp) {
-            lo = beta;
-            beta = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
-        } else {
-            hi = beta;
-            beta = 0.5f * (lo + hi);
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) {
+            S += __shfl_xor_sync(kFull, S, m);
+            U += __shfl_xor_sync(kFull, U, m);
+            V += __shfl_xor_sync(kFull, V, m);
         }
+        const float mu = U / S;
+        const float H = logf(S) + beta * mu;
+        const float f = H - log_perp;
+        if (fabsf(f) < kBisectTol) break;
+        if (f > 0.f)
+            lo = beta;
+        else
+            hi = beta;
+        const float slope = -beta * (V / S - mu * mu);
+        float nxt = beta - f / slope;
+        if (!(slope < 0.f) || !(nxt > lo) || !(nxt < hi)) nxt = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
+        beta = nxt;
     }
     float S = 0.f;
+    const float nb = -beta * kLog2e;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        p[r] = (r * 32 + lane < k) ? expf(-beta * sh[r]) : 0.f;
+        p[r] = (r * 32 + lane < k) ? exp2f(nb * sh[r]) : 0.f;
         S += p[r];
     }
     S = warp_sum(S);

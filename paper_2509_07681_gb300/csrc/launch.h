@@ -44,6 +44,24 @@ struct KnnParams {
     float* d2;                 // n_q x k
 };
 
+struct InsertParams {
+    int64_t N, n_old;
+    int32_t k_hd, k_ld, n4, xpitch;
+    float log_perp;
+    uint32_t t;
+    uint64_t seed;
+    const float* X32;
+    float* Y;
+    float* V;
+    float* A;
+    float* R;
+    int32_t* hd_idx;   // current HD buffer (rows of existing points are read)
+    float* hd_d2;
+    int32_t* ld_idx;   // current LD buffer
+    float* P;
+    float* beta;
+};
+
 // step kernels, one translation unit per HD storage precision
 cudaError_t step_launch_f32(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
 cudaError_t step_launch_bf16(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
@@ -65,6 +83,8 @@ cudaError_t launch_check_lists(const int32_t* idx, int64_t N, int k, uint32_t* e
 cudaError_t launch_check_finite(const float* X, int64_t n, uint32_t* err, cudaStream_t s);
 cudaError_t launch_ld_distances(const float* Y, const int32_t* idx, int64_t N, int k, int DP, float* d2,
                                 cudaStream_t s);
+
+cudaError_t launch_insert(const InsertParams& q, int DP, cudaStream_t s);
 
 // evaluation
 cudaError_t launch_exact_knn(const KnnParams& kp, cudaStream_t s);

@@ -9,8 +9,9 @@ namespace fsne {
 // Random-stream identifiers: every draw uses the Philox counter
 // (iteration, point, stream, slot) under the 64-bit seed.
 constexpr uint32_t kStreamCoin = 0;
-constexpr uint32_t kStreamHd = 1;
-constexpr uint32_t kStreamLd = 2;
+// One block per (iteration, point, slot) drives both refinements: words 0-1
+// the HD candidate of slot s, words 2-3 the LD candidate of slot s.
+constexpr uint32_t kStreamRefine = 1;
 constexpr uint32_t kStreamNeg = 3;
 constexpr uint32_t kStreamMlp = 4;
 constexpr uint32_t kStreamInsert = 5;
@@ -37,6 +38,8 @@ constexpr float kBisectTol = 1e-5f;  // |H - ln perp| in FP32
 constexpr int kBisectMaxIt = 64;
 
 constexpr int kHdAdaptive = 0, kHdAlways = 1, kHdNever = 2;
+
+constexpr int kHashSlots = 256;  // per-warp membership set in shared memory
 
 // Device-resident scalars of the method (one per handle).
 struct DevScalars {

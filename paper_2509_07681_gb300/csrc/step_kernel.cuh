@@ -24,15 +24,18 @@ namespace fsne {
 
 constexpr int kWarpsPerBlock = 8;
 
+// Resident blocks per SM the register budget is sized for (8 warps each).
+template <int DP>
+constexpr int step_min_blocks() { return DP >= 32 ? 2 : 3; }
+
 template <int DP, int RH, int XM>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, step_min_blocks<DP>())
 step_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     float* xs = reinterpret_cast<float*>(smem + wib * p.smem_per_warp);
-    int32_t* s_hd = reinterpret_cast<int32_t*>(xs + p.xs_floats);  // 64 entries
-    int32_t* s_ld = s_hd + 64;                                      // 32 entries
+    uint32_t* tab = reinterpret_cast<uint32_t*>(xs + p.xs_floats);  // warp hash set
     __shared__ double s_z[kWarpsPerBlock];
     __shared__ unsigned long long s_cnt[kWarpsPerBlock][3];
 
@@ -80,6 +83,9 @@ step_kernel(const StepParams p) {
         float yi[DP];
         load_row<DP>(Y + gi * DP, yi);
 
+        // one Philox block per slot: words 0-1 drive the HD candidate, 2-3 the LD one
+        const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+
         // ---------------- HD refinement
         uint32_t nh_idx[RH];
         float nh_d2[RH];
@@ -94,8 +100,11 @@ step_kernel(const StepParams p) {
             const float* xrow = p.X32 + gi * p.xpitch;
             for (int f = lane * 4; f < p.xpitch; f += 128)
                 *reinterpret_cast<float4*>(xs + f) = __ldg(reinterpret_cast<const float4*>(xrow + f));
+            hset_clear(tab, lane);
             __syncwarp();
-            const uint4 w = philox(t, i, kStreamHd, static_cast<uint32_t>(lane), p.seed);
+#pragma unroll
+            for (int r = 0; r < RH; ++r)
+                if (r * 32 + lane < k_hd) hset_insert(tab, hidx[r]);
             const uint32_t e0 = lane < kHdNnEnd ? map_index(w.x, k_hd) : map_index(w.x, k_ld);
             const uint32_t hv = warp_get<RH>(hidx, e0);
             const uint32_t lv = __shfl_sync(kFull, lidx, static_cast<int>(e0 & 31u));
@@ -108,11 +117,8 @@ step_kernel(const StepParams p) {
                 c = static_cast<uint32_t>(__ldg(ld_idx_c + static_cast<int64_t>(lv) * k_ld + map_index(w.y, k_ld)));
             else
                 c = map_other(w.x, N, i);
-            bool valid = (c != i) && (c < N);
-#pragma unroll
-            for (int r = 0; r < RH; ++r)
-#pragma unroll 8
-                for (int m = 0; m < 32; ++m) valid &= (__shfl_sync(kFull, hidx[r], m) != c);
+            __syncwarp();
+            bool valid = (c != i) && (c < N) && !hset_has(tab, c);
             const unsigned same = __match_any_sync(kFull, c);
             valid &= (same & ((1u << lane) - 1u)) == 0u;
 
@@ -193,20 +199,22 @@ step_kernel(const StepParams p) {
         // ---------------- LD refinement (candidates from the lists of iteration t)
         uint32_t nl;
         {
-            const uint4 w = philox(t, i, kStreamLd, static_cast<uint32_t>(lane), p.seed);
-            const uint32_t e0 = lane < kLdNnEnd ? map_index(w.x, k_ld) : map_index(w.x, k_hd);
+            __syncwarp();
+            hset_clear(tab, lane);
+            __syncwarp();
+            if (lane < k_ld) hset_insert(tab, lidx);
+            const uint32_t e0 = lane < kLdNnEnd ? map_index(w.z, k_ld) : map_index(w.z, k_hd);
             const uint32_t lv = __shfl_sync(kFull, lidx, static_cast<int>(e0 & 31u));
             const uint32_t hv = warp_get<RH>(hidx, e0);
             uint32_t c;
             if (lane < kLdNnEnd)
-                c = static_cast<uint32_t>(__ldg(ld_idx_c + static_cast<int64_t>(lv) * k_ld + map_index(w.y, k_ld)));
+                c = static_cast<uint32_t>(__ldg(ld_idx_c + static_cast<int64_t>(lv) * k_ld + map_index(w.w, k_ld)));
             else if (lane < kLdHdNbEnd)
                 c = hv;
             else
-                c = map_other(w.x, N, i);
-            bool valid = (c != i) && (c < N);
-#pragma unroll 8
-            for (int m = 0; m < 32; ++m) valid &= (__shfl_sync(kFull, lidx, m) != c);
+                c = map_other(w.z, N, i);
+            __syncwarp();
+            bool valid = (c != i) && (c < N) && !hset_has(tab, c);
             const unsigned same = __match_any_sync(kFull, c);
             valid &= (same & ((1u << lane) - 1u)) == 0u;
             uint64_t k2[2] = {kSentinel, kSentinel};
@@ -226,20 +234,25 @@ step_kernel(const StepParams p) {
         }
 
         // ---------------- forces over the new lists at Y_t
+        // S_i = HD u LD lists of iteration t+1, as a warp hash set
+        __syncwarp();
+        hset_clear(tab, lane);
+        __syncwarp();
 #pragma unroll
-        for (int r = 0; r < RH; ++r) {
-            const int e = r * 32 + lane;
-            if (e < k_hd) s_hd[e] = static_cast<int32_t>(nh_idx[r]);
-        }
-        if (lane < k_ld) s_ld[lane] = static_cast<int32_t>(nl);
+        for (int r = 0; r < RH; ++r)
+            if (r * 32 + lane < k_hd) hset_insert(tab, nh_idx[r]);
+        __syncwarp();
+        const bool ld_in_hd = lane < k_ld && hset_has(tab, nl);
+        __syncwarp();
+        if (lane < k_ld) hset_insert(tab, nl);
         __syncwarp();
 
-        float att[DP], rep[DP];
+        // attraction components in acc[0..DP), repulsion in acc[RO..RO+DP)
+        constexpr int RO = DP <= 16 ? 16 : DP;
+        constexpr int NACC = DP <= 4 ? RO + DP : 2 * RO;
+        float acc[NACC];
 #pragma unroll
-        for (int c = 0; c < DP; ++c) {
-            att[c] = 0.f;
-            rep[c] = 0.f;
-        }
+        for (int c = 0; c < NACC; ++c) acc[c] = 0.f;
         float z = 0.f;
         const float alpha = p.alpha, inv_alpha = p.inv_alpha;
         auto interact = [&](const float (&yj)[DP], float& w_out, float& winv_out, float (&dy)[DP]) {
@@ -265,81 +278,65 @@ step_kernel(const StepParams p) {
                 const float fr = 4.f * w * invZ * winv;
 #pragma unroll
                 for (int c = 0; c < DP; ++c) {
-                    att[c] = __fmaf_rn(fa, dy[c], att[c]);
-                    rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
+                    acc[c] = __fmaf_rn(fa, dy[c], acc[c]);
+                    acc[RO + c] = __fmaf_rn(fr, dy[c], acc[RO + c]);
                 }
                 z += w;
                 atomic_add_row<DP>(p.A + static_cast<int64_t>(j) * DP, dy, -fa);
             }
         }
         if (lane < k_ld) {
-            bool in_hd = false;
-            for (int m = 0; m < k_hd; ++m) in_hd |= (s_hd[m] == static_cast<int32_t>(nl));
-            if (!in_hd) {
+            if (!ld_in_hd) {
                 float yj[DP], dy[DP], w, winv;
                 load_row<DP>(Y + static_cast<int64_t>(nl) * DP, yj);
                 interact(yj, w, winv, dy);
                 const float fr = 4.f * w * invZ * winv;
 #pragma unroll
-                for (int c = 0; c < DP; ++c) rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
+                for (int c = 0; c < DP; ++c) acc[RO + c] = __fmaf_rn(fr, dy[c], acc[RO + c]);
                 z += w;
             }
         }
         for (int s = lane; s < p.n_neg; s += 32) {
             const uint4 w4 = philox(t, i, kStreamNeg, static_cast<uint32_t>(s), p.seed);
-            const int32_t j = static_cast<int32_t>(map_other(w4.x, N, i));
-            bool in_s = false;
-            for (int m = 0; m < k_hd; ++m) in_s |= (s_hd[m] == j);
-            for (int m = 0; m < k_ld; ++m) in_s |= (s_ld[m] == j);
-            if (!in_s) {
+            const uint32_t j = map_other(w4.x, N, i);
+            if (!hset_has(tab, j)) {
                 float yj[DP], dy[DP], w, winv;
                 load_row<DP>(Y + static_cast<int64_t>(j) * DP, yj);
                 interact(yj, w, winv, dy);
                 const float fr = p.neg_scale * 4.f * w * invZ * winv;
 #pragma unroll
-                for (int c = 0; c < DP; ++c) rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
+                for (int c = 0; c < DP; ++c) acc[RO + c] = __fmaf_rn(fr, dy[c], acc[RO + c]);
                 z = __fmaf_rn(p.neg_scale, w, z);
             }
         }
-        // warp reductions: lane c < DP ends with component c
+        // warp reductions: the lane owning component c adds A_i[c] and stores R_i[c]
         if constexpr (DP <= 4) {
 #pragma unroll
-            for (int c = 0; c < DP; ++c) {
-                att[c] = warp_sum(att[c]);
-                rep[c] = warp_sum(rep[c]);
-            }
+            for (int c = 0; c < NACC; ++c) acc[c] = warp_sum(acc[c]);
             if (lane < DP) {
-                float a = att[0], b = rep[0];
+                float a = acc[0], b = acc[RO];
 #pragma unroll
                 for (int c = 1; c < DP; ++c)
                     if (lane == c) {
-                        a = att[c];
-                        b = rep[c];
+                        a = acc[c];
+                        b = acc[RO + c];
                     }
                 atomicAdd(p.A + gi * DP + lane, a);
                 p.R[gi * DP + lane] = b;
             }
         } else if constexpr (DP == 32) {
-            const float a = warp_reduce_scatter32(att, lane);
-            const float b = warp_reduce_scatter32(rep, lane);
+            const float a = warp_reduce_scatter32<0>(acc, lane);
+            const float b = warp_reduce_scatter32<32>(acc, lane);
             atomicAdd(p.A + gi * DP + lane, a);
             p.R[gi * DP + lane] = b;
         } else {
-            float v[32];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] = 0.f;
-#pragma unroll
-            for (int c = 0; c < DP; ++c) {
-                v[c] = att[c];
-                v[16 + c] = rep[c];
-            }
-            const float s = warp_reduce_scatter32(v, lane);
+            const float v = warp_reduce_scatter32(acc, lane);
             const int c = lane & 15;
             if (c < DP) {
                 if (lane < 16)
-                    atomicAdd(p.A + gi * DP + c, s);
+                    atomicAdd(p.A + gi * DP + c, v);
                 else
-                    p.R[gi * DP + c] = s;
+                    p.R[gi * DP + c] = v;
             }
         }
         z = warp_sum(z);

@@ -214,3 +214,58 @@ def test_whole_run_blobs_recall_and_structure():
     r = rnx_curve(ld, exact, len(X))
     assert r[99] > 0.5
     assert math.isfinite(s["Zhat"]) and s["error_word"] == 0
+
+
+def test_insertion_matches_oracle():
+    """funcsne_insert (mean placement) against the oracle from the same state:
+    the new points' HD/LD lists, positions and bandwidths, the scalars, and
+    the next iteration over the grown state."""
+    X = synth.blobs(n=2600, dim=30, n_clusters=6, seed=15)
+    p = dict(d=2, k_hd=16, k_ld=8, n_neg=8, alpha=1.0, perplexity=8.0)
+    m = _make(X[:2000], p, hd_mode=1)
+    m.step(30)
+    st = m.export_state()
+    o = oracle_from_state(X[:2000], st, p, hd_mode=1)
+    first = m.insert(X[2000:])
+    o.insert(X[2000:])
+    assert first == 2000 and m.N == 2600
+    st1 = m.export_state()
+    new = range(2000, 2600)
+    X64 = X.astype(np.float64)
+    bad, amb = compare_sets(st1["hd_idx"], o.hd_idx, new, X64, fp32_band(30))
+    assert bad == 0 and amb <= 2
+    same = [i for i in new if set(st1["hd_idx"][i].tolist()) == set(o.hd_idx[i].tolist())]
+    ys = np.array(same)
+    assert np.max(rel_err_rows(st1["Y"][ys].astype(np.float64), o.Y[ys])) < 1e-5
+    np.testing.assert_allclose(st1["beta"][ys], o.beta[ys], rtol=5e-3)
+    for i in same:
+        assert set(st1["ld_idx"][i].tolist()) == set(o.ld_idx[i].tolist())
+    assert abs(st1["Zhat"] - o.Zhat) <= 1e-5 * o.Zhat and st1["E"] == o.E
+    # old points are untouched
+    np.testing.assert_array_equal(st1["hd_idx"][:2000], st["hd_idx"])
+    np.testing.assert_array_equal(st1["Y"][:2000], st["Y"])
+    # one more iteration over the grown state
+    o2 = oracle_from_state(X, st1, p, hd_mode=1)
+    m.debug_step()
+    st2 = m.export_state()
+    o2.step()
+    bad, amb = compare_sets(st2["hd_idx"], o2.hd_idx, range(2600), X64, fp32_band(30))
+    assert bad == 0 and amb <= 3
+    m.close()
+
+
+def test_insertion_grows_repeatedly_and_keeps_stepping():
+    X = synth.swissroll(n=3000, dim=16, n_clusters=8, seed=16)
+    p = dict(d=8, k_hd=32, k_ld=16, n_neg=16, alpha=1.0, perplexity=30.0)
+    m = _make(X[:1000], p)
+    m.step(20)
+    for b in range(4):
+        lo = 1000 + 500 * b
+        assert m.insert(X[lo:lo + 500]) == lo
+        m.step(10)
+    m.sync()
+    assert m.N == 3000 and m.stats()["N"] == 3000
+    hd = m.knn(F.SPACE_HD, with_d2=False)
+    assert hd.min() >= 0 and hd.max() < 3000
+    assert np.isfinite(m.embedding()).all()
+    m.close()

@@ -331,3 +331,49 @@ def test_whole_run_finds_neighbours_and_structure():
     r = rnx_curve(ld_exact, exact, len(X))
     assert r[99] > 0.6
     assert rnx_auc(ld_exact, exact, len(X), kmax=16) > 0.15
+
+
+# ---------------------------------------------------------------- insertion
+def test_insertion_lists_placement_and_scalars():
+    X = synth.blobs(n=700, dim=12, n_clusters=5, seed=13)
+    st = O.OracleState(X[:600], 2, 16, 12, 8, 1.0, 8.0, seed=13)
+    for _ in range(60):
+        st.step()
+    z0, e0 = st.Zhat, st.E
+    first = st.insert(X[600:])
+    assert first == 600 and st.N == 700
+    new = np.arange(600, 700)
+    for i in new:
+        row = st.hd_idx[i]
+        assert len(set(row.tolist())) == 16 and row.max() < 600 and row.min() >= 0
+        d2 = ((st.X[row] - st.X[i]) ** 2).sum(1)
+        assert np.all(np.diff(d2) >= 0)
+        # mean placement over the listed HD neighbours
+        np.testing.assert_allclose(st.Y[i], st.Y[row].mean(0), rtol=1e-12, atol=1e-15)
+        assert np.all(st.V[i] == 0)
+        assert st.ld_idx[i].tolist() == row[:12].tolist()
+        assert abs(st.P[i].sum() - 1) < 1e-9
+    assert abs(st.Zhat - z0 * (700 * 699) / (600 * 599)) <= 1e-12 * st.Zhat
+    assert st.E == max(e0, 100 / 700)
+    # four neighbour-of-neighbour rounds from a random start already find a
+    # large share of the exact neighbours among the existing points (random
+    # lists would find about 16/600 of them); later iterations refine the rest
+    ex, _ = O.bruteforce_knn(X[:600], 16)
+    exact_new = []
+    for i in new:
+        d2 = ((X[:600].astype(np.float64) - X[i]) ** 2).sum(1)
+        exact_new.append(np.lexsort((np.arange(600), d2))[:16])
+    assert recall(st.hd_idx[new], np.array(exact_new)) > 0.4
+    # the state keeps stepping
+    out = st.step()
+    assert np.isfinite(st.Y).all() and out["A"].shape == (700, 2)
+
+
+def test_insertion_with_more_ld_than_hd_neighbours():
+    X = synth.blobs(n=300, dim=6, n_clusters=3, seed=14)
+    st = O.OracleState(X[:250], 2, 8, 12, 4, 1.0, 5.0, seed=14)
+    st.insert(X[250:])
+    for i in range(250, 300):
+        row = st.ld_idx[i]
+        assert len(set(row.tolist())) == 12 and row.max() < 250
+        assert row[:8].tolist() == st.hd_idx[i].tolist()
