@@ -47,13 +47,21 @@ def _env_int(name, default):
 
 
 def algorithmic_bytes_per_point(D, d, k_hd, k_ld, n_neg, row_bytes, rerank_rows=0.0):
-    """Minimum bytes one point moves in one fused-step launch (forced HD
-    refinement), before sector rounding. See the design doc for the derivation."""
+    """Minimum bytes one point moves in each kernel of one iteration (HD
+    refinement forced), before sector rounding. the design doc derives them."""
     y = 4 * d
-    hd = (1 + 32) * row_bytes + rerank_rows * 4 * D + 2 * 8 * k_hd + 4 * k_hd + 20 * 4
-    ld = (1 + k_ld + 32) * y + 2 * 4 * k_ld + 16 * 4
-    forces = (k_hd + k_ld + n_neg) * y + k_hd * y + 2 * y
-    return hd + ld + forces
+    hd = ((1 + 32) * row_bytes + rerank_rows * 4 * D   # own row, candidate rows, exact re-ranks
+          + 8 * k_hd + 4 * k_ld                        # HD list (index, d2) and LD list of t
+          + 20 * 4                                     # neighbour-of-neighbour index reads
+          + 8 * k_hd)                                  # HD list of t+1
+    ld = (4 * k_ld + 4 * k_hd + 16 * 4                 # LD and HD lists of t, index reads
+          + (1 + k_ld + 32) * y                        # own, old-list and candidate rows of Y_t
+          + 4 * k_ld)                                  # LD list of t+1
+    forces = (8 * k_hd + 4 * k_ld                      # HD list and P, LD list of t+1
+              + (1 + k_hd + k_ld + n_neg) * y          # own row and gathered rows of Y_t
+              + k_hd * y + 2 * y)                      # reverse attraction (scatter), A_i and R_i
+    update = 7 * y                                     # Y, V, A read+write, R read
+    return {"hd_refine": hd, "ld_refine": ld, "forces": forces, "update": update}
 
 
 def kernel_source_hash():
@@ -75,10 +83,10 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def committed_traffic(kernel_hash, precision):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    valid only for the kernel sources it was captured from."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_spectrum-1m.json")
+def committed_traffic(kernel_hash, precision, kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, valid
+    only for the kernel sources it was captured from."""
+    path = os.path.join(ROOT, "profiles", "kernels_spectrum-1m.json")
     try:
         with open(path) as f:
             js = json.load(f)
@@ -86,7 +94,7 @@ def committed_traffic(kernel_hash, precision):
         return None
     if js.get("kernel_hash") != kernel_hash:
         return None
-    ent = js.get("dram_bytes_per_launch", {}).get(precision)
+    ent = js.get("dram_bytes_per_launch", {}).get(precision, {}).get(kernel)
     return float(ent) if ent is not None else None
 
 
@@ -184,7 +192,7 @@ def run_ours(args, rank, world):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ms_step, ms_upd = m.profile_step(K)
+        kms = m.profile_step(K)
         e1.record(stream)
         barrier()
         total_ms = e0.elapsed_time(e1)
@@ -196,7 +204,7 @@ def run_ours(args, rank, world):
             total_ms = float(t.item())
         scored = s1["cand_scored"] - s0["cand_scored"]
         rer = s1["cand_reranked"] - s0["cand_reranked"]
-        results[name] = dict(total_ms=total_ms, step_ms=ms_step / K, upd_ms=ms_upd / K,
+        results[name] = dict(total_ms=total_ms, kernel_ms={k: v / K for k, v in kms.items()},
                              rerank_rows=(rer / (N * K)) if prec != F.FP32 else 0.0,
                              rerank_frac=(rer / scored) if scored else None,
                              hd_idx=m.knn(F.SPACE_HD, with_d2=False))
@@ -240,18 +248,19 @@ def run_ours(args, rank, world):
     peak, peak_kind = measured_peaks()
     khash = kernel_source_hash()
     row_bytes = {"fp32": 4 * D, "bf16": 2 * D, "fp8": D + 4}
-    rf = {}
     for name in results:
         r = results[name]
-        alg = N * algorithmic_bytes_per_point(D, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], row_bytes[name],
-                                              r["rerank_rows"])
-        r["alg_bytes"] = alg
-        r["achieved_gbs"] = alg / (r["step_ms"] / 1e3) / 1e9
-    traffic = committed_traffic(khash, "bf16")
-    roofline = {"bound": "hbm", "achieved": round(head["achieved_gbs"], 1), "peak": peak, "unit": "GB/s",
-                "frac": round(head["achieved_gbs"] / peak, 4), "traffic": traffic,
-                "kernel": "step_kernel<16,1,BF16>", "peak_source": peak_kind,
-                "alg_bytes_per_launch": int(head["alg_bytes"])}
+        per = algorithmic_bytes_per_point(D, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], row_bytes[name],
+                                          r["rerank_rows"])
+        r["alg_bytes"] = {k: N * v for k, v in per.items()}
+        r["achieved_gbs"] = {k: r["alg_bytes"][k] / (r["kernel_ms"][k] / 1e3) / 1e9 for k in per}
+    top = max(head["kernel_ms"], key=head["kernel_ms"].get)
+    traffic = committed_traffic(khash, "bf16", top)
+    roofline = {"bound": "hbm", "achieved": round(head["achieved_gbs"][top], 1), "peak": peak, "unit": "GB/s",
+                "frac": round(head["achieved_gbs"][top] / peak, 4), "traffic": traffic,
+                "kernel": f"{top} (BF16 rows)", "peak_source": peak_kind,
+                "alg_bytes_per_launch": int(head["alg_bytes"][top]),
+                "step_frac": round(sum(head["alg_bytes"].values()) / (head["total_ms"] / K / 1e3) / 1e9 / peak, 4)}
     cpu = cpu_baseline(args, X, p, sample_n=100000, steps=2) if world == 1 else None
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -263,17 +272,18 @@ def run_ours(args, rank, world):
                    "burn_in": BURN_IN, "l2": "working set > L2 (X 208 MB + lists 768 MB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "precisions": {n: {"iters_per_s": round(K / (r["total_ms"] / 1e3), 2),
-                           "step_kernel_ms": round(r["step_ms"], 4), "update_kernel_ms": round(r["upd_ms"], 4),
+                           "kernel_ms": {k: round(v, 4) for k, v in r["kernel_ms"].items()},
                            "recall_at_k_hd": round(r["recall"], 5), "sets_equal_fp32": r["sets_equal_fp32"],
                            "rerank_rows_per_point": round(r["rerank_rows"], 3),
                            "rerank_fraction": None if r["rerank_frac"] is None else round(r["rerank_frac"], 4),
-                           "achieved_alg_gbs": round(r["achieved_gbs"], 1)} for n, r in results.items()},
+                           "achieved_alg_gbs": {k: round(v, 1) for k, v in r["achieved_gbs"].items()}}
+                       for n, r in results.items()},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": round(world * K / e2e_s, 3), "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes / K),
                 "d2h_bytes_per_step": int(N * p["d"] * 4),
                 "note": "create from pinned host X (H2D, init) + K x (step + embedding read-back), BF16"},
-        "gpu_launches": 2 * K * len(results),
+        "gpu_launches": 4 * K * len(results),
         "clocks": clk,
         "kernel_hash": khash,
     }
@@ -350,12 +360,15 @@ def run_profile_case(args):
     X, p = synth.make(WORKLOAD, n=args.n)
     m = F.FuncSNE(X, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0)
     m.set_option("hd_mode", 1)
+    if args.burn_in:
+        m.step(args.burn_in)
+        m.sync()
     for name in args.precisions.split(","):
         m.set_option("precision", {"fp32": F.FP32, "bf16": F.BF16, "fp8": F.FP8}[name])
         m.profile_step(args.warmup)
-        a, b = m.profile_step(args.steps)
+        kms = m.profile_step(args.steps)
         m.sync()
-        print(f"{name}: N={X.shape[0]} step_kernel {a / args.steps:.4f} ms update {b / args.steps:.4f} ms",
+        print(f"{name}: N={X.shape[0]} " + " ".join(f"{k} {v / args.steps:.4f} ms" for k, v in kms.items()),
               flush=True)
     m.close()
 
@@ -371,6 +384,7 @@ def main():
     ap.add_argument("--mode", choices=["bench", "ncu"], default="bench",
                     help="ncu: the short fixed launch sequence used for profiling")
     ap.add_argument("--precisions", default="fp32,bf16,fp8", help="precisions of --mode ncu")
+    ap.add_argument("--burn-in", type=int, default=0, help="--mode ncu: untimed iterations first")
     args = ap.parse_args()
     if args.mode == "ncu":
         run_profile_case(args)

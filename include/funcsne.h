@@ -183,11 +183,11 @@ int funcsne_import_state(funcsne_t *h, const funcsne_state_t *st);
 int funcsne_debug_step(funcsne_t *h, float *att, float *rep);
 
 /* Run n_iters iterations like funcsne_step but with direct kernel launches
- * and CUDA events around each kernel on the handle's stream; waits for the
- * stream and writes the summed device time (milliseconds) of the fused
- * step kernel and of the update kernel. For measurement. */
-int funcsne_profile_step(funcsne_t *h, int32_t n_iters, double *ms_step_kernel,
-                         double *ms_update_kernel);
+ * and CUDA events between the kernels on the handle's stream; waits for
+ * the stream and writes into ms_per_kernel[0..3] the summed device time
+ * (milliseconds) of the HD refinement, LD refinement, forces and update
+ * kernels. For measurement. */
+int funcsne_profile_step(funcsne_t *h, int32_t n_iters, double *ms_per_kernel);
 
 /* Exact k nearest HD neighbours (FP32 distances, ties by index) of the n_q
  * query points `queries` (int32, host or device), by brute force over all

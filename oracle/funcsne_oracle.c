@@ -71,8 +71,8 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
  * (iteration, point, purpose, slot), key = the 64-bit seed). */
 enum {
     STREAM_COIN = 0,
-    STREAM_REFINE = 1, /* words 0-1: HD candidate of the slot, words 2-3: LD candidate */
-    STREAM_NEG = 3,
+    STREAM_REFINE = 1, /* words 0-1: HD candidate of the slot, words 2-3: LD candidate,
+                          words 1 and 3 also seed the negative samples */
     STREAM_MLP = 4,
     STREAM_INSERT = 5,
     STREAM_INIT_HD = 6,
@@ -110,6 +110,20 @@ static void draw4(uint64_t seed, uint32_t t, uint32_t i, uint32_t stream, uint32
 static int64_t map_index(uint32_t u, int64_t m)
 {
     return (int64_t)(((uint64_t)u * (uint64_t)m) >> 32);
+}
+
+/* Negative sample s seeded by words 1 and 3 of the Philox block of slot
+ * s mod 32: the 32-bit finalizer of MurmurHash3 (Appleby) applied to
+ * w1 xor (w3 + (s div 32 + 1) * 0x9E3779B9). */
+static uint32_t negative_word(uint32_t w1, uint32_t w3, uint32_t pass)
+{
+    uint32_t h = w1 ^ (w3 + (pass + 1u) * 0x9E3779B9u);
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
 }
 
 /* uniform point index in [0, N) minus {i}. */
@@ -412,8 +426,11 @@ static void sort_hd_list(oracle_state *st, int64_t i)
  *   repulsion:  for j in S_i = N_HD(i) u N_LD(i):
  *               R_i += 4 (w_ij / Zhat) w^{1/alpha} (y_i - y_j);
  *               negatives s < n_neg: j_s uniform over the other points from
- *               counter (t, i, NEG, s); a draw inside S_i contributes 0;
- *               the others are scaled by (N-1)/n_neg.
+ *               negative_word of the block (t, i, stream, s mod 32), where
+ *               stream is REFINE in an iteration (the block that also draws
+ *               the candidates of slot s) and ZINIT for the first estimate;
+ *               a draw inside S_i contributes 0; the others are scaled by
+ *               (N-1)/n_neg.
  */
 double oracle_forces(const oracle_state *st, uint32_t t, uint32_t neg_stream, double zhat,
                      double *A, double *R, double *z_per_point)
@@ -473,8 +490,8 @@ double oracle_forces(const oracle_state *st, uint32_t t, uint32_t neg_stream, do
             double scale = (double)(N - 1) / (double)st->n_neg;
             for (int s = 0; s < st->n_neg; ++s) {
                 uint32_t w4[4];
-                draw4(st->seed, t, (uint32_t)i, neg_stream, (uint32_t)s, w4);
-                int64_t j = map_other(w4[0], N, i);
+                draw4(st->seed, t, (uint32_t)i, neg_stream, (uint32_t)(s % 32), w4);
+                int64_t j = map_other(negative_word(w4[1], w4[3], (uint32_t)(s / 32)), N, i);
                 if (contains(S, ns, j)) continue;
                 const double *yj = st->Y + j * d;
                 double r2 = sqdist(yi, yj, d);
@@ -632,7 +649,7 @@ void oracle_step(oracle_state *st, double bisect_tol, int bisect_maxit, double *
     free(nh_d2);
     free(nl_idx);
 
-    double zt = oracle_forces(st, st->t, STREAM_NEG, st->Zhat, A_out, R_out, z_out);
+    double zt = oracle_forces(st, st->t, STREAM_REFINE, st->Zhat, A_out, R_out, z_out);
     double exag = (st->t < (uint32_t)st->exag_iters) ? st->exaggeration : 1.0;
     for (int64_t e = 0; e < N * d; ++e) {
         double g = st->att_ratio * exag * A_out[e] - st->rep_ratio * R_out[e];

@@ -17,7 +17,7 @@ __all__ = ["lib", "philox", "OracleState", "bisect", "entropy", "topk_merge",
 
 ORACLE_BISECT_TOL = 1e-9
 ORACLE_BISECT_MAXIT = 200
-STREAMS = dict(COIN=0, REFINE=1, NEG=3, MLP=4, INSERT=5, INIT_HD=6, INIT_LD=7,
+STREAMS = dict(COIN=0, REFINE=1, MLP=4, INSERT=5, INIT_HD=6, INIT_LD=7,
                INIT_Y=8, ZINIT=9)
 CAND_HD = 32
 CAND_LD = 32
@@ -267,7 +267,7 @@ class OracleState:
         lib().oracle_ld_candidates(C.byref(self._s), int(i), _p(out, _lp))
         return out
 
-    def forces(self, zhat=None, t=None, stream=STREAMS["NEG"]):
+    def forces(self, zhat=None, t=None, stream=STREAMS["REFINE"]):
         """Returns (A, R, Z_t, z per point) for the current lists, P and Y."""
         A = np.zeros_like(self.Y)
         R = np.zeros_like(self.Y)

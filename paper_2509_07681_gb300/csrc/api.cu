@@ -50,8 +50,8 @@ struct funcsne {
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
-    int step_blocks = 0, update_blocks = 0;
-    size_t step_smem = 0;
+    int hd_blocks = 0, ld_blocks = 0, fo_blocks = 0, update_blocks = 0;
+    size_t hd_smem = 0, ld_smem = 0, fo_smem = 0;
     cudaGraphExec_t graph1 = nullptr, graph8 = nullptr;
     std::string err;
 };
@@ -147,7 +147,8 @@ StepParams step_params(const funcsne* h) {
 UpdateParams update_params(const funcsne* h, float* dbg_att, float* dbg_rep) {
     UpdateParams u{};
     u.n_elem = h->yelem;
-    u.n_zpart = h->step_blocks;
+    u.n_zpart = h->fo_blocks;
+    u.n_cnt = h->hd_blocks;
     u.hd_mode = h->hd_mode;
     u.N = h->N;
     u.lr = static_cast<float>(h->lr);
@@ -169,30 +170,47 @@ UpdateParams update_params(const funcsne* h, float* dbg_att, float* dbg_rep) {
     return u;
 }
 
-cudaError_t launch_step_kernel(const funcsne* h, const StepParams& p, cudaStream_t s) {
-    switch (h->precision) {
-        case FUNCSNE_FP32: return step_launch_f32(p, h->DP, h->RH, h->step_blocks, h->step_smem, s);
-        case FUNCSNE_BF16: return step_launch_bf16(p, h->DP, h->RH, h->step_blocks, h->step_smem, s);
-        default: return step_launch_fp8(p, h->DP, h->RH, h->step_blocks, h->step_smem, s);
+// The phase kernels of one iteration: 0 HD refinement, 1 LD refinement,
+// 2 forces, 3 update.
+constexpr int kPhases = 4;
+
+cudaError_t launch_phase(const funcsne* h, int phase, const StepParams& p, cudaStream_t s) {
+    switch (phase) {
+        case 0:
+            switch (h->precision) {
+                case FUNCSNE_FP32: return hd_refine_launch_f32(p, h->RH, h->hd_blocks, h->hd_smem, s);
+                case FUNCSNE_BF16: return hd_refine_launch_bf16(p, h->RH, h->hd_blocks, h->hd_smem, s);
+                default: return hd_refine_launch_fp8(p, h->RH, h->hd_blocks, h->hd_smem, s);
+            }
+        case 1: return ld_refine_launch(p, h->DP, h->RH, h->ld_blocks, h->ld_smem, s);
+        case 2: return forces_launch(p, h->DP, h->RH, h->fo_blocks, h->fo_smem, s);
+        default: return update_launch(update_params(h, nullptr, nullptr), h->update_blocks, s);
     }
 }
 
-// Grid of the step kernel: resident blocks per SM x SMs (persistent warps).
-int configure_step(funcsne* h) {
-    h->step_smem = static_cast<size_t>(8) * (h->xs_floats * 4 + kHashSlots * 4);
-    int occ = 0;
-    switch (h->precision) {
-        case FUNCSNE_FP32: occ = step_occupancy_f32(h->DP, h->RH, h->step_smem); break;
-        case FUNCSNE_BF16: occ = step_occupancy_bf16(h->DP, h->RH, h->step_smem); break;
-        default: occ = step_occupancy_fp8(h->DP, h->RH, h->step_smem); break;
-    }
+// Persistent grids: resident blocks per SM x SMs, at most one warp per point.
+int grid_for_occupancy(const funcsne* h, int occ) {
     if (occ < 1) occ = 1;
     int64_t blocks = static_cast<int64_t>(occ) * h->num_sms;
     const int64_t need = (h->N + 7) / 8;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     if (blocks > h->max_blocks) blocks = h->max_blocks;
-    h->step_blocks = static_cast<int>(blocks);
+    return static_cast<int>(blocks);
+}
+
+int configure_step(funcsne* h) {
+    h->hd_smem = static_cast<size_t>(8) * (h->xs_floats * 4 + kHashSlots * 4);
+    h->ld_smem = h->fo_smem = static_cast<size_t>(8) * kHashSlots * 4;
+    int occ = 0;
+    switch (h->precision) {
+        case FUNCSNE_FP32: occ = hd_refine_occupancy_f32(h->RH, h->hd_smem); break;
+        case FUNCSNE_BF16: occ = hd_refine_occupancy_bf16(h->RH, h->hd_smem); break;
+        default: occ = hd_refine_occupancy_fp8(h->RH, h->hd_smem); break;
+    }
+    h->hd_blocks = grid_for_occupancy(h, occ);
+    h->ld_blocks = grid_for_occupancy(h, ld_refine_occupancy(h->DP, h->RH, h->ld_smem));
+    h->fo_blocks = grid_for_occupancy(h, forces_occupancy(h->DP, h->RH, h->fo_smem));
     int64_t ub = (h->yelem / 4 + 255) / 256;
     if (ub > 4L * h->num_sms) ub = 4L * h->num_sms;
     if (ub < 1) ub = 1;
@@ -203,7 +221,7 @@ int configure_step(funcsne* h) {
 
 int enqueue_iteration(funcsne* h, cudaStream_t s, float* dbg_att, float* dbg_rep) {
     const StepParams p = step_params(h);
-    FSNE_CUDA(h, launch_step_kernel(h, p, s));
+    for (int ph = 0; ph < 3; ++ph) FSNE_CUDA(h, launch_phase(h, ph, p, s));
     FSNE_CUDA(h, update_launch(update_params(h, dbg_att, dbg_rep), h->update_blocks, s));
     return FUNCSNE_OK;
 }
@@ -214,13 +232,12 @@ int build_graph(funcsne* h, int iters, cudaGraphExec_t* out) {
     FSNE_CUDA(h, cudaStreamBeginCapture(h->own_stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < iters; ++k) {
         const StepParams p = step_params(h);
-        cudaError_t e1 = launch_step_kernel(h, p, h->own_stream);
-        cudaError_t e2 = update_launch(update_params(h, nullptr, nullptr), h->update_blocks, h->own_stream);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaError_t e = cudaSuccess;
+        for (int ph = 0; ph < kPhases && e == cudaSuccess; ++ph) e = launch_phase(h, ph, p, h->own_stream);
+        if (e != cudaSuccess) {
             cudaStreamEndCapture(h->own_stream, &g);
             if (g) cudaGraphDestroy(g);
-            return fail(h, FUNCSNE_E_CUDA, "graph capture: %s",
-                        cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+            return fail(h, FUNCSNE_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
         }
     }
     FSNE_CUDA(h, cudaStreamEndCapture(h->own_stream, &g));
@@ -579,7 +596,9 @@ int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
     else if (k == "hd_mode") *v = h->hd_mode;
     else if (k == "alpha") *v = h->alpha;
     else if (k == "precision") *v = h->precision;
-    else if (k == "step_blocks") *v = h->step_blocks;
+    else if (k == "hd_blocks") *v = h->hd_blocks;
+    else if (k == "ld_blocks") *v = h->ld_blocks;
+    else if (k == "forces_blocks") *v = h->fo_blocks;
     else return fail(h, FUNCSNE_E_ARG, "unknown option '%s'", key);
     return FUNCSNE_OK;
 }
@@ -858,36 +877,35 @@ int funcsne_debug_step(funcsne_t* h, float* att, float* rep) {
     return check_errors(h);
 }
 
-int funcsne_profile_step(funcsne_t* h, int32_t n_iters, double* ms_step, double* ms_update) {
-    if (!h || !ms_step || !ms_update) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+int funcsne_profile_step(funcsne_t* h, int32_t n_iters, double* ms_per_kernel) {
+    if (!h || !ms_per_kernel) return fail(h, FUNCSNE_E_ARG, "NULL argument");
     if (n_iters < 1) return fail(h, FUNCSNE_E_ARG, "n_iters must be >= 1");
-    std::vector<cudaEvent_t> ev(static_cast<size_t>(3 * n_iters), nullptr);
+    const int ne = kPhases + 1;
+    std::vector<cudaEvent_t> ev(static_cast<size_t>(ne) * n_iters, nullptr);
     for (auto& e : ev) FSNE_CUDA(h, cudaEventCreate(&e));
     int rc = FUNCSNE_OK;
     for (int k = 0; k < n_iters && rc == FUNCSNE_OK; ++k) {
         const StepParams p = step_params(h);
-        cudaError_t e = cudaEventRecord(ev[3 * k], h->stream);
-        if (e == cudaSuccess) e = launch_step_kernel(h, p, h->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[3 * k + 1], h->stream);
-        if (e == cudaSuccess) e = update_launch(update_params(h, nullptr, nullptr), h->update_blocks, h->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[3 * k + 2], h->stream);
-        if (e != cudaSuccess) rc = fail(h, FUNCSNE_E_CUDA, "profile_step: %s", cudaGetErrorString(e));
-    }
-    double a = 0.0, b = 0.0;
-    if (rc == FUNCSNE_OK) {
-        cudaError_t e = cudaStreamSynchronize(h->stream);
-        for (int k = 0; k < n_iters && e == cudaSuccess; ++k) {
-            float x = 0.f, y = 0.f;
-            e = cudaEventElapsedTime(&x, ev[3 * k], ev[3 * k + 1]);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&y, ev[3 * k + 1], ev[3 * k + 2]);
-            a += x;
-            b += y;
+        cudaError_t e = cudaEventRecord(ev[ne * k], h->stream);
+        for (int ph = 0; ph < kPhases && e == cudaSuccess; ++ph) {
+            e = launch_phase(h, ph, p, h->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[ne * k + ph + 1], h->stream);
         }
         if (e != cudaSuccess) rc = fail(h, FUNCSNE_E_CUDA, "profile_step: %s", cudaGetErrorString(e));
     }
+    double acc[kPhases] = {0.0, 0.0, 0.0, 0.0};
+    if (rc == FUNCSNE_OK) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        for (int k = 0; k < n_iters && e == cudaSuccess; ++k)
+            for (int ph = 0; ph < kPhases && e == cudaSuccess; ++ph) {
+                float x = 0.f;
+                e = cudaEventElapsedTime(&x, ev[ne * k + ph], ev[ne * k + ph + 1]);
+                acc[ph] += x;
+            }
+        if (e != cudaSuccess) rc = fail(h, FUNCSNE_E_CUDA, "profile_step: %s", cudaGetErrorString(e));
+    }
     for (auto& e : ev) cudaEventDestroy(e);
-    *ms_step = a;
-    *ms_update = b;
+    for (int ph = 0; ph < kPhases; ++ph) ms_per_kernel[ph] = acc[ph];
     return rc;
 }
 

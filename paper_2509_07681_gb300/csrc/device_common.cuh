@@ -86,6 +86,18 @@ __device__ __forceinline__ T warp_get(const T (&v)[R], uint32_t e) {
     return out;
 }
 
+template <int R>
+__device__ __forceinline__ uint64_t warp_get64(const uint64_t (&v)[R], uint32_t e) {
+    uint64_t out = v[0];
+    const int src = static_cast<int>(e & 31u);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint64_t x = shfl64(v[r], src);
+        if (static_cast<uint32_t>(r) == (e >> 5)) out = x;
+    }
+    return out;
+}
+
 // ---------------------------------------------------------------- bitonic networks
 // Ascending sort of 32*R keys held as element e = r*32 + lane.
 template <int R>
@@ -148,6 +160,66 @@ __device__ __forceinline__ void merge_candidates(uint64_t (&old)[R], uint64_t ca
         warp_bitonic_merge<2>(m, lane);
         old[0] = m[0];
         old[1] = m[1];
+    }
+}
+
+__device__ __forceinline__ uint64_t shfl_up64(uint64_t v, int d) {
+    const uint32_t lo = __shfl_up_sync(kFull, static_cast<uint32_t>(v), d);
+    const uint32_t hi = __shfl_up_sync(kFull, static_cast<uint32_t>(v >> 32), d);
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+__device__ __forceinline__ uint64_t shfl_down64(uint64_t v, int d) {
+    const uint32_t lo = __shfl_down_sync(kFull, static_cast<uint32_t>(v), d);
+    const uint32_t hi = __shfl_down_sync(kFull, static_cast<uint32_t>(v >> 32), d);
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+
+// Inserts the candidate keys that precede thr (one per lane) into a sorted
+// warp list of 32*R keys, one at a time: each insertion finds its position by
+// a ballot and shifts the tail up by one element. Afterwards the first k
+// entries are the k smallest of (list, candidates) whenever thr is the
+// list's k-th key. Cheap when few candidates qualify.
+template <int R>
+__device__ __forceinline__ void insert_candidates(uint64_t (&lst)[R], uint64_t cand, uint64_t thr, int lane) {
+    unsigned m = __ballot_sync(kFull, cand < thr);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const uint64_t c = shfl64(cand, src);
+        int pos = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) pos += __popc(__ballot_sync(kFull, lst[r] < c));
+        uint64_t prev[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t up = shfl_up64(lst[r], 1);
+            const uint64_t tail = r > 0 ? shfl64(lst[r > 0 ? r - 1 : 0], 31) : up;
+            prev[r] = lane == 0 ? tail : up;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = r * 32 + lane;
+            lst[r] = e < pos ? lst[r] : (e == pos ? c : prev[r]);
+        }
+    }
+}
+
+// Sorts one key per lane ascending by odd-even transposition, stopping as
+// soon as the list is sorted (a list that was sorted at the previous
+// iteration usually needs no pass or one). At most 32 passes.
+__device__ __forceinline__ void warp_sort_nearly_sorted(uint64_t& k, int lane) {
+    for (int pass = 0; pass < 32; ++pass) {
+        const uint64_t nxt = shfl_down64(k, 1);
+        if (__all_sync(kFull, lane == 31 || k <= nxt)) return;
+#pragma unroll
+        for (int ph = 0; ph < 2; ++ph) {
+            // pairs (2m + ph, 2m + ph + 1)
+            const bool low = ((lane - ph) & 1) == 0;
+            const int partner = low ? lane + 1 : lane - 1;
+            const bool has = partner >= 0 && partner < 32;
+            const uint64_t o = shfl64(k, has ? partner : lane);
+            if (has) k = low ? (k < o ? k : o) : (k < o ? o : k);
+        }
     }
 }
 
@@ -431,16 +503,17 @@ __device__ __forceinline__ float warp_bisect(const float (&d2)[R], int k, float 
             U += __shfl_xor_sync(kFull, U, m);
             V += __shfl_xor_sync(kFull, V, m);
         }
-        const float mu = U / S;
-        const float H = logf(S) + beta * mu;
+        const float invS = __fdividef(1.f, S);
+        const float mu = U * invS;
+        const float H = __logf(S) + beta * mu;
         const float f = H - log_perp;
         if (fabsf(f) < kBisectTol) break;
         if (f > 0.f)
             lo = beta;
         else
             hi = beta;
-        const float slope = -beta * (V / S - mu * mu);
-        float nxt = beta - f / slope;
+        const float slope = -beta * (V * invS - mu * mu);
+        float nxt = beta - __fdividef(f, slope);
         if (!(slope < 0.f) || !(nxt > lo) || !(nxt < hi)) nxt = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
         beta = nxt;
     }
@@ -456,6 +529,18 @@ __device__ __forceinline__ float warp_bisect(const float (&d2)[R], int k, float 
 #pragma unroll
     for (int r = 0; r < R; ++r) p[r] *= invS;
     return beta;
+}
+
+// Negative sample s of a point: the MurmurHash3 finalizer (fmix32) of words
+// 1 and 3 of the point's Philox block for slot s mod 32, salted by s div 32.
+__device__ __forceinline__ uint32_t negative_word(uint32_t w1, uint32_t w3, uint32_t pass) {
+    uint32_t h = w1 ^ (w3 + (pass + 1u) * 0x9E3779B9u);
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
 }
 
 // Coin of iteration t: HD refinement iff u < 0.05 + 0.95 E (FP64, explicit

@@ -193,9 +193,9 @@ __global__ void __launch_bounds__(256) zinit_kernel(ZinitParams z) {
             for (int m = 0; m < z.k_hd; ++m) in_hd |= (s_list[wib][m] == j);
             if (!in_hd) zi += wfun(j);
         }
+        const uint4 w = philox(z.t, i, z.stream, static_cast<uint32_t>(lane), z.seed);
         for (int s = lane; s < z.n_neg; s += 32) {
-            const uint4 w = philox(z.t, i, z.stream, static_cast<uint32_t>(s), z.seed);
-            const int32_t j = static_cast<int32_t>(map_other(w.x, N, i));
+            const int32_t j = static_cast<int32_t>(map_other(negative_word(w.y, w.w, static_cast<uint32_t>(s >> 5)), N, i));
             bool in_s = false;
             for (int m = 0; m < z.k_hd; ++m) in_s |= (s_list[wib][m] == j);
             for (int m = 0; m < z.k_ld; ++m) in_s |= (s_list[wib][64 + m] == j);

@@ -62,13 +62,18 @@ struct InsertParams {
     float* beta;
 };
 
-// step kernels, one translation unit per HD storage precision
-cudaError_t step_launch_f32(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
-cudaError_t step_launch_bf16(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
-cudaError_t step_launch_fp8(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
-int step_occupancy_f32(int DP, int RH, size_t smem);
-int step_occupancy_bf16(int DP, int RH, size_t smem);
-int step_occupancy_fp8(int DP, int RH, size_t smem);
+// phase kernels of the iteration (HD refinement: one translation unit per
+// HD storage precision)
+cudaError_t hd_refine_launch_f32(const StepParams& p, int RH, int blocks, size_t smem, cudaStream_t s);
+cudaError_t hd_refine_launch_bf16(const StepParams& p, int RH, int blocks, size_t smem, cudaStream_t s);
+cudaError_t hd_refine_launch_fp8(const StepParams& p, int RH, int blocks, size_t smem, cudaStream_t s);
+int hd_refine_occupancy_f32(int RH, size_t smem);
+int hd_refine_occupancy_bf16(int RH, size_t smem);
+int hd_refine_occupancy_fp8(int RH, size_t smem);
+cudaError_t ld_refine_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
+cudaError_t forces_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
+int ld_refine_occupancy(int DP, int RH, size_t smem);
+int forces_occupancy(int DP, int RH, size_t smem);
 cudaError_t update_launch(const UpdateParams& u, int blocks, cudaStream_t s);
 
 // set-up

@@ -12,7 +12,6 @@ constexpr uint32_t kStreamCoin = 0;
 // One block per (iteration, point, slot) drives both refinements: words 0-1
 // the HD candidate of slot s, words 2-3 the LD candidate of slot s.
 constexpr uint32_t kStreamRefine = 1;
-constexpr uint32_t kStreamNeg = 3;
 constexpr uint32_t kStreamMlp = 4;
 constexpr uint32_t kStreamInsert = 5;
 constexpr uint32_t kStreamInitHd = 6;
@@ -89,13 +88,14 @@ struct StepParams {
     float* P;
     float* beta;
     DevScalars* sc;
-    double* zpart;               // one FP64 partial of Z_t per block
-    unsigned long long* cnt;     // per-block counters: n_new, scored, reranked
+    double* zpart;               // one FP64 partial of Z_t per forces block
+    unsigned long long* cnt;     // per HD-refinement block: n_new, scored, reranked
 };
 
 struct UpdateParams {
     int64_t n_elem;       // N * DP
-    int32_t n_zpart;      // blocks of the step kernel
+    int32_t n_zpart;      // blocks of the forces kernel (Z partials)
+    int32_t n_cnt;        // blocks of the HD refinement kernel (counters)
     int32_t hd_mode;
     int64_t N;
     float lr, momentum, att, rep, exaggeration;

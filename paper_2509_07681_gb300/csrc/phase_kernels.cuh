@@ -1,0 +1,426 @@
+// The FUnc-SNE iteration as three phase kernels (one warp per point,
+// persistent grids) plus the update kernel (update_kernel.cu).
+//
+// Iteration t, Jacobi order (all reads see state t; writes go to the t+1
+// list buffers, to P/beta of the point itself, or to accumulators):
+//   hd_refine_kernel  (Section 3) when the coin of t fires: 32 candidates
+//     (slots 0-15 HD neighbour of an HD neighbour, 16-19 LD neighbour,
+//     20-23 LD neighbour of an LD neighbour, 24-31 random; words 0-1 of the
+//     slot's Philox block), dedup against the list / self / earlier slots,
+//     FP32 distances (or dequantised BF16 / FP8 distances with an error band
+//     and an exact FP32 re-rank of every candidate that can enter), top-k on
+//     (d2, idx), new-neighbour flag, warm-restart bandwidth calibration;
+//   ld_refine_kernel  every iteration: 32 candidates (slots 0-15 LD
+//     neighbour of an LD neighbour, 16-23 HD neighbour of iteration t, 24-31
+//     random; words 2-3), distances at Y_t of the old list and the
+//     candidates, top-k_ld on (d2, idx);
+//   forces_kernel     over the lists of t+1 at Y_t: attraction
+//     4 (p_{j|i}/2N) w^{1/alpha} (y_i - y_j) added to A_i and subtracted from
+//     A_j; repulsion 4 (w_ij / Zhat_t) w^{1/alpha} (y_i - y_j) over
+//     S_i = HD u LD and over n_neg Philox-seeded negatives outside S_i
+//     scaled by (N-1)/n_neg; per-point Z_t terms summed per block in FP64.
+// hd_refine and ld_refine only read state t, so they may run concurrently.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace fsne {
+
+constexpr int kWarpsPerBlock = 8;
+// Up to this many qualifying candidates are merged by single insertions;
+// more go through the bitonic network.
+constexpr int kInsertMax = 12;
+
+struct ListView {
+    const int32_t* __restrict__ hd_idx_c;
+    const float* __restrict__ hd_d2_c;
+    int32_t* __restrict__ hd_idx_n;
+    float* __restrict__ hd_d2_n;
+    const int32_t* __restrict__ ld_idx_c;
+    int32_t* __restrict__ ld_idx_n;
+};
+
+__device__ __forceinline__ ListView list_view(const StepParams& p, int hc, int lc) {
+    ListView v;
+    v.hd_idx_c = hc ? p.hd_idx1 : p.hd_idx0;
+    v.hd_d2_c = hc ? p.hd_d21 : p.hd_d20;
+    v.hd_idx_n = hc ? p.hd_idx0 : p.hd_idx1;
+    v.hd_d2_n = hc ? p.hd_d20 : p.hd_d21;
+    v.ld_idx_c = lc ? p.ld_idx1 : p.ld_idx0;
+    v.ld_idx_n = lc ? p.ld_idx0 : p.ld_idx1;
+    return v;
+}
+
+// ------------------------------------------------------------------ HD refinement
+template <int RH, int XM>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+hd_refine_kernel(const StepParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    float* xs = reinterpret_cast<float*>(smem + wib * p.smem_per_warp);
+    uint32_t* tab = reinterpret_cast<uint32_t*>(xs + p.xs_floats);
+    __shared__ unsigned long long s_cnt[kWarpsPerBlock][3];
+
+    const DevScalars* sc = p.sc;
+    const uint32_t t = sc->t;
+    if (!hd_coin(t, sc->E, p.seed, p.hd_mode)) return;  // uniform over the grid
+    const ListView L = list_view(p, sc->hd_cur, sc->ld_cur);
+    const uint32_t N = static_cast<uint32_t>(p.N);
+    const int k_hd = p.k_hd, k_ld = p.k_ld;
+
+    for (int f = p.xpitch + lane; f < p.xs_floats; f += 32) xs[f] = 0.f;
+    unsigned long long c_new = 0, c_scored = 0, c_rerank = 0;
+
+    const int64_t tw = static_cast<int64_t>(gridDim.x) * kWarpsPerBlock;
+    for (int64_t gi = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + wib; gi < p.N; gi += tw) {
+        const uint32_t i = static_cast<uint32_t>(gi);
+        uint32_t hidx[RH];
+        float hd2[RH];
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            const int e = r * 32 + lane;
+            hidx[r] = e < k_hd ? static_cast<uint32_t>(__ldg(L.hd_idx_c + gi * k_hd + e)) : 0xffffffffu;
+            hd2[r] = e < k_hd ? __ldg(L.hd_d2_c + gi * k_hd + e) : __uint_as_float(0x7f800000u);
+        }
+        const uint32_t lidx = lane < k_ld ? static_cast<uint32_t>(__ldg(L.ld_idx_c + gi * k_ld + lane)) : 0xffffffffu;
+        const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+        __syncwarp();
+        const float* xrow = p.X32 + gi * p.xpitch;
+        for (int f = lane * 4; f < p.xpitch; f += 128)
+            *reinterpret_cast<float4*>(xs + f) = __ldg(reinterpret_cast<const float4*>(xrow + f));
+        hset_clear(tab, lane);
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < RH; ++r)
+            if (r * 32 + lane < k_hd) hset_insert(tab, hidx[r]);
+        const uint32_t e0 = lane < kHdNnEnd ? map_index(w.x, k_hd) : map_index(w.x, k_ld);
+        const uint32_t hv = warp_get<RH>(hidx, e0);
+        const uint32_t lv = __shfl_sync(kFull, lidx, static_cast<int>(e0 & 31u));
+        uint32_t c;
+        if (lane < kHdNnEnd)
+            c = static_cast<uint32_t>(__ldg(L.hd_idx_c + static_cast<int64_t>(hv) * k_hd + map_index(w.y, k_hd)));
+        else if (lane < kHdLdNbEnd)
+            c = lv;
+        else if (lane < kHdLdNnEnd)
+            c = static_cast<uint32_t>(__ldg(L.ld_idx_c + static_cast<int64_t>(lv) * k_ld + map_index(w.y, k_ld)));
+        else
+            c = map_other(w.x, N, i);
+        __syncwarp();
+        bool valid = (c != i) && (c < N) && !hset_has(tab, c);
+        valid &= (__match_any_sync(kFull, c) & ((1u << lane) - 1u)) == 0u;
+
+        uint64_t ck = kSentinel;
+        if constexpr (XM == 0) {
+            if (valid) ck = make_key(dist_f32(xs, p.X32 + static_cast<int64_t>(c) * p.xpitch, p.n4), c);
+        } else {
+            const float thr = warp_get<RH>(hd2, static_cast<uint32_t>(k_hd - 1));
+            bool need = false;
+            if (valid) {
+                ApproxDist a;
+                if constexpr (XM == 1)
+                    a = dist_bf16(xs, reinterpret_cast<const uint16_t*>(p.Xq + static_cast<int64_t>(c) * p.qpitch),
+                                  p.nq, p.q_u, p.q_gamma);
+                else
+                    a = dist_fp8(xs, p.Xq + static_cast<int64_t>(c) * p.qpitch, p.nq, p.qscale_off, p.q_u,
+                                 p.q_a, p.q_gamma);  // nq = code words for FP8
+                need = __fsub_rd(a.d2, a.band) <= thr;
+                ++c_scored;
+            }
+            if (need) {
+                ++c_rerank;
+                ck = make_key(dist_f32(xs, p.X32 + static_cast<int64_t>(c) * p.xpitch, p.n4), c);
+            }
+        }
+        // flag: some candidate precedes the old k-th entry
+        uint64_t keys[RH];
+#pragma unroll
+        for (int r = 0; r < RH; ++r) keys[r] = (r * 32 + lane < k_hd) ? make_key(hd2[r], hidx[r]) : kSentinel;
+        const uint64_t kth = warp_get64<RH>(keys, static_cast<uint32_t>(k_hd - 1));
+        const int nqual = __popc(__ballot_sync(kFull, ck < kth));
+        if (nqual > 0) {
+            if (nqual > kInsertMax)
+                merge_candidates<RH>(keys, ck, lane);
+            else
+                insert_candidates<RH>(keys, ck, kth, lane);
+        }
+        float nd2[RH];
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            const int e = r * 32 + lane;
+            nd2[r] = key_d2(keys[r]);
+            if (e < k_hd) {
+                L.hd_idx_n[gi * k_hd + e] = static_cast<int32_t>(key_idx(keys[r]));
+                L.hd_d2_n[gi * k_hd + e] = nd2[r];
+            }
+        }
+        if (nqual > 0) {
+            float pv[RH];
+            const float b = warp_bisect<RH>(nd2, k_hd, p.log_perp, p.beta[gi], pv, lane);
+#pragma unroll
+            for (int r = 0; r < RH; ++r) {
+                const int e = r * 32 + lane;
+                if (e < k_hd) p.P[gi * k_hd + e] = pv[r];
+            }
+            if (lane == 0) p.beta[gi] = b;
+            ++c_new;
+        }
+        __syncwarp();
+    }
+    unsigned long long cs = c_scored, cr = c_rerank;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+        cs += __shfl_xor_sync(kFull, cs, m);
+        cr += __shfl_xor_sync(kFull, cr, m);
+    }
+    if (lane == 0) {
+        s_cnt[wib][0] = c_new;
+        s_cnt[wib][1] = cs;
+        s_cnt[wib][2] = cr;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, b = 0, c = 0;
+        for (int v = 0; v < kWarpsPerBlock; ++v) {
+            a += s_cnt[v][0];
+            b += s_cnt[v][1];
+            c += s_cnt[v][2];
+        }
+        p.cnt[3 * blockIdx.x + 0] = a;
+        p.cnt[3 * blockIdx.x + 1] = b;
+        p.cnt[3 * blockIdx.x + 2] = c;
+    }
+}
+
+// ------------------------------------------------------------------ LD refinement
+template <int DP, int RH>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+ld_refine_kernel(const StepParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint32_t* tab = reinterpret_cast<uint32_t*>(smem) + wib * kHashSlots;
+
+    const DevScalars* sc = p.sc;
+    const uint32_t t = sc->t;
+    const ListView L = list_view(p, sc->hd_cur, sc->ld_cur);
+    const uint32_t N = static_cast<uint32_t>(p.N);
+    const int k_hd = p.k_hd, k_ld = p.k_ld;
+    const float* __restrict__ Y = p.Y;
+
+    const int64_t tw = static_cast<int64_t>(gridDim.x) * kWarpsPerBlock;
+    for (int64_t gi = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + wib; gi < p.N; gi += tw) {
+        const uint32_t i = static_cast<uint32_t>(gi);
+        uint32_t hidx[RH];
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            const int e = r * 32 + lane;
+            hidx[r] = e < k_hd ? static_cast<uint32_t>(__ldg(L.hd_idx_c + gi * k_hd + e)) : 0xffffffffu;
+        }
+        const uint32_t lidx = lane < k_ld ? static_cast<uint32_t>(__ldg(L.ld_idx_c + gi * k_ld + lane)) : 0xffffffffu;
+        float yi[DP];
+        load_row<DP>(Y + gi * DP, yi);
+        const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+        hset_clear(tab, lane);
+        __syncwarp();
+        if (lane < k_ld) hset_insert(tab, lidx);
+        const uint32_t e0 = lane < kLdNnEnd ? map_index(w.z, k_ld) : map_index(w.z, k_hd);
+        const uint32_t lv = __shfl_sync(kFull, lidx, static_cast<int>(e0 & 31u));
+        const uint32_t hv = warp_get<RH>(hidx, e0);
+        uint32_t c;
+        if (lane < kLdNnEnd)
+            c = static_cast<uint32_t>(__ldg(L.ld_idx_c + static_cast<int64_t>(lv) * k_ld + map_index(w.w, k_ld)));
+        else if (lane < kLdHdNbEnd)
+            c = hv;
+        else
+            c = map_other(w.z, N, i);
+        __syncwarp();
+        bool valid = (c != i) && (c < N) && !hset_has(tab, c);
+        valid &= (__match_any_sync(kFull, c) & ((1u << lane) - 1u)) == 0u;
+        uint64_t lk[1] = {kSentinel};
+        uint64_t ck = kSentinel;
+        if (lane < k_ld) {
+            float yo[DP];
+            load_row<DP>(Y + static_cast<int64_t>(lidx) * DP, yo);
+            lk[0] = make_key(sqdist_ld<DP>(yi, yo), lidx);
+        }
+        if (valid) {
+            float yc[DP];
+            load_row<DP>(Y + static_cast<int64_t>(c) * DP, yc);
+            ck = make_key(sqdist_ld<DP>(yi, yc), c);
+        }
+        // the old list ordered under the distances at Y_t, then the candidates
+        warp_sort<1>(lk, lane);
+        const uint64_t thr = shfl64(lk[0], k_ld - 1);
+        const int nqual = __popc(__ballot_sync(kFull, ck < thr));
+        if (nqual > kInsertMax)
+            merge_candidates<1>(lk, ck, lane);
+        else if (nqual > 0)
+            insert_candidates<1>(lk, ck, thr, lane);
+        if (lane < k_ld) L.ld_idx_n[gi * k_ld + lane] = static_cast<int32_t>(key_idx(lk[0]));
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ forces
+// Per-lane interaction with point j: returns w and w^{1/alpha} and the
+// difference vector y_i - y_j.
+template <int DP>
+__device__ __forceinline__ void interaction(const float (&yi)[DP], const float* __restrict__ yrow, float inv_alpha,
+                                            float alpha, float (&dy)[DP], float& w, float& winv) {
+    float yj[DP];
+    load_row<DP>(yrow, yj);
+    float r2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < DP; ++c) {
+        dy[c] = __fsub_rn(yi[c], yj[c]);
+        r2 = __fmaf_rn(dy[c], dy[c], r2);
+    }
+    winv = __fdividef(1.f, __fmaf_rn(r2, inv_alpha, 1.f));
+    w = alpha == 1.f ? winv : exp2f(alpha * __log2f(winv));
+}
+
+template <int DP>
+constexpr int forces_min_blocks() { return DP >= 32 ? 2 : 3; }
+
+template <int DP, int RH>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, forces_min_blocks<DP>())
+forces_kernel(const StepParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint32_t* tab = reinterpret_cast<uint32_t*>(smem) + wib * kHashSlots;
+    __shared__ double s_z[kWarpsPerBlock];
+
+    const DevScalars* sc = p.sc;
+    const uint32_t t = sc->t;
+    const bool fire = hd_coin(t, sc->E, p.seed, p.hd_mode);
+    // lists of iteration t+1: the HD buffer flips only when the coin fired
+    const int32_t* __restrict__ hd_new = (sc->hd_cur ^ (fire ? 1 : 0)) ? p.hd_idx1 : p.hd_idx0;
+    const int32_t* __restrict__ ld_new = sc->ld_cur ? p.ld_idx0 : p.ld_idx1;
+    const float invZ = static_cast<float>(1.0 / sc->Zhat);
+    const uint32_t N = static_cast<uint32_t>(p.N);
+    const int k_hd = p.k_hd, k_ld = p.k_ld;
+    const float* __restrict__ Y = p.Y;
+    const float alpha = p.alpha, inv_alpha = p.inv_alpha;
+    constexpr int RO = DP <= 16 ? 16 : DP;
+    constexpr int NACC = DP <= 4 ? RO + DP : 2 * RO;
+
+    double z_acc = 0.0;
+    const int64_t tw = static_cast<int64_t>(gridDim.x) * kWarpsPerBlock;
+    for (int64_t gi = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + wib; gi < p.N; gi += tw) {
+        const uint32_t i = static_cast<uint32_t>(gi);
+        uint32_t nh[RH];
+        float pv[RH];
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            const int e = r * 32 + lane;
+            nh[r] = e < k_hd ? static_cast<uint32_t>(__ldg(hd_new + gi * k_hd + e)) : 0xffffffffu;
+            pv[r] = e < k_hd ? p.P[gi * k_hd + e] : 0.f;
+        }
+        const uint32_t nl = lane < k_ld ? static_cast<uint32_t>(__ldg(ld_new + gi * k_ld + lane)) : 0xffffffffu;
+        float yi[DP];
+        load_row<DP>(Y + gi * DP, yi);
+        const uint4 wq = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+        // S_i = HD u LD lists of t+1 as a warp hash set
+        hset_clear(tab, lane);
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < RH; ++r)
+            if (r * 32 + lane < k_hd) hset_insert(tab, nh[r]);
+        __syncwarp();
+        const bool ld_in_hd = lane < k_ld && hset_has(tab, nl);
+        __syncwarp();
+        if (lane < k_ld) hset_insert(tab, nl);
+        __syncwarp();
+
+        // attraction components in acc[0..DP), repulsion in acc[RO..RO+DP)
+        float acc[NACC];
+#pragma unroll
+        for (int c = 0; c < NACC; ++c) acc[c] = 0.f;
+        float z = 0.f;
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            if (r * 32 + lane < k_hd) {
+                float dy[DP], w, winv;
+                interaction<DP>(yi, Y + static_cast<int64_t>(nh[r]) * DP, inv_alpha, alpha, dy, w, winv);
+                const float fa = 4.f * pv[r] * p.inv2N * winv;
+                const float fr = 4.f * w * invZ * winv;
+#pragma unroll
+                for (int c = 0; c < DP; ++c) {
+                    acc[c] = __fmaf_rn(fa, dy[c], acc[c]);
+                    acc[RO + c] = __fmaf_rn(fr, dy[c], acc[RO + c]);
+                }
+                z += w;
+                atomic_add_row<DP>(p.A + static_cast<int64_t>(nh[r]) * DP, dy, -fa);
+            }
+        }
+        // repulsion from LD neighbours outside the HD list, then from the negatives
+        const int n_pass = 1 + (p.n_neg + 31) / 32;
+        for (int pass = 0; pass < n_pass; ++pass) {
+            uint32_t j;
+            float scale;
+            bool on;
+            if (pass == 0) {
+                j = nl;
+                scale = 1.f;
+                on = lane < k_ld && !ld_in_hd;
+            } else {
+                const int s = (pass - 1) * 32 + lane;
+                j = map_other(negative_word(wq.y, wq.w, static_cast<uint32_t>(pass - 1)), N, i);
+                scale = p.neg_scale;
+                on = s < p.n_neg && !hset_has(tab, j);
+            }
+            if (on) {
+                float dy[DP], w, winv;
+                interaction<DP>(yi, Y + static_cast<int64_t>(j) * DP, inv_alpha, alpha, dy, w, winv);
+                const float fr = scale * 4.f * w * invZ * winv;
+#pragma unroll
+                for (int c = 0; c < DP; ++c) acc[RO + c] = __fmaf_rn(fr, dy[c], acc[RO + c]);
+                z = __fmaf_rn(scale, w, z);
+            }
+        }
+        // warp reductions: the lane owning component c adds A_i[c] and stores R_i[c]
+        if constexpr (DP <= 4) {
+#pragma unroll
+            for (int c = 0; c < NACC; ++c) acc[c] = warp_sum(acc[c]);
+            if (lane < DP) {
+                float a = acc[0], b = acc[RO];
+#pragma unroll
+                for (int c = 1; c < DP; ++c)
+                    if (lane == c) {
+                        a = acc[c];
+                        b = acc[RO + c];
+                    }
+                atomicAdd(p.A + gi * DP + lane, a);
+                p.R[gi * DP + lane] = b;
+            }
+        } else if constexpr (DP == 32) {
+            const float a = warp_reduce_scatter32<0>(acc, lane);
+            const float b = warp_reduce_scatter32<32>(acc, lane);
+            atomicAdd(p.A + gi * DP + lane, a);
+            p.R[gi * DP + lane] = b;
+        } else {
+            const float v = warp_reduce_scatter32(acc, lane);
+            const int c = lane & 15;
+            if (c < DP) {
+                if (lane < 16)
+                    atomicAdd(p.A + gi * DP + c, v);
+                else
+                    p.R[gi * DP + c] = v;
+            }
+        }
+        z = warp_sum(z);
+        z_acc += static_cast<double>(z);
+        __syncwarp();
+    }
+    if (lane == 0) s_z[wib] = z_acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double zb = 0.0;
+        for (int v = 0; v < kWarpsPerBlock; ++v) zb += s_z[v];
+        p.zpart[blockIdx.x] = zb;
+    }
+}
+
+}  // namespace fsne

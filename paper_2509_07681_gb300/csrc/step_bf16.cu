@@ -1,11 +1,11 @@
-// Fused step kernels with BF16 HD rows (FP32 re-rank at the list boundary).
-#include "step_instances.cuh"
+// HD refinement with BF16 rows (FP32 re-rank at the list boundary).
+#include "phase_instances.cuh"
 
 namespace fsne {
 
-cudaError_t step_launch_bf16(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s) {
-    return step_launch_xm<1>(p, DP, RH, blocks, smem, s);
+cudaError_t hd_refine_launch_bf16(const StepParams& p, int RH, int blocks, size_t smem, cudaStream_t s) {
+    return hd_refine_launch_xm<1>(p, RH, blocks, smem, s);
 }
-int step_occupancy_bf16(int DP, int RH, size_t smem) { return step_occupancy_xm<1>(DP, RH, smem); }
+int hd_refine_occupancy_bf16(int RH, size_t smem) { return hd_refine_occupancy_xm<1>(RH, smem); }
 
 }  // namespace fsne

@@ -1,12 +1,64 @@
-// Fused step kernels with FP32 HD rows, and the LD distance read-out.
-#include "step_instances.cuh"
+// Phase kernels: HD refinement with FP32 rows, LD refinement and forces for
+// every LD row width, and the LD distance read-out.
+#include "phase_instances.cuh"
 
 namespace fsne {
 
-cudaError_t step_launch_f32(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s) {
-    return step_launch_xm<0>(p, DP, RH, blocks, smem, s);
+cudaError_t hd_refine_launch_f32(const StepParams& p, int RH, int blocks, size_t smem, cudaStream_t s) {
+    return hd_refine_launch_xm<0>(p, RH, blocks, smem, s);
 }
-int step_occupancy_f32(int DP, int RH, size_t smem) { return step_occupancy_xm<0>(DP, RH, smem); }
+int hd_refine_occupancy_f32(int RH, size_t smem) { return hd_refine_occupancy_xm<0>(RH, smem); }
+
+#define FSNE_DP_RH(X)                                                                           \
+    X(2, 1) X(4, 1) X(8, 1) X(16, 1) X(32, 1) X(2, 2) X(4, 2) X(8, 2) X(16, 2) X(32, 2)
+
+cudaError_t ld_refine_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s) {
+#define FSNE_CASE(dp, rh)                                                                       \
+    if (DP == dp && RH == rh) {                                                                 \
+        FSNE_SET_SMEM((ld_refine_kernel<dp, rh>), smem);                                        \
+        ld_refine_kernel<dp, rh><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);                  \
+        return cudaGetLastError();                                                              \
+    }
+    FSNE_DP_RH(FSNE_CASE)
+#undef FSNE_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t forces_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s) {
+#define FSNE_CASE(dp, rh)                                                                       \
+    if (DP == dp && RH == rh) {                                                                 \
+        FSNE_SET_SMEM((forces_kernel<dp, rh>), smem);                                           \
+        forces_kernel<dp, rh><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);                     \
+        return cudaGetLastError();                                                              \
+    }
+    FSNE_DP_RH(FSNE_CASE)
+#undef FSNE_CASE
+    return cudaErrorInvalidValue;
+}
+
+int ld_refine_occupancy(int DP, int RH, size_t smem) {
+    int n = 0;
+#define FSNE_CASE(dp, rh)                                                                       \
+    if (DP == dp && RH == rh) {                                                                 \
+        FSNE_SET_SMEM((ld_refine_kernel<dp, rh>), smem);                                        \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ld_refine_kernel<dp, rh>, kWarpsPerBlock * 32, smem); \
+    }
+    FSNE_DP_RH(FSNE_CASE)
+#undef FSNE_CASE
+    return n;
+}
+
+int forces_occupancy(int DP, int RH, size_t smem) {
+    int n = 0;
+#define FSNE_CASE(dp, rh)                                                                       \
+    if (DP == dp && RH == rh) {                                                                 \
+        FSNE_SET_SMEM((forces_kernel<dp, rh>), smem);                                           \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, forces_kernel<dp, rh>, kWarpsPerBlock * 32, smem); \
+    }
+    FSNE_DP_RH(FSNE_CASE)
+#undef FSNE_CASE
+    return n;
+}
 
 // LD distances of the current LD lists (read-out only).
 __global__ void ld_distances_kernel(const float* __restrict__ Y, const int32_t* __restrict__ idx, int64_t N,

@@ -50,12 +50,15 @@ __global__ void __launch_bounds__(256) update_kernel(const UpdateParams u) {
     if (threadIdx.x < 32) {
         double z = 0.0;
         unsigned long long nn = 0, ns = 0, nr = 0;
-        for (int b = threadIdx.x; b < u.n_zpart; b += 32) {
-            z += u.zpart[b];
-            nn += u.cnt[3 * b];
-            ns += u.cnt[3 * b + 1];
-            nr += u.cnt[3 * b + 2];
-        }
+        const DevScalars* s0 = u.sc;
+        const bool fired = hd_coin(t, s0->E, u.seed, u.hd_mode);
+        for (int b = threadIdx.x; b < u.n_zpart; b += 32) z += u.zpart[b];
+        if (fired)
+            for (int b = threadIdx.x; b < u.n_cnt; b += 32) {
+                nn += u.cnt[3 * b];
+                ns += u.cnt[3 * b + 1];
+                nr += u.cnt[3 * b + 2];
+            }
         z = warp_sum_d(z);
 #pragma unroll
         for (int m = 16; m > 0; m >>= 1) {

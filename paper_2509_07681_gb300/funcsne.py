@@ -63,7 +63,7 @@ ABI_FUNCTIONS = {
     "funcsne_export_state": (C.c_int, [_h, C.POINTER(State)]),
     "funcsne_import_state": (C.c_int, [_h, C.POINTER(State)]),
     "funcsne_debug_step": (C.c_int, [_h, _vp, _vp]),
-    "funcsne_profile_step": (C.c_int, [_h, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "funcsne_profile_step": (C.c_int, [_h, C.c_int32, C.POINTER(C.c_double)]),
     "funcsne_exact_knn": (C.c_int, [_h, _vp, C.c_int64, C.c_int32, _vp, _vp]),
     "funcsne_exact_knn_noalloc": (C.c_int, [_vp, C.c_int64, C.c_int32, C.c_int32, _vp, C.c_int64, C.c_int32,
                                             _vp, _vp, _vp]),
@@ -203,10 +203,14 @@ def funcsne_debug_step(h, att, rep):
     return att, rep
 
 
+PHASE_KERNELS = ("hd_refine", "ld_refine", "forces", "update")
+
+
 def funcsne_profile_step(h, n_iters):
-    a, b = C.c_double(), C.c_double()
-    _check(load().funcsne_profile_step(h, int(n_iters), C.byref(a), C.byref(b)), h)
-    return a.value, b.value
+    """Summed milliseconds per kernel over n_iters iterations (dict)."""
+    out = (C.c_double * 4)()
+    _check(load().funcsne_profile_step(h, int(n_iters), out), h)
+    return dict(zip(PHASE_KERNELS, list(out)))
 
 
 def funcsne_exact_knn(h, queries, k, idx, d2=None):
@@ -270,7 +274,7 @@ class FuncSNE:
         funcsne_sync(self.h)
 
     def profile_step(self, n=1):
-        """(ms in the fused step kernel, ms in the update kernel) over n iterations."""
+        """Milliseconds per kernel (hd_refine, ld_refine, forces, update) over n iterations."""
         return funcsne_profile_step(self.h, n)
 
     def embedding(self, out=None):
