@@ -192,6 +192,40 @@ hd_refine_kernel(const StepParams p) {
     }
 }
 
+// LD rows are gathered by groups of G = DP/CW lanes (CW = 4 floats per lane,
+// 2 when DP = 2): one 16-byte load per lane, R = 32/G rows per warp
+// instruction. Lane l owns components [CW (l mod G), CW (l mod G) + CW) of
+// every row its group touches.
+template <int DP>
+struct RowSplit {
+    static constexpr int CW = DP >= 4 ? 4 : DP;  // floats per lane
+    static constexpr int G = DP / CW;            // lanes per row
+    static constexpr int R = 32 / G;             // rows per pass
+};
+
+template <int CW>
+__device__ __forceinline__ void load_chunk(const float* __restrict__ src, float (&v)[CW]) {
+    if constexpr (CW == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(src));
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = a.z;
+        v[3] = a.w;
+    } else {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(src));
+        v[0] = a.x;
+        v[1] = a.y;
+    }
+}
+
+// Sum over the G lanes of a row group (xor butterfly inside the group).
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int m = 1; m < G; m <<= 1) v += __shfl_xor_sync(kFull, v, m);
+    return v;
+}
+
 // ------------------------------------------------------------------ LD refinement
 template <int DP, int RH>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
@@ -262,30 +296,14 @@ ld_refine_kernel(const StepParams p) {
     }
 }
 
-// ------------------------------------------------------------------ forces
-// Per-lane interaction with point j: returns w and w^{1/alpha} and the
-// difference vector y_i - y_j.
 template <int DP>
-__device__ __forceinline__ void interaction(const float (&yi)[DP], const float* __restrict__ yrow, float inv_alpha,
-                                            float alpha, float (&dy)[DP], float& w, float& winv) {
-    float yj[DP];
-    load_row<DP>(yrow, yj);
-    float r2 = 0.f;
-#pragma unroll
-    for (int c = 0; c < DP; ++c) {
-        dy[c] = __fsub_rn(yi[c], yj[c]);
-        r2 = __fmaf_rn(dy[c], dy[c], r2);
-    }
-    winv = __fdividef(1.f, __fmaf_rn(r2, inv_alpha, 1.f));
-    w = alpha == 1.f ? winv : exp2f(alpha * __log2f(winv));
-}
-
-template <int DP>
-constexpr int forces_min_blocks() { return DP >= 32 ? 2 : 3; }
+constexpr int forces_min_blocks() { return 4; }
 
 template <int DP, int RH>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, forces_min_blocks<DP>())
 forces_kernel(const StepParams p) {
+    using S = RowSplit<DP>;
+    constexpr int CW = S::CW, G = S::G, R = S::R;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -303,8 +321,8 @@ forces_kernel(const StepParams p) {
     const int k_hd = p.k_hd, k_ld = p.k_ld;
     const float* __restrict__ Y = p.Y;
     const float alpha = p.alpha, inv_alpha = p.inv_alpha;
-    constexpr int RO = DP <= 16 ? 16 : DP;
-    constexpr int NACC = DP <= 4 ? RO + DP : 2 * RO;
+    const int gq = lane / G;          // row slot of this lane within a pass
+    const int co = CW * (lane % G);   // first component owned by this lane
 
     double z_acc = 0.0;
     const int64_t tw = static_cast<int64_t>(gridDim.x) * kWarpsPerBlock;
@@ -319,8 +337,8 @@ forces_kernel(const StepParams p) {
             pv[r] = e < k_hd ? p.P[gi * k_hd + e] : 0.f;
         }
         const uint32_t nl = lane < k_ld ? static_cast<uint32_t>(__ldg(ld_new + gi * k_ld + lane)) : 0xffffffffu;
-        float yi[DP];
-        load_row<DP>(Y + gi * DP, yi);
+        float yi[CW];
+        load_chunk<CW>(Y + gi * DP + co, yi);
         const uint4 wq = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
         // S_i = HD u LD lists of t+1 as a warp hash set
         hset_clear(tab, lane);
@@ -334,80 +352,101 @@ forces_kernel(const StepParams p) {
         if (lane < k_ld) hset_insert(tab, nl);
         __syncwarp();
 
-        // attraction components in acc[0..DP), repulsion in acc[RO..RO+DP)
-        float acc[NACC];
+        float att[CW], rep[CW];
 #pragma unroll
-        for (int c = 0; c < NACC; ++c) acc[c] = 0.f;
+        for (int c = 0; c < CW; ++c) {
+            att[c] = 0.f;
+            rep[c] = 0.f;
+        }
         float z = 0.f;
-#pragma unroll
-        for (int r = 0; r < RH; ++r) {
-            if (r * 32 + lane < k_hd) {
-                float dy[DP], w, winv;
-                interaction<DP>(yi, Y + static_cast<int64_t>(nh[r]) * DP, inv_alpha, alpha, dy, w, winv);
-                const float fa = 4.f * pv[r] * p.inv2N * winv;
-                const float fr = 4.f * w * invZ * winv;
-#pragma unroll
-                for (int c = 0; c < DP; ++c) {
-                    acc[c] = __fmaf_rn(fa, dy[c], acc[c]);
-                    acc[RO + c] = __fmaf_rn(fr, dy[c], acc[RO + c]);
-                }
-                z += w;
-                atomic_add_row<DP>(p.A + static_cast<int64_t>(nh[r]) * DP, dy, -fa);
-            }
-        }
-        // repulsion from LD neighbours outside the HD list, then from the negatives
-        const int n_pass = 1 + (p.n_neg + 31) / 32;
-        for (int pass = 0; pass < n_pass; ++pass) {
-            uint32_t j;
-            float scale;
-            bool on;
-            if (pass == 0) {
-                j = nl;
-                scale = 1.f;
-                on = lane < k_ld && !ld_in_hd;
-            } else {
-                const int s = (pass - 1) * 32 + lane;
-                j = map_other(negative_word(wq.y, wq.w, static_cast<uint32_t>(pass - 1)), N, i);
-                scale = p.neg_scale;
-                on = s < p.n_neg && !hset_has(tab, j);
-            }
+        // One interaction per row group: w, w^{1/alpha} and this lane's
+        // components of y_i - y_j. Every lane of the warp executes it (the
+        // group reduction is a warp shuffle); lanes with on == false read no
+        // row and contribute nothing.
+        auto interact = [&](uint32_t j, bool on, float (&dy)[CW], float& w, float& winv) {
+            float yj[CW];
             if (on) {
-                float dy[DP], w, winv;
-                interaction<DP>(yi, Y + static_cast<int64_t>(j) * DP, inv_alpha, alpha, dy, w, winv);
-                const float fr = scale * 4.f * w * invZ * winv;
+                load_chunk<CW>(Y + static_cast<int64_t>(j) * DP + co, yj);
+            } else {
 #pragma unroll
-                for (int c = 0; c < DP; ++c) acc[RO + c] = __fmaf_rn(fr, dy[c], acc[RO + c]);
-                z = __fmaf_rn(scale, w, z);
+                for (int c = 0; c < CW; ++c) yj[c] = yi[c];
+            }
+            float r2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+                dy[c] = __fsub_rn(yi[c], yj[c]);
+                r2 = __fmaf_rn(dy[c], dy[c], r2);
+            }
+            r2 = group_sum<G>(r2);
+            winv = on ? __fdividef(1.f, __fmaf_rn(r2, inv_alpha, 1.f)) : 0.f;
+            w = (alpha == 1.f || !on) ? winv : exp2f(alpha * __log2f(winv));
+        };
+        // HD neighbours: attraction (both directions of p_ij) and repulsion
+        for (int b = 0; b < k_hd; b += R) {
+            const int e = b + gq;
+            const uint32_t j = warp_get<RH>(nh, static_cast<uint32_t>(e));
+            const float pe = warp_get<RH>(pv, static_cast<uint32_t>(e));
+            const bool on = e < k_hd;
+            float dy[CW], w, winv;
+            interact(j, on, dy, w, winv);
+            const float fa = 4.f * pe * p.inv2N * winv;
+            const float fr = 4.f * w * invZ * winv;
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+                att[c] = __fmaf_rn(fa, dy[c], att[c]);
+                rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
+            }
+            if (lane % G == 0) z += w;
+            if (on) {
+                if constexpr (CW == 4)
+                    atomicAdd(reinterpret_cast<float4*>(p.A + static_cast<int64_t>(j) * DP + co),
+                              make_float4(-fa * dy[0], -fa * dy[1], -fa * dy[2], -fa * dy[3]));
+                else
+                    atomicAdd(reinterpret_cast<float2*>(p.A + static_cast<int64_t>(j) * DP + co),
+                              make_float2(-fa * dy[0], -fa * dy[1]));
             }
         }
-        // warp reductions: the lane owning component c adds A_i[c] and stores R_i[c]
-        if constexpr (DP <= 4) {
+        // LD neighbours outside the HD list: repulsion
+        for (int b = 0; b < k_ld; b += R) {
+            const int l = b + gq;
+            const uint32_t j = __shfl_sync(kFull, nl, l & 31);
+            const bool on = __shfl_sync(kFull, ld_in_hd ? 0 : 1, l & 31) && l < k_ld;
+            float dy[CW], w, winv;
+            interact(j, on, dy, w, winv);
+            const float fr = 4.f * w * invZ * winv;
 #pragma unroll
-            for (int c = 0; c < NACC; ++c) acc[c] = warp_sum(acc[c]);
-            if (lane < DP) {
-                float a = acc[0], b = acc[RO];
+            for (int c = 0; c < CW; ++c) rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
+            if (lane % G == 0) z += w;
+        }
+        // Philox-seeded negatives outside S_i, scaled by (N-1)/n_neg
+        for (int b = 0; b < p.n_neg; b += R) {
+            const int s = b + gq;
+            const uint32_t w1 = __shfl_sync(kFull, wq.y, s & 31);
+            const uint32_t w3 = __shfl_sync(kFull, wq.w, s & 31);
+            const uint32_t j = map_other(negative_word(w1, w3, static_cast<uint32_t>(s >> 5)), N, i);
+            const bool on = s < p.n_neg && !hset_has(tab, j);
+            float dy[CW], w, winv;
+            interact(j, on, dy, w, winv);
+            const float fr = p.neg_scale * 4.f * w * invZ * winv;
 #pragma unroll
-                for (int c = 1; c < DP; ++c)
-                    if (lane == c) {
-                        a = acc[c];
-                        b = acc[RO + c];
-                    }
-                atomicAdd(p.A + gi * DP + lane, a);
-                p.R[gi * DP + lane] = b;
+            for (int c = 0; c < CW; ++c) rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
+            if (lane % G == 0) z = __fmaf_rn(p.neg_scale, w, z);
+        }
+        // sum over the row groups; lanes 0..G-1 then hold A_i and R_i
+#pragma unroll
+        for (int m = G; m < 32; m <<= 1)
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+                att[c] += __shfl_xor_sync(kFull, att[c], m);
+                rep[c] += __shfl_xor_sync(kFull, rep[c], m);
             }
-        } else if constexpr (DP == 32) {
-            const float a = warp_reduce_scatter32<0>(acc, lane);
-            const float b = warp_reduce_scatter32<32>(acc, lane);
-            atomicAdd(p.A + gi * DP + lane, a);
-            p.R[gi * DP + lane] = b;
-        } else {
-            const float v = warp_reduce_scatter32(acc, lane);
-            const int c = lane & 15;
-            if (c < DP) {
-                if (lane < 16)
-                    atomicAdd(p.A + gi * DP + c, v);
-                else
-                    p.R[gi * DP + c] = v;
+        if (lane < G) {
+            if constexpr (CW == 4) {
+                atomicAdd(reinterpret_cast<float4*>(p.A + gi * DP + co), make_float4(att[0], att[1], att[2], att[3]));
+                *reinterpret_cast<float4*>(p.R + gi * DP + co) = make_float4(rep[0], rep[1], rep[2], rep[3]);
+            } else {
+                atomicAdd(reinterpret_cast<float2*>(p.A + gi * DP + co), make_float2(att[0], att[1]));
+                *reinterpret_cast<float2*>(p.R + gi * DP + co) = make_float2(rep[0], rep[1]);
             }
         }
         z = warp_sum(z);
