@@ -883,3 +883,154 @@ void oracle_insert(oracle_state *st, int64_t n_old, double bisect_tol, int bisec
     free(nd2);
     free(off);
 }
+
+/* ------------------------------------------------------------------ */
+/* Learned placement: a D-H-H-d ReLU MLP trained online on the (x_i, y_i) */
+/* pairs of the running embedding (an addition to the method; the paper   */
+/* has no learned part). Parameters, flat: W1 (H x D) b1 (H) W2 (H x H)    */
+/* b2 (H) W3 (d x H) b3 (d), row-major.                                    */
+/* ------------------------------------------------------------------ */
+
+/* Round to bfloat16, nearest-even, through binary32 (the value the device
+ * rounds is a binary32). */
+double oracle_bf16(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x; /* inf / nan unchanged */
+    u += 0x7fffu + ((u >> 16) & 1u);
+    u &= 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+static double maybe_bf16(double x, int round) { return round ? oracle_bf16(x) : x; }
+
+/* Initial parameters: weights of layer l uniform in (-a, a), a =
+ * sqrt(6 / fan_in) for the hidden layers and sqrt(3 / fan_in) for the
+ * output layer; entry (r, c) from word c mod 4 of the Philox block at
+ * counter (l, r, MLP_INIT, c div 4) as a (2 (w + 0.5) 2^-32 - 1), rounded
+ * to binary32; biases 0. */
+void oracle_mlp_init(int D, int H, int d, uint64_t seed, double *theta)
+{
+    int dims[3][2] = {{H, D}, {H, H}, {d, H}};
+    double *p = theta;
+    for (int l = 0; l < 3; ++l) {
+        int rows = dims[l][0], cols = dims[l][1];
+        double a = sqrt((l < 2 ? 6.0 : 3.0) / (double)cols);
+        for (int r = 0; r < rows; ++r)
+            for (int c = 0; c < cols; ++c) {
+                uint32_t w[4];
+                draw4(seed, (uint32_t)(l + 1), (uint32_t)r, 10u, (uint32_t)(c / 4), w);
+                double u = ((double)w[c % 4] + 0.5) * (1.0 / 4294967296.0);
+                p[r * cols + c] = (double)(float)(a * (2.0 * u - 1.0));
+            }
+        p += rows * cols;
+        for (int r = 0; r < rows; ++r) p[r] = 0.0;
+        p += rows;
+    }
+}
+
+/*
+ * Loss and gradient of one batch: X (B x D), targets T (B x d).
+ *   H1 = r(relu(X W1^T + b1)), H2 = r(relu(H1 W2^T + b2)), O = H2 W3^T + b3,
+ *   L = mean over B*d of (O - T)^2,
+ *   G3 = r(2 (O - T) / (B d)), G2 = r((G3 W3) * [H2 > 0]),
+ *   G1 = r((G2 W2) * [H1 > 0]),
+ *   dW3 = G3^T H2, db3 = sum G3, dW2 = G2^T H1, db2 = sum G2,
+ *   dW1 = G1^T X, db1 = sum G1,
+ * where r() rounds to bfloat16 when `round` is set (the device's operand
+ * precision) and is the identity otherwise. Weights are used as given.
+ * Writes O (B x d) when non-NULL; returns L.
+ */
+double oracle_mlp_grad(int B, int D, int H, int d, const double *theta, const double *X, const double *T,
+                       int round, double *grad, double *O_out)
+{
+    const double *W1 = theta, *b1 = W1 + (size_t)H * D, *W2 = b1 + H, *b2 = W2 + (size_t)H * H;
+    const double *W3 = b2 + H, *b3 = W3 + (size_t)d * H;
+    double *gW1 = grad, *gb1 = gW1 + (size_t)H * D, *gW2 = gb1 + H, *gb2 = gW2 + (size_t)H * H;
+    double *gW3 = gb2 + H, *gb3 = gW3 + (size_t)d * H;
+    size_t np = (size_t)H * D + H + (size_t)H * H + H + (size_t)d * H + d;
+    memset(grad, 0, sizeof(double) * np);
+    double *H1 = (double *)malloc(sizeof(double) * (size_t)H);
+    double *H2 = (double *)malloc(sizeof(double) * (size_t)H);
+    double *G2 = (double *)malloc(sizeof(double) * (size_t)H);
+    double *G1 = (double *)malloc(sizeof(double) * (size_t)H);
+    double *G3 = (double *)malloc(sizeof(double) * (size_t)d);
+    double loss = 0.0;
+    for (int b = 0; b < B; ++b) {
+        const double *x = X + (size_t)b * D;
+        for (int h = 0; h < H; ++h) {
+            double z = b1[h];
+            for (int f = 0; f < D; ++f) z += W1[(size_t)h * D + f] * x[f];
+            H1[h] = maybe_bf16(z > 0.0 ? z : 0.0, round);
+        }
+        for (int h = 0; h < H; ++h) {
+            double z = b2[h];
+            for (int g = 0; g < H; ++g) z += W2[(size_t)h * H + g] * H1[g];
+            H2[h] = maybe_bf16(z > 0.0 ? z : 0.0, round);
+        }
+        for (int c = 0; c < d; ++c) {
+            double o = b3[c];
+            for (int g = 0; g < H; ++g) o += W3[(size_t)c * H + g] * H2[g];
+            if (O_out) O_out[(size_t)b * d + c] = o;
+            double e = o - T[(size_t)b * d + c];
+            loss += e * e;
+            G3[c] = maybe_bf16(2.0 * e / ((double)B * d), round);
+        }
+        for (int c = 0; c < d; ++c) {
+            for (int g = 0; g < H; ++g) gW3[(size_t)c * H + g] += G3[c] * H2[g];
+            gb3[c] += G3[c];
+        }
+        for (int g = 0; g < H; ++g) {
+            double s = 0.0;
+            for (int c = 0; c < d; ++c) s += G3[c] * W3[(size_t)c * H + g];
+            G2[g] = maybe_bf16(H2[g] > 0.0 ? s : 0.0, round);
+        }
+        for (int h = 0; h < H; ++h) {
+            for (int g = 0; g < H; ++g) gW2[(size_t)h * H + g] += G2[h] * H1[g];
+            gb2[h] += G2[h];
+        }
+        for (int g = 0; g < H; ++g) {
+            double s = 0.0;
+            for (int h = 0; h < H; ++h) s += G2[h] * W2[(size_t)h * H + g];
+            G1[g] = maybe_bf16(H1[g] > 0.0 ? s : 0.0, round);
+        }
+        for (int h = 0; h < H; ++h) {
+            for (int f = 0; f < D; ++f) gW1[(size_t)h * D + f] += G1[h] * x[f];
+            gb1[h] += G1[h];
+        }
+    }
+    free(H1);
+    free(H2);
+    free(G2);
+    free(G1);
+    free(G3);
+    return loss / ((double)B * d);
+}
+
+/* Forward pass only (placement): O = MLP(X) with the same roundings. */
+void oracle_mlp_forward(int B, int D, int H, int d, const double *theta, const double *X, int round, double *O)
+{
+    double *T = (double *)calloc((size_t)B * d, sizeof(double));
+    size_t np = (size_t)H * D + H + (size_t)H * H + H + (size_t)d * H + d;
+    double *g = (double *)malloc(sizeof(double) * np);
+    oracle_mlp_grad(B, D, H, d, theta, X, T, round, g, O);
+    free(T);
+    free(g);
+}
+
+/* Adam (Kingma & Ba 2015) with bias correction, step number `step` >= 1:
+ * m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2;
+ * theta -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */
+void oracle_adam(int64_t n, double *theta, const double *g, double *m, double *v, int step, double lr,
+                 double b1, double b2, double eps)
+{
+    double c1 = 1.0 - pow(b1, step), c2 = 1.0 - pow(b2, step);
+    for (int64_t e = 0; e < n; ++e) {
+        m[e] = b1 * m[e] + (1.0 - b1) * g[e];
+        v[e] = b2 * v[e] + (1.0 - b2) * g[e] * g[e];
+        theta[e] -= lr * (m[e] / c1) / (sqrt(v[e] / c2) + eps);
+    }
+}

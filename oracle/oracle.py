@@ -11,7 +11,7 @@ import numpy as np
 
 from .build import build_oracle
 
-__all__ = ["lib", "philox", "OracleState", "bisect", "entropy", "topk_merge",
+__all__ = ["lib", "philox", "OracleState", "bf16", "mlp_size", "mlp_init", "mlp_grad", "mlp_forward", "adam", "bisect", "entropy", "topk_merge",
            "exact_z", "kl_divergence", "exact_grad", "bruteforce_knn", "query_knn",
            "ORACLE_BISECT_TOL", "ORACLE_BISECT_MAXIT", "STREAMS", "CAND_HD", "CAND_LD"]
 
@@ -89,6 +89,17 @@ def _declare(L):
     L.oracle_query_knn.restype = None
     L.oracle_insert.argtypes = [sp, C.c_int64, C.c_double, C.c_int]
     L.oracle_insert.restype = None
+    L.oracle_bf16.argtypes = [C.c_double]
+    L.oracle_bf16.restype = C.c_double
+    L.oracle_mlp_init.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, _dp]
+    L.oracle_mlp_init.restype = None
+    L.oracle_mlp_grad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, C.c_int, _dp, _dp]
+    L.oracle_mlp_grad.restype = C.c_double
+    L.oracle_mlp_forward.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, _dp]
+    L.oracle_mlp_forward.restype = None
+    L.oracle_adam.argtypes = [C.c_int64, _dp, _dp, _dp, _dp, C.c_int, C.c_double, C.c_double, C.c_double,
+                              C.c_double]
+    L.oracle_adam.restype = None
 
 
 def _p(a, t):
@@ -176,6 +187,53 @@ def query_knn(X, queries, k):
     lib().oracle_query_knn(_p(X, _dp), X.shape[0], X.shape[1], _p(q, _lp), len(q), k,
                            _p(idx, _ip), _p(d2, _dp))
     return idx, d2
+
+
+def bf16(x):
+    """Round to bfloat16 (nearest even) through binary32, elementwise."""
+    x = np.asarray(x, dtype=np.float64)
+    f = x.astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    fin = (u & 0x7F800000) != 0x7F800000
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    out = np.where(fin, r.view(np.float32), f).astype(np.float64)
+    return out
+
+
+def mlp_size(D, H, d):
+    return H * D + H + H * H + H + d * H + d
+
+
+def mlp_init(D, H, d, seed):
+    th = np.zeros(mlp_size(D, H, d))
+    lib().oracle_mlp_init(D, H, d, seed, _p(th, _dp))
+    return th
+
+
+def mlp_grad(theta, X, T, H, round_bf16=True):
+    """(loss, flat gradient, outputs) of one batch."""
+    theta, X, T = _f64(theta), _f64(X), _f64(T)
+    B, D = X.shape
+    d = T.shape[1]
+    g = np.zeros_like(theta)
+    O = np.zeros((B, d))
+    loss = lib().oracle_mlp_grad(B, D, H, d, _p(theta, _dp), _p(X, _dp), _p(T, _dp), int(round_bf16),
+                                 _p(g, _dp), _p(O, _dp))
+    return loss, g, O
+
+
+def mlp_forward(theta, X, H, d, round_bf16=True):
+    theta, X = _f64(theta), _f64(X)
+    B, D = X.shape
+    O = np.zeros((B, d))
+    lib().oracle_mlp_forward(B, D, H, d, _p(theta, _dp), _p(X, _dp), int(round_bf16), _p(O, _dp))
+    return O
+
+
+def adam(theta, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam step on float64 arrays."""
+    lib().oracle_adam(len(theta), _p(theta, _dp), _p(_f64(g), _dp), _p(m, _dp), _p(v, _dp), int(step),
+                      float(lr), float(b1), float(b2), float(eps))
 
 
 class OracleState:

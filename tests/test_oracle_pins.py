@@ -377,3 +377,86 @@ def test_insertion_with_more_ld_than_hd_neighbours():
         row = st.ld_idx[i]
         assert len(set(row.tolist())) == 12 and row.max() < 250
         assert row[:8].tolist() == st.hd_idx[i].tolist()
+
+
+# ---------------------------------------------------------------- learned placement (MLP)
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(20).standard_normal(20000) * np.exp(np.random.default_rng(21).uniform(-20, 20, 20000))
+    x[:5] = [1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -(1.0 + 2 ** -8), 0.0, 65504.0]
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(O.bf16(x), ref)
+    assert O.lib().oracle_bf16(1.0 + 2 ** -8) == 1.0  # tie to even
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(22)
+    D, H, d, B = 6, 10, 3, 7
+    th = O.mlp_init(D, H, d, 5) + 0.05 * rng.standard_normal(O.mlp_size(D, H, d))
+    X = rng.standard_normal((B, D))
+    T = rng.standard_normal((B, d))
+    loss, g, _ = O.mlp_grad(th, X, T, H, round_bf16=False)
+    h = 1e-6
+    for e in rng.choice(len(th), 40, replace=False):
+        tp, tm = th.copy(), th.copy()
+        tp[e] += h
+        tm[e] -= h
+        fd = (O.mlp_grad(tp, X, T, H, False)[0] - O.mlp_grad(tm, X, T, H, False)[0]) / (2 * h)
+        assert abs(fd - g[e]) <= 1e-6 * max(1.0, abs(g).max())
+
+
+def test_mlp_forward_is_the_composition_of_layers():
+    # an independent numpy restatement of the network for one input
+    rng = np.random.default_rng(23)
+    D, H, d = 4, 6, 2
+    th = O.mlp_init(D, H, d, 3)
+    W1 = th[:H * D].reshape(H, D)
+    b1 = th[H * D:H * D + H]
+    o = H * D + H
+    W2 = th[o:o + H * H].reshape(H, H)
+    b2 = th[o + H * H:o + H * H + H]
+    o += H * H + H
+    W3 = th[o:o + d * H].reshape(d, H)
+    b3 = th[o + d * H:]
+    x = rng.standard_normal((5, D))
+    ref = np.maximum(np.maximum(x @ W1.T + b1, 0) @ W2.T + b2, 0) @ W3.T + b3
+    np.testing.assert_allclose(O.mlp_forward(th, x, H, d, round_bf16=False), ref, rtol=1e-12, atol=1e-14)
+
+
+def test_mlp_init_ranges():
+    D, H, d = 50, 256, 8
+    th = O.mlp_init(D, H, d, 0)
+    W1 = th[:H * D]
+    a = np.sqrt(6 / D)
+    assert np.abs(W1).max() < a and abs(W1.mean()) < 0.02 * a
+    assert abs(W1.var() - a * a / 3) < 0.05 * a * a / 3
+    assert np.all(th[H * D:H * D + H] == 0)
+    assert np.all(th.astype(np.float32).astype(np.float64) == th)  # binary32 values
+
+
+def test_adam_first_step_closed_form():
+    g = np.array([0.3, -2.0, 1e-9, 0.0])
+    th = np.zeros(4)
+    m = np.zeros(4)
+    v = np.zeros(4)
+    O.adam(th, g, m, v, 1, lr=1e-3, eps=1e-8)
+    # first step: m_hat = g, v_hat = g^2, so the update is lr g / (|g| + eps)
+    np.testing.assert_allclose(th, -1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+
+
+def test_mlp_training_fits_a_smooth_map():
+    rng = np.random.default_rng(24)
+    D, H, d, B = 8, 32, 2, 256
+    A = rng.standard_normal((D, d))
+    X = rng.standard_normal((4 * B, D))
+    T = np.tanh(X @ A)
+    th = O.mlp_init(D, H, d, 1)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    losses = []
+    for step in range(1, 301):
+        b = rng.choice(len(X), B, replace=False)
+        loss, g, _ = O.mlp_grad(th, O.bf16(X[b]), T[b], H, round_bf16=True)
+        losses.append(loss)
+        O.adam(th, g, m, v, step, lr=3e-3)
+    assert np.mean(losses[-20:]) < 0.2 * np.mean(losses[:5])
