@@ -79,7 +79,28 @@ typedef struct {
     uint32_t error_word;   /* device error bits (0 = none)                          */
     int64_t cand_scored;   /* HD candidates scored (cumulative)                      */
     int64_t cand_reranked; /* of which re-ranked from FP32 rows (cumulative)         */
+    int64_t mlp_steps;     /* training steps of the placement MLP                    */
+    double mlp_loss;       /* its loss on the last training batch                    */
 } funcsne_stats_t;
+
+/* One training step of the placement MLP with its intermediate values, for
+ * testing. Each pointer may be NULL (skipped) and may be host or device
+ * memory. B = option "mlp_batch", H = "mlp_hidden", n_params =
+ * H D + H + H H + H + d H + d (layout W1 b1 W2 b2 W3 b3, row-major). */
+typedef struct {
+    int32_t *batch_idx;   /* B point indices of the batch                       */
+    float *xhat;          /* B x D normalised inputs (bfloat16 values)           */
+    float *target;        /* B x d scaled targets y / s                          */
+    float *output;        /* B x d network outputs                               */
+    float *theta_before;  /* n_params FP32 parameters before the step            */
+    float *weights_bf16;  /* n_params bfloat16 copy the step used (as float)     */
+    float *grad;          /* n_params gradient                                    */
+    float *theta_after;   /* n_params FP32 parameters after the Adam update       */
+    double loss;          /* mean squared error of the batch                      */
+    float scale;          /* s = RMS of the batch's y                             */
+    int32_t step;         /* Adam step number of this step (1 = first)            */
+    int64_t n_params;
+} funcsne_mlp_debug_t;
 
 /*
  * funcsne_create -- allocate a handle and initialise the method's state
@@ -117,6 +138,12 @@ int funcsne_create(const float *X, int64_t N, int32_t D, int32_t d, int32_t k_hd
  *                    (Section 3); 1: every iteration; 2: never
  *   "precision"      FUNCSNE_FP32 / FUNCSNE_BF16 / FUNCSNE_FP8 HD storage
  *   "alpha"          tail parameter (may change between steps)
+ *   "surrogate"      1: train the placement MLP inside funcsne_step, one
+ *                    step before every "mlp_every"-th iteration (default 0)
+ *   "mlp_every"      iterations between training steps (default 10)
+ *   "mlp_lr"         Adam learning rate (default 1e-3)
+ *   "mlp_batch"      training batch size B (default 4096; before first use)
+ *   "mlp_hidden"     hidden width H (default 256; before first use)
  * Unknown keys or out-of-range values: FUNCSNE_E_ARG.
  */
 int funcsne_set_option(funcsne_t *h, const char *key, double value);
@@ -158,6 +185,22 @@ int funcsne_sync(funcsne_t *h);
  */
 int funcsne_insert(funcsne_t *h, const float *X_new, int64_t n_new, int32_t placement,
                    int64_t *first_id);
+
+/*
+ * Placement MLP (an addition to the method; the paper has no learned part):
+ * a D-H-H-d ReLU network with bfloat16 weights and FP32 accumulation,
+ * trained by Adam (lr "mlp_lr", beta 0.9 / 0.999, eps 1e-8) to map the
+ * normalised x_i of B points drawn by Philox to y_i / s (s = RMS of the
+ * batch's y). Inputs are normalised by the per-feature mean and standard
+ * deviation of the points present at its first use. It places points
+ * inserted with FUNCSNE_PLACE_SURROGATE at s MLP(x).
+ * funcsne_mlp_train runs n_steps training steps now; funcsne_mlp_predict
+ * writes s MLP(x) for the n rows of X (n x D, host or device) into Y_out
+ * (n x d); funcsne_mlp_debug_step runs one step and exports its values.
+ */
+int funcsne_mlp_train(funcsne_t *h, int32_t n_steps);
+int funcsne_mlp_predict(const funcsne_t *h, const float *X, int64_t n, float *Y_out);
+int funcsne_mlp_debug_step(funcsne_t *h, funcsne_mlp_debug_t *out);
 
 /* Copy the first min(N, cap_rows) rows of the N x d embedding into Y_out. */
 int funcsne_get_embedding(const funcsne_t *h, float *Y_out, int64_t cap_rows);

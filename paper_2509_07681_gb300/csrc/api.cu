@@ -53,6 +53,23 @@ struct funcsne {
     int hd_blocks = 0, ld_blocks = 0, fo_blocks = 0, update_blocks = 0;
     size_t hd_smem = 0, ld_smem = 0, fo_smem = 0;
     cudaGraphExec_t graph1 = nullptr, graph8 = nullptr;
+    uint32_t t_host = 0;  // host mirror of the iteration counter
+    // learned placement (MLP surrogate)
+    int32_t mlp_H = 256, mlp_B = 4096, mlp_every = 10;
+    float mlp_lr = 1e-3f;
+    bool surrogate = false;
+    uint32_t mlp_steps = 0;  // host mirror of the Adam step count
+    struct {
+        bool ready = false;
+        int64_t n_params = 0;
+        float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *mu = nullptr, *sigma = nullptr;
+        __nv_bfloat16* wb = nullptr;
+        int32_t* idx = nullptr;
+        float *T = nullptr, *O = nullptr, *scale = nullptr;
+        __nv_bfloat16 *Xb = nullptr, *H1 = nullptr, *H2 = nullptr, *G3 = nullptr, *G2 = nullptr, *G1 = nullptr;
+        double *part = nullptr, *loss = nullptr;
+        uint32_t* step = nullptr;
+    } mlp;
     std::string err;
 };
 
@@ -281,6 +298,15 @@ void free_all(funcsne* h) {
     cudaFree(h->sc);
     cudaFree(h->zpart);
     cudaFree(h->cnt);
+    auto& q = h->mlp;
+    for (void* p : {static_cast<void*>(q.theta), static_cast<void*>(q.m), static_cast<void*>(q.v),
+                    static_cast<void*>(q.grad), static_cast<void*>(q.mu), static_cast<void*>(q.sigma),
+                    static_cast<void*>(q.wb), static_cast<void*>(q.idx), static_cast<void*>(q.T),
+                    static_cast<void*>(q.O), static_cast<void*>(q.scale), static_cast<void*>(q.Xb),
+                    static_cast<void*>(q.H1), static_cast<void*>(q.H2), static_cast<void*>(q.G3),
+                    static_cast<void*>(q.G2), static_cast<void*>(q.G1), static_cast<void*>(q.part),
+                    static_cast<void*>(q.loss), static_cast<void*>(q.step)})
+        cudaFree(p);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
 }
 
@@ -339,6 +365,99 @@ ZinitParams zinit_params(const funcsne* h, const int32_t* hd, const int32_t* ld,
     z.ld_idx = ld;
     z.part = part;
     return z;
+}
+
+MlpParams mlp_params(const funcsne* h) {
+    const auto& q = h->mlp;
+    MlpParams p{};
+    p.N = h->N;
+    p.B = h->mlp_B;
+    p.D = h->D;
+    p.H = h->mlp_H;
+    p.d = h->d;
+    p.DP = h->DP;
+    p.xpitch = h->xpitch;
+    p.n_params = q.n_params;
+    p.seed = h->seed;
+    p.lr = h->mlp_lr;
+    p.beta1 = 0.9f;
+    p.beta2 = 0.999f;
+    p.eps = 1e-8f;
+    p.X32 = h->X32;
+    p.Y = h->Y;
+    p.mu = q.mu;
+    p.sigma = q.sigma;
+    p.theta = q.theta;
+    p.m = q.m;
+    p.v = q.v;
+    p.grad = q.grad;
+    p.wb = q.wb;
+    p.idx = q.idx;
+    p.T = q.T;
+    p.Xb = q.Xb;
+    p.H1 = q.H1;
+    p.H2 = q.H2;
+    p.G3 = q.G3;
+    p.G2 = q.G2;
+    p.G1 = q.G1;
+    p.O = q.O;
+    p.part = q.part;
+    p.loss = q.loss;
+    p.scale = q.scale;
+    p.step = q.step;
+    return p;
+}
+
+// Allocate and initialise the surrogate on first use: input statistics of
+// the current points, initial parameters, zero moments.
+int ensure_mlp(funcsne* h) {
+    auto& q = h->mlp;
+    if (q.ready) return FUNCSNE_OK;
+    const int64_t D = h->D, H = h->mlp_H, d = h->d, B = h->mlp_B;
+    q.n_params = H * D + H + H * H + H + d * H + d;
+    FSNE_CUDA(h, dalloc(&q.theta, q.n_params));
+    FSNE_CUDA(h, dalloc(&q.m, q.n_params));
+    FSNE_CUDA(h, dalloc(&q.v, q.n_params));
+    FSNE_CUDA(h, dalloc(&q.grad, q.n_params));
+    FSNE_CUDA(h, dalloc(&q.wb, q.n_params));
+    FSNE_CUDA(h, dalloc(&q.mu, D));
+    FSNE_CUDA(h, dalloc(&q.sigma, D));
+    FSNE_CUDA(h, dalloc(&q.idx, B));
+    FSNE_CUDA(h, dalloc(&q.T, B * d));
+    FSNE_CUDA(h, dalloc(&q.O, B * d));
+    FSNE_CUDA(h, dalloc(&q.Xb, B * D));
+    FSNE_CUDA(h, dalloc(&q.H1, B * H));
+    FSNE_CUDA(h, dalloc(&q.H2, B * H));
+    FSNE_CUDA(h, dalloc(&q.G3, B * d));
+    FSNE_CUDA(h, dalloc(&q.G2, B * H));
+    FSNE_CUDA(h, dalloc(&q.G1, B * H));
+    FSNE_CUDA(h, dalloc(&q.part, (B * d + 255) / 256 + (B + 255) / 256 + 8));
+    FSNE_CUDA(h, dalloc(&q.loss, 1));
+    FSNE_CUDA(h, dalloc(&q.scale, 1));
+    FSNE_CUDA(h, dalloc(&q.step, 1));
+    FSNE_CUDA(h, cudaMemsetAsync(q.m, 0, q.n_params * sizeof(float), h->stream));
+    FSNE_CUDA(h, cudaMemsetAsync(q.v, 0, q.n_params * sizeof(float), h->stream));
+    FSNE_CUDA(h, cudaMemsetAsync(q.step, 0, sizeof(uint32_t), h->stream));
+    FSNE_CUDA(h, cudaMemsetAsync(q.loss, 0, sizeof(double), h->stream));
+    const float one = 1.f;
+    FSNE_CUDA(h, cudaMemcpyAsync(q.scale, &one, sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    FSNE_CUDA(h, launch_mlp_stats(h->X32, h->N, h->D, h->xpitch, q.mu, q.sigma, h->stream));
+    FSNE_CUDA(h, launch_mlp_init(q.theta, q.wb, h->D, h->mlp_H, h->d, h->seed, h->stream));
+    FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    q.ready = true;
+    h->mlp_steps = 0;
+    return FUNCSNE_OK;
+}
+
+int mlp_train_now(funcsne* h, int n) {
+    int rc = ensure_mlp(h);
+    if (rc) return rc;
+    const MlpParams q = mlp_params(h);
+    for (int k = 0; k < n; ++k) {
+        FSNE_CUDA(h, launch_mlp_train_step(q, h->stream));
+        ++h->mlp_steps;
+    }
+    return FUNCSNE_OK;
 }
 
 // Reallocate every per-point array for new_cap rows (N rows kept, the rest zero).
@@ -567,6 +686,19 @@ int funcsne_set_option(funcsne_t* h, const char* key, double v) {
     } else if (k == "alpha") {
         if (!(v > 0)) return fail(h, FUNCSNE_E_ARG, "alpha must be > 0");
         h->alpha = static_cast<float>(v);
+    } else if (k == "surrogate") {
+        if (v != 0 && v != 1) return fail(h, FUNCSNE_E_ARG, "surrogate must be 0 or 1");
+        h->surrogate = v != 0;
+    } else if (k == "mlp_every") {
+        if (v < 1 || v > 1e6 || v != static_cast<int>(v)) return fail(h, FUNCSNE_E_ARG, "mlp_every must be a positive integer");
+        h->mlp_every = static_cast<int32_t>(v);
+    } else if (k == "mlp_lr") {
+        if (!(v > 0)) return fail(h, FUNCSNE_E_ARG, "mlp_lr must be > 0");
+        h->mlp_lr = static_cast<float>(v);
+    } else if (k == "mlp_batch" || k == "mlp_hidden") {
+        if (h->mlp.ready) return fail(h, FUNCSNE_E_STATE, "%s must be set before the surrogate is first used", key);
+        if (v < 16 || v > 65536 || v != static_cast<int>(v)) return fail(h, FUNCSNE_E_ARG, "%s must be an integer in [16, 65536]", key);
+        (k == "mlp_batch" ? h->mlp_B : h->mlp_H) = static_cast<int32_t>(v);
     } else if (k == "precision") {
         const int m = static_cast<int>(v);
         if (m != v || m < 0 || m > 2) return fail(h, FUNCSNE_E_ARG, "precision must be 0, 1 or 2");
@@ -596,6 +728,11 @@ int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
     else if (k == "hd_mode") *v = h->hd_mode;
     else if (k == "alpha") *v = h->alpha;
     else if (k == "precision") *v = h->precision;
+    else if (k == "surrogate") *v = h->surrogate ? 1 : 0;
+    else if (k == "mlp_every") *v = h->mlp_every;
+    else if (k == "mlp_lr") *v = h->mlp_lr;
+    else if (k == "mlp_batch") *v = h->mlp_B;
+    else if (k == "mlp_hidden") *v = h->mlp_H;
     else if (k == "hd_blocks") *v = h->hd_blocks;
     else if (k == "ld_blocks") *v = h->ld_blocks;
     else if (k == "forces_blocks") *v = h->fo_blocks;
@@ -624,6 +761,19 @@ int funcsne_step(funcsne_t* h, int32_t n_iters) {
         int rc = build_graph(h, 1, &h->graph1);
         if (rc) return rc;
     }
+    if (h->surrogate) {
+        // the surrogate trains on (x_i, y_i) of the current state before every
+        // mlp_every-th iteration
+        for (int k = 0; k < n_iters; ++k) {
+            if (h->t_host % static_cast<uint32_t>(h->mlp_every) == 0) {
+                int rc = mlp_train_now(h, 1);
+                if (rc) return rc;
+            }
+            FSNE_CUDA(h, cudaGraphLaunch(h->graph1, h->stream));
+            ++h->t_host;
+        }
+        return FUNCSNE_OK;
+    }
     if (n_iters >= 8 && !h->graph8) {
         int rc = build_graph(h, 8, &h->graph8);
         if (rc) return rc;
@@ -634,7 +784,85 @@ int funcsne_step(funcsne_t* h, int32_t n_iters) {
         left -= 8;
     }
     while (left-- > 0) FSNE_CUDA(h, cudaGraphLaunch(h->graph1, h->stream));
+    h->t_host += static_cast<uint32_t>(n_iters);
     return FUNCSNE_OK;
+}
+
+int funcsne_mlp_train(funcsne_t* h, int32_t n_steps) {
+    if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
+    if (n_steps < 0) return fail(h, FUNCSNE_E_ARG, "n_steps must be >= 0");
+    return mlp_train_now(h, n_steps);
+}
+
+int funcsne_mlp_predict(const funcsne_t* hc, const float* X, int64_t n, float* Y_out) {
+    funcsne* h = const_cast<funcsne*>(hc);
+    if (!h || !X || !Y_out) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    if (n < 0) return fail(h, FUNCSNE_E_ARG, "n must be >= 0");
+    if (n == 0) return FUNCSNE_OK;
+    int rc = ensure_mlp(h);
+    if (rc) return rc;
+    float *xd = nullptr, *yd = nullptr;
+    cudaError_t e = dalloc(&xd, static_cast<size_t>(n) * h->xpitch);
+    if (e == cudaSuccess) e = dalloc(&yd, static_cast<size_t>(n) * h->DP);
+    if (e == cudaSuccess) e = cudaMemsetAsync(xd, 0, static_cast<size_t>(n) * h->xpitch * 4, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(xd, h->xpitch * 4, X, h->D * 4, h->D * 4, static_cast<size_t>(n), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = launch_mlp_place(mlp_params(h), xd, h->xpitch, 0, n, yd, h->DP, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(Y_out, h->d * 4, yd, h->DP * 4, h->d * 4, static_cast<size_t>(n), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(xd);
+    cudaFree(yd);
+    FSNE_CUDA(h, e);
+    return FUNCSNE_OK;
+}
+
+int funcsne_mlp_debug_step(funcsne_t* h, funcsne_mlp_debug_t* out) {
+    if (!h || !out) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    int rc = ensure_mlp(h);
+    if (rc) return rc;
+    auto& q = h->mlp;
+    const size_t np = static_cast<size_t>(q.n_params);
+    const size_t B = static_cast<size_t>(h->mlp_B), D = static_cast<size_t>(h->D), d = static_cast<size_t>(h->d);
+    float* tmp = nullptr;
+    FSNE_CUDA(h, dalloc(&tmp, np > B * D ? np : B * D));
+    auto finish = [&](cudaError_t e) -> int {
+        cudaFree(tmp);
+        FSNE_CUDA(h, e);
+        return static_cast<int>(FUNCSNE_OK);
+    };
+    cudaError_t e = cudaSuccess;
+    if (out->theta_before) e = cudaMemcpyAsync(out->theta_before, q.theta, np * 4, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess && out->weights_bf16) {
+        e = launch_bf16_to_f32(q.wb, static_cast<int64_t>(np), tmp, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out->weights_bf16, tmp, np * 4, cudaMemcpyDefault, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+    uint32_t step0 = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&step0, q.step, 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = launch_mlp_train_step(mlp_params(h), h->stream);
+    if (e != cudaSuccess) return finish(e);
+    ++h->mlp_steps;
+    if (out->batch_idx) e = cudaMemcpyAsync(out->batch_idx, q.idx, B * 4, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess && out->target) e = cudaMemcpyAsync(out->target, q.T, B * d * 4, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess && out->output) e = cudaMemcpyAsync(out->output, q.O, B * d * 4, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess && out->grad) e = cudaMemcpyAsync(out->grad, q.grad, np * 4, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess && out->theta_after) e = cudaMemcpyAsync(out->theta_after, q.theta, np * 4, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess && out->xhat) {
+        e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = launch_bf16_to_f32(q.Xb, static_cast<int64_t>(B * D), tmp, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out->xhat, tmp, B * D * 4, cudaMemcpyDefault, h->stream);
+    }
+    double loss = 0.0;
+    float scale = 1.f;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&loss, q.loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&scale, q.scale, sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    out->loss = loss;
+    out->scale = scale;
+    out->step = static_cast<int32_t>(step0) + 1;
+    out->n_params = q.n_params;
+    return finish(e);
 }
 
 int funcsne_sync(funcsne_t* h) {
@@ -696,6 +924,8 @@ int funcsne_insert(funcsne_t* h, const float* X_new, int64_t n_new, int32_t plac
     q.P = h->P;
     q.beta = h->beta;
     FSNE_CUDA(h, launch_insert(q, h->DP, h->stream));
+    if (placement == FUNCSNE_PLACE_SURROGATE && h->mlp.ready && h->mlp_steps > 0)
+        FSNE_CUDA(h, launch_mlp_place(mlp_params(h), h->X32, h->xpitch, n_old, n_new, h->Y, h->DP, h->stream));
     // the scalars of the grown state: Zhat scaled by the ordered pair count,
     // inserted points count as points with new neighbours
     s.Zhat *= (static_cast<double>(N2) * static_cast<double>(N2 - 1)) /
@@ -768,6 +998,12 @@ int funcsne_get_stats(const funcsne_t* hc, funcsne_stats_t* st) {
     st->error_word = s.err;
     st->cand_scored = static_cast<int64_t>(s.cand_scored);
     st->cand_reranked = static_cast<int64_t>(s.cand_reranked);
+    st->mlp_steps = h->mlp_steps;
+    st->mlp_loss = 0.0;
+    if (h->mlp.ready) {
+        FSNE_CUDA(h, cudaMemcpyAsync(&st->mlp_loss, h->mlp.loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
     return FUNCSNE_OK;
 }
 
@@ -849,6 +1085,7 @@ int funcsne_import_state(funcsne_t* h, const funcsne_state_t* st) {
     s.Zhat = st->Zhat;
     s.E = st->E;
     s.t = st->t;
+    h->t_host = st->t;
     s.err = 0;
     s.ticket = 0;
     s.n_new = 0;
@@ -867,6 +1104,7 @@ int funcsne_debug_step(funcsne_t* h, float* att, float* rep) {
         FSNE_CUDA(h, e);
     }
     int rc = enqueue_iteration(h, h->stream, da, dr);
+    if (!rc) ++h->t_host;
     if (!rc) rc = copy_rows<float>(h, att, h->d, da, h->DP, h->N, h->d);
     if (!rc) rc = copy_rows<float>(h, rep, h->d, dr, h->DP, h->N, h->d);
     e = cudaStreamSynchronize(h->stream);
@@ -906,6 +1144,7 @@ int funcsne_profile_step(funcsne_t* h, int32_t n_iters, double* ms_per_kernel) {
     }
     for (auto& e : ev) cudaEventDestroy(e);
     for (int ph = 0; ph < kPhases; ++ph) ms_per_kernel[ph] = acc[ph];
+    h->t_host += static_cast<uint32_t>(n_iters);
     return rc;
 }
 

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 
 #include "params.h"
 
@@ -90,6 +91,43 @@ cudaError_t launch_ld_distances(const float* Y, const int32_t* idx, int64_t N, i
                                 cudaStream_t s);
 
 cudaError_t launch_insert(const InsertParams& q, int DP, cudaStream_t s);
+
+struct MlpParams {
+    int64_t N;                  // points the batches are drawn from
+    int32_t B, D, H, d, DP, xpitch;
+    int64_t n_params;
+    uint64_t seed;
+    float lr, beta1, beta2, eps;
+    const float* X32;
+    const float* Y;
+    const float* mu;            // D
+    const float* sigma;         // D
+    float* theta;               // FP32 master parameters (flat)
+    float* m;
+    float* v;
+    float* grad;
+    __nv_bfloat16* wb;          // bfloat16 copy of theta
+    int32_t* idx;               // B batch indices
+    float* T;                   // B x d targets (scaled)
+    __nv_bfloat16* Xb;          // B x D inputs
+    __nv_bfloat16* H1;          // B x H
+    __nv_bfloat16* H2;          // B x H
+    __nv_bfloat16* G3;          // B x d
+    __nv_bfloat16* G2;          // B x H
+    __nv_bfloat16* G1;          // B x H
+    float* O;                   // B x d outputs
+    double* part;               // reduction partials
+    double* loss;               // device scalar
+    float* scale;               // device scalar: RMS of the last batch's targets
+    uint32_t* step;             // device scalar: Adam steps taken
+};
+
+cudaError_t launch_mlp_stats(const float* X, int64_t N, int D, int xpitch, float* mu, float* sigma, cudaStream_t s);
+cudaError_t launch_mlp_init(float* theta, __nv_bfloat16* wb, int D, int H, int d, uint64_t seed, cudaStream_t s);
+cudaError_t launch_mlp_train_step(const MlpParams& q, cudaStream_t s);
+cudaError_t launch_mlp_place(const MlpParams& q, const float* X, int xpitch, int64_t first, int64_t rows, float* Y,
+                             int DP, cudaStream_t s);
+cudaError_t launch_bf16_to_f32(const __nv_bfloat16* in, int64_t n, float* out, cudaStream_t s);
 
 // evaluation
 cudaError_t launch_exact_knn(const KnnParams& kp, cudaStream_t s);

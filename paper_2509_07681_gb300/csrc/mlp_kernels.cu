@@ -1,0 +1,394 @@
+// Online MLP surrogate of the embedding map x -> y (an addition to the
+// method: it places inserted points before the iteration refines them).
+//
+// Network D-H-H-d, ReLU, bfloat16 operands with FP32 accumulation:
+//   X^ = bf16((x - mu) / sigma),  H1 = bf16(relu(X^ W1^T + b1)),
+//   H2 = bf16(relu(H1 W2^T + b2)),  O = H2 W3^T + b3,
+//   target T = y / s with s = RMS of the batch's y,  L = mean (O - T)^2,
+//   G3 = bf16(2 (O - T) / (B d)),  G2 = bf16((G3 W3) [H2 > 0]),
+//   G1 = bf16((G2 W2) [H1 > 0]),  dW3 = G3^T H2,  dW2 = G2^T H1,
+//   dW1 = G1^T X^,  db = column sums of G;  Adam with bias correction on
+//   FP32 master parameters, then the bfloat16 copy is refreshed.
+// Parameters are one flat array: W1 (H x D) b1 (H) W2 (H x H) b2 (H)
+// W3 (d x H) b3 (d). The GEMMs are tiled CUDA-core kernels: a training
+// step is ~2 GFLOP every few iterations, far below 0.1% of an iteration's
+// time, so the dense-contraction hardware would not change the step time.
+#include "device_common.cuh"
+#include "launch.h"
+
+namespace fsne {
+
+// ------------------------------------------------------------------ GEMM
+// C[m][n] = sum_k opA(m,k) opB(k,n); opA(m,k) = TA ? A[k][m] : A[m][k],
+// opB(k,n) = TB ? B[n][k] : B[k][n]; A, B bfloat16 row-major with leading
+// dimensions lda, ldb. 64 x 64 tiles, K-steps of 16, 256 threads (4 x 4 each).
+enum { kEpiBiasReluBf16 = 0, kEpiBiasF32 = 1, kEpiMaskBf16 = 2, kEpiF32 = 3 };
+
+struct GemmArgs {
+    int M, N, K, lda, ldb, ldc;
+    const __nv_bfloat16* A;
+    const __nv_bfloat16* B;
+    const float* bias;          // N (bias epilogues)
+    const __nv_bfloat16* mask;  // M x N, ldc (mask epilogue): keep where mask > 0
+    __nv_bfloat16* Cb;          // bfloat16 output
+    float* Cf;                  // FP32 output
+};
+
+template <int TA, int TB, int EPI>
+__global__ void __launch_bounds__(256) gemm_bf16_kernel(const GemmArgs g) {
+    __shared__ float As[16][64 + 4];
+    __shared__ float Bs[16][64 + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int k0 = 0; k0 < g.K; k0 += 16) {
+        // load a 64 x 16 tile of opA and a 16 x 64 tile of opB (4 elements per thread)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = threadIdx.x + 256 * q;  // 0..1023
+            const int kk = e & 15, mm = e >> 4;   // A tile: (mm, kk)
+            const int m = m0 + mm, k = k0 + kk;
+            float va = 0.f;
+            if (m < g.M && k < g.K)
+                va = __bfloat162float(TA ? g.A[static_cast<int64_t>(k) * g.lda + m] : g.A[static_cast<int64_t>(m) * g.lda + k]);
+            As[kk][mm] = va;
+            const int nn = e & 63, kb = e >> 6;   // B tile: (kb, nn)
+            const int n = n0 + nn, k2 = k0 + kb;
+            float vb = 0.f;
+            if (n < g.N && k2 < g.K)
+                vb = __bfloat162float(TB ? g.B[static_cast<int64_t>(n) * g.ldb + k2] : g.B[static_cast<int64_t>(k2) * g.ldb + n]);
+            Bs[kb][nn] = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = __fmaf_rn(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int m = m0 + ty * 4 + r;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int n = n0 + tx * 4 + c;
+            if (n >= g.N) continue;
+            const int64_t o = static_cast<int64_t>(m) * g.ldc + n;
+            float v = acc[r][c];
+            if constexpr (EPI == kEpiBiasReluBf16) {
+                v += g.bias[n];
+                g.Cb[o] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+            } else if constexpr (EPI == kEpiBiasF32) {
+                g.Cf[o] = v + g.bias[n];
+            } else if constexpr (EPI == kEpiMaskBf16) {
+                g.Cb[o] = __bfloat162float(g.mask[o]) > 0.f ? __float2bfloat16_rn(v) : __float2bfloat16_rn(0.f);
+            } else {
+                g.Cf[o] = v;
+            }
+        }
+    }
+}
+
+template <int TA, int TB, int EPI>
+static void gemm(const GemmArgs& g, cudaStream_t s) {
+    const dim3 grid((g.N + 63) / 64, (g.M + 63) / 64);
+    gemm_bf16_kernel<TA, TB, EPI><<<grid, 256, 0, s>>>(g);
+}
+
+// ------------------------------------------------------------------ data
+// Per-feature mean and standard deviation of the first N rows (FP64 sums).
+__global__ void mlp_stats_kernel(const float* __restrict__ X, int64_t N, int xpitch, float* mu, float* sigma) {
+    const int f = blockIdx.x;
+    double s = 0.0, s2 = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double v = X[i * xpitch + f];
+        s += v;
+        s2 += v * v;
+    }
+    __shared__ double ps[256], ps2[256];
+    ps[threadIdx.x] = s;
+    ps2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            ps[threadIdx.x] += ps[threadIdx.x + w];
+            ps2[threadIdx.x] += ps2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double m = ps[0] / static_cast<double>(N);
+        const double var = ps2[0] / static_cast<double>(N) - m * m;
+        mu[f] = static_cast<float>(m);
+        sigma[f] = var > 0.0 ? static_cast<float>(sqrt(var)) : 1.f;
+    }
+}
+
+// Normalised bfloat16 input rows X^ of the given point indices.
+__global__ void mlp_inputs_kernel(const float* __restrict__ X, int xpitch, int D, const int32_t* __restrict__ idx,
+                                  int64_t first, int rows, const float* __restrict__ mu,
+                                  const float* __restrict__ sigma, __nv_bfloat16* Xb) {
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= static_cast<int64_t>(rows) * D) return;
+    const int r = static_cast<int>(e / D), f = static_cast<int>(e % D);
+    const int64_t i = idx ? idx[r] : first + r;
+    Xb[e] = __float2bfloat16_rn((X[i * xpitch + f] - mu[f]) / sigma[f]);
+}
+
+// Batch of the training step `step`: row b is point map(w0, N) of the
+// Philox block at counter (step, b, MLP, 0); targets y (scaled later).
+__global__ void mlp_batch_kernel(MlpParams q) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t step = *q.step;
+    __shared__ double red[256];
+    double acc = 0.0;
+    if (b < q.B) {
+        const uint4 w = philox(step, static_cast<uint32_t>(b), kStreamMlp, 0u, q.seed);
+        const uint32_t i = map_index(w.x, static_cast<uint32_t>(q.N));
+        q.idx[b] = static_cast<int32_t>(i);
+        for (int c = 0; c < q.d; ++c) {
+            const float y = q.Y[static_cast<int64_t>(i) * q.DP + c];
+            q.T[b * q.d + c] = y;
+            acc += static_cast<double>(y) * y;
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) q.part[blockIdx.x] = red[0];
+}
+
+// s = RMS of the batch targets (1 when zero); targets divided by s.
+__global__ void mlp_scale_kernel(MlpParams q, int nparts) {
+    __shared__ float s_scale;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < nparts; ++b) t += q.part[b];
+        const double ms = t / (static_cast<double>(q.B) * q.d);
+        const float s = ms > 0.0 ? static_cast<float>(sqrt(ms)) : 1.f;
+        s_scale = s;
+        *q.scale = s;
+    }
+    __syncthreads();
+    const float inv = 1.f / s_scale;
+    for (int e = threadIdx.x; e < q.B * q.d; e += blockDim.x) q.T[e] *= inv;
+}
+
+// G3 = bf16(2 (O - T) / (B d)); loss partials.
+__global__ void mlp_loss_kernel(MlpParams q) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double red[256];
+    double l = 0.0;
+    if (e < q.B * q.d) {
+        const float r = q.O[e] - q.T[e];
+        l = static_cast<double>(r) * r;
+        q.G3[e] = __float2bfloat16_rn(2.f * r / static_cast<float>(q.B * q.d));
+    }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) q.part[blockIdx.x] = red[0];
+}
+
+__global__ void mlp_loss_finish_kernel(MlpParams q, int nparts) {
+    if (threadIdx.x != 0) return;
+    double t = 0.0;
+    for (int b = 0; b < nparts; ++b) t += q.part[b];
+    *q.loss = t / (static_cast<double>(q.B) * q.d);
+}
+
+// out[c] = sum over rows of G[r][c] (bias gradients), FP32.
+__global__ void mlp_colsum_kernel(const __nv_bfloat16* __restrict__ G, int rows, int cols, float* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += __bfloat162float(G[static_cast<int64_t>(r) * cols + c]);
+    out[c] = s;
+}
+
+// Adam with bias correction; refreshes the bfloat16 copy; step advances in
+// mlp_step_kernel.
+__global__ void mlp_adam_kernel(MlpParams q) {
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= q.n_params) return;
+    const int step = static_cast<int>(*q.step) + 1;
+    const float c1 = 1.f - powf(q.beta1, static_cast<float>(step));
+    const float c2 = 1.f - powf(q.beta2, static_cast<float>(step));
+    const float g = q.grad[e];
+    const float m = q.beta1 * q.m[e] + (1.f - q.beta1) * g;
+    const float v = q.beta2 * q.v[e] + (1.f - q.beta2) * g * g;
+    q.m[e] = m;
+    q.v[e] = v;
+    const float th = q.theta[e] - q.lr * (m / c1) / (sqrtf(v / c2) + q.eps);
+    q.theta[e] = th;
+    q.wb[e] = __float2bfloat16_rn(th);
+}
+
+__global__ void mlp_step_kernel(MlpParams q) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *q.step += 1u;
+}
+
+// Y[first + r][c] = s O[r][c] for the placed rows (LD padding untouched).
+__global__ void mlp_place_kernel(const float* __restrict__ O, int rows, int d, int DP, int64_t first,
+                                 const float* __restrict__ scale, float* Y) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * d) return;
+    const int r = e / d, c = e % d;
+    Y[(first + r) * DP + c] = *scale * O[e];
+}
+
+// ------------------------------------------------------------------ host side
+static int blocks_for(int64_t n, int t) { return static_cast<int>((n + t - 1) / t); }
+
+cudaError_t launch_mlp_stats(const float* X, int64_t N, int D, int xpitch, float* mu, float* sigma, cudaStream_t s) {
+    mlp_stats_kernel<<<D, 256, 0, s>>>(X, N, xpitch, mu, sigma);
+    return cudaGetLastError();
+}
+
+// forward of `rows` input rows already in q.Xb: H1, H2, O.
+static void mlp_forward(const MlpParams& q, int rows, cudaStream_t s) {
+    const int D = q.D, H = q.H, d = q.d;
+    const __nv_bfloat16* W1 = q.wb;
+    const __nv_bfloat16* W2 = q.wb + static_cast<int64_t>(H) * D + H;
+    const __nv_bfloat16* W3 = W2 + static_cast<int64_t>(H) * H + H;
+    const float* b1 = q.theta + static_cast<int64_t>(H) * D;
+    const float* b2 = b1 + H + static_cast<int64_t>(H) * H;
+    const float* b3 = b2 + H + static_cast<int64_t>(d) * H;
+    GemmArgs g{};
+    g.M = rows; g.N = H; g.K = D; g.lda = D; g.ldb = D; g.ldc = H;
+    g.A = q.Xb; g.B = W1; g.bias = b1; g.Cb = q.H1;
+    gemm<0, 1, kEpiBiasReluBf16>(g, s);
+    g.K = H; g.lda = H; g.ldb = H; g.A = q.H1; g.B = W2; g.bias = b2; g.Cb = q.H2;
+    gemm<0, 1, kEpiBiasReluBf16>(g, s);
+    g.N = d; g.ldc = d; g.A = q.H2; g.B = W3; g.bias = b3; g.Cb = nullptr; g.Cf = q.O;
+    gemm<0, 1, kEpiBiasF32>(g, s);
+}
+
+cudaError_t launch_mlp_train_step(const MlpParams& q, cudaStream_t s) {
+    const int B = q.B, D = q.D, H = q.H, d = q.d;
+    const int nb = blocks_for(B, 256);
+    mlp_batch_kernel<<<nb, 256, 0, s>>>(q);
+    mlp_scale_kernel<<<1, 256, 0, s>>>(q, nb);
+    mlp_inputs_kernel<<<blocks_for(static_cast<int64_t>(B) * D, 256), 256, 0, s>>>(q.X32, q.xpitch, D, q.idx, 0, B,
+                                                                                   q.mu, q.sigma, q.Xb);
+    mlp_forward(q, B, s);
+    const int nl = blocks_for(static_cast<int64_t>(B) * d, 256);
+    mlp_loss_kernel<<<nl, 256, 0, s>>>(q);
+    mlp_loss_finish_kernel<<<1, 32, 0, s>>>(q, nl);
+    // backward
+    const __nv_bfloat16* W2 = q.wb + static_cast<int64_t>(H) * D + H;
+    const __nv_bfloat16* W3 = W2 + static_cast<int64_t>(H) * H + H;
+    float* gW1 = q.grad;
+    float* gb1 = gW1 + static_cast<int64_t>(H) * D;
+    float* gW2 = gb1 + H;
+    float* gb2 = gW2 + static_cast<int64_t>(H) * H;
+    float* gW3 = gb2 + H;
+    float* gb3 = gW3 + static_cast<int64_t>(d) * H;
+    GemmArgs g{};
+    // dW3 = G3^T H2 (d x H)
+    g.M = d; g.N = H; g.K = B; g.lda = d; g.ldb = H; g.ldc = H; g.A = q.G3; g.B = q.H2; g.Cf = gW3;
+    gemm<1, 0, kEpiF32>(g, s);
+    // G2 = (G3 W3) [H2 > 0]  (B x H)
+    g = GemmArgs{};
+    g.M = B; g.N = H; g.K = d; g.lda = d; g.ldb = H; g.ldc = H; g.A = q.G3; g.B = W3; g.mask = q.H2; g.Cb = q.G2;
+    gemm<0, 0, kEpiMaskBf16>(g, s);
+    // dW2 = G2^T H1 (H x H)
+    g = GemmArgs{};
+    g.M = H; g.N = H; g.K = B; g.lda = H; g.ldb = H; g.ldc = H; g.A = q.G2; g.B = q.H1; g.Cf = gW2;
+    gemm<1, 0, kEpiF32>(g, s);
+    // G1 = (G2 W2) [H1 > 0]  (B x H)
+    g = GemmArgs{};
+    g.M = B; g.N = H; g.K = H; g.lda = H; g.ldb = H; g.ldc = H; g.A = q.G2; g.B = W2; g.mask = q.H1; g.Cb = q.G1;
+    gemm<0, 0, kEpiMaskBf16>(g, s);
+    // dW1 = G1^T X^ (H x D)
+    g = GemmArgs{};
+    g.M = H; g.N = D; g.K = B; g.lda = H; g.ldb = D; g.ldc = D; g.A = q.G1; g.B = q.Xb; g.Cf = gW1;
+    gemm<1, 0, kEpiF32>(g, s);
+    mlp_colsum_kernel<<<blocks_for(d, 128), 128, 0, s>>>(q.G3, B, d, gb3);
+    mlp_colsum_kernel<<<blocks_for(H, 128), 128, 0, s>>>(q.G2, B, H, gb2);
+    mlp_colsum_kernel<<<blocks_for(H, 128), 128, 0, s>>>(q.G1, B, H, gb1);
+    mlp_adam_kernel<<<blocks_for(q.n_params, 256), 256, 0, s>>>(q);
+    mlp_step_kernel<<<1, 32, 0, s>>>(q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_place(const MlpParams& q, const float* X, int xpitch, int64_t first, int64_t rows, float* Y,
+                             int DP, cudaStream_t s) {
+    for (int64_t r0 = 0; r0 < rows; r0 += q.B) {
+        const int n = static_cast<int>(rows - r0 < q.B ? rows - r0 : q.B);
+        mlp_inputs_kernel<<<blocks_for(static_cast<int64_t>(n) * q.D, 256), 256, 0, s>>>(
+            X, xpitch, q.D, nullptr, first + r0, n, q.mu, q.sigma, q.Xb);
+        mlp_forward(q, n, s);
+        mlp_place_kernel<<<blocks_for(static_cast<int64_t>(n) * q.d, 256), 256, 0, s>>>(q.O, n, q.d, DP, first + r0,
+                                                                                        q.scale, Y);
+    }
+    return cudaGetLastError();
+}
+
+// Initial parameters: weights of layer l (0-based) uniform in (-a, a) with
+// a = sqrt(6 / fan_in) for l < 2 and sqrt(3 / fan_in) for the output layer;
+// entry (r, c) from word c mod 4 of the Philox block at counter
+// (l + 1, r, MLP_INIT, c div 4) as a (2 (w + 0.5) 2^-32 - 1) in FP64,
+// rounded to binary32; biases 0.
+__global__ void mlp_init_kernel(float* theta, __nv_bfloat16* wb, int D, int H, int d, uint64_t seed) {
+    const int64_t n1 = static_cast<int64_t>(H) * D, n2 = static_cast<int64_t>(H) * H, n3 = static_cast<int64_t>(d) * H;
+    const int64_t total = n1 + H + n2 + H + n3 + d;
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    int layer = -1, cols = 0;
+    int64_t off = e;
+    if (off < n1) { layer = 0; cols = D; }
+    else if ((off -= n1) < H) { layer = -1; }
+    else if ((off -= H) < n2) { layer = 1; cols = H; }
+    else if ((off -= n2) < H) { layer = -1; }
+    else if ((off -= H) < n3) { layer = 2; cols = H; }
+    float v = 0.f;
+    if (layer >= 0) {
+        const int r = static_cast<int>(off / cols), c = static_cast<int>(off % cols);
+        const uint4 w = philox(static_cast<uint32_t>(layer + 1), static_cast<uint32_t>(r), kStreamMlpInit,
+                               static_cast<uint32_t>(c / 4), seed);
+        const uint32_t word = (c & 3) == 0 ? w.x : (c & 3) == 1 ? w.y : (c & 3) == 2 ? w.z : w.w;
+        const double a = sqrt((layer < 2 ? 6.0 : 3.0) / static_cast<double>(cols));
+        const double u = (static_cast<double>(word) + 0.5) * (1.0 / 4294967296.0);
+        v = static_cast<float>(a * (2.0 * u - 1.0));
+    }
+    theta[e] = v;
+    wb[e] = __float2bfloat16_rn(v);
+}
+
+cudaError_t launch_mlp_init(float* theta, __nv_bfloat16* wb, int D, int H, int d, uint64_t seed, cudaStream_t s) {
+    const int64_t total = static_cast<int64_t>(H) * D + H + static_cast<int64_t>(H) * H + H + static_cast<int64_t>(d) * H + d;
+    mlp_init_kernel<<<blocks_for(total, 256), 256, 0, s>>>(theta, wb, D, H, d, seed);
+    return cudaGetLastError();
+}
+
+__global__ void bf16_to_f32_kernel(const __nv_bfloat16* in, int64_t n, float* out) {
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = __bfloat162float(in[e]);
+}
+
+cudaError_t launch_bf16_to_f32(const __nv_bfloat16* in, int64_t n, float* out, cudaStream_t s) {
+    bf16_to_f32_kernel<<<blocks_for(n, 256), 256, 0, s>>>(in, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fsne

@@ -12,7 +12,8 @@ constexpr uint32_t kStreamCoin = 0;
 // One block per (iteration, point, slot) drives both refinements: words 0-1
 // the HD candidate of slot s, words 2-3 the LD candidate of slot s.
 constexpr uint32_t kStreamRefine = 1;
-constexpr uint32_t kStreamMlp = 4;
+constexpr uint32_t kStreamMlp = 4;       // training batches
+constexpr uint32_t kStreamMlpInit = 10;  // initial MLP parameters
 constexpr uint32_t kStreamInsert = 5;
 constexpr uint32_t kStreamInitHd = 6;
 constexpr uint32_t kStreamInitLd = 7;

@@ -15,7 +15,7 @@ import os
 import numpy as np
 
 __all__ = ["load", "FuncSNEError", "FuncSNE", "FP32", "BF16", "FP8", "SPACE_HD", "SPACE_LD",
-           "PLACE_MEAN", "PLACE_SURROGATE", "State", "Stats", "ABI_FUNCTIONS"]
+           "PLACE_MEAN", "PLACE_SURROGATE", "State", "Stats", "MlpDebug", "ABI_FUNCTIONS"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfuncsne.so")
@@ -43,7 +43,14 @@ class Stats(C.Structure):
     _fields_ = [("N", C.c_int64), ("t", C.c_uint32), ("E", C.c_double), ("Zhat", C.c_double),
                 ("last_Z", C.c_double), ("last_n_new", C.c_int64), ("last_coin", C.c_int32),
                 ("precision", C.c_int32), ("error_word", C.c_uint32), ("cand_scored", C.c_int64),
-                ("cand_reranked", C.c_int64)]
+                ("cand_reranked", C.c_int64), ("mlp_steps", C.c_int64), ("mlp_loss", C.c_double)]
+
+
+class MlpDebug(C.Structure):
+    _fields_ = [("batch_idx", C.c_void_p), ("xhat", C.c_void_p), ("target", C.c_void_p), ("output", C.c_void_p),
+                ("theta_before", C.c_void_p), ("weights_bf16", C.c_void_p), ("grad", C.c_void_p),
+                ("theta_after", C.c_void_p), ("loss", C.c_double), ("scale", C.c_float), ("step", C.c_int32),
+                ("n_params", C.c_int64)]
 
 
 _h = C.c_void_p
@@ -67,6 +74,9 @@ ABI_FUNCTIONS = {
     "funcsne_exact_knn": (C.c_int, [_h, _vp, C.c_int64, C.c_int32, _vp, _vp]),
     "funcsne_exact_knn_noalloc": (C.c_int, [_vp, C.c_int64, C.c_int32, C.c_int32, _vp, C.c_int64, C.c_int32,
                                             _vp, _vp, _vp]),
+    "funcsne_mlp_train": (C.c_int, [_h, C.c_int32]),
+    "funcsne_mlp_predict": (C.c_int, [_h, _vp, C.c_int64, _vp]),
+    "funcsne_mlp_debug_step": (C.c_int, [_h, C.POINTER(MlpDebug)]),
     "funcsne_last_error": (C.c_char_p, [_h]),
     "funcsne_destroy": (None, [_h]),
 }
@@ -231,6 +241,28 @@ def funcsne_exact_knn_noalloc(X, N, D, ldx, queries, k, idx, d2=None, stream=Non
     return idx, d2
 
 
+def funcsne_mlp_train(h, n_steps):
+    _check(load().funcsne_mlp_train(h, int(n_steps)), h)
+
+
+def funcsne_mlp_predict(h, X, out):
+    px, k0 = _ptr(X)
+    po, k1 = _ptr(out)
+    _check(load().funcsne_mlp_predict(h, px, X.shape[0], po), h)
+    return out
+
+
+def funcsne_mlp_debug_step(h, arrays):
+    st = MlpDebug()
+    keep = []
+    for f in ("batch_idx", "xhat", "target", "output", "theta_before", "weights_bf16", "grad", "theta_after"):
+        p, k = _ptr(arrays.get(f))
+        setattr(st, f, p)
+        keep.append(k)
+    _check(load().funcsne_mlp_debug_step(h, C.byref(st)), h)
+    return dict(loss=st.loss, scale=st.scale, step=st.step, n_params=st.n_params)
+
+
 def funcsne_last_error(h=None):
     m = load().funcsne_last_error(h)
     return m.decode() if m else ""
@@ -318,6 +350,27 @@ class FuncSNE:
         d2 = np.empty((len(q), k), np.float32)
         funcsne_exact_knn(self.h, q, k, idx, d2)
         return idx, d2
+
+    def mlp_train(self, n_steps=1):
+        funcsne_mlp_train(self.h, n_steps)
+
+    def mlp_predict(self, X):
+        X = _as_f32(X)
+        out = np.empty((X.shape[0], self.d), np.float32)
+        return funcsne_mlp_predict(self.h, X, out)
+
+    def mlp_debug_step(self):
+        """One training step of the placement MLP; returns its inputs, outputs,
+        gradient and parameters before / after (numpy arrays)."""
+        B = int(self.get_option("mlp_batch"))
+        H = int(self.get_option("mlp_hidden"))
+        n = H * self.D + H + H * H + H + self.d * H + self.d
+        a = dict(batch_idx=np.empty(B, np.int32), xhat=np.empty((B, self.D), np.float32),
+                 target=np.empty((B, self.d), np.float32), output=np.empty((B, self.d), np.float32),
+                 theta_before=np.empty(n, np.float32), weights_bf16=np.empty(n, np.float32),
+                 grad=np.empty(n, np.float32), theta_after=np.empty(n, np.float32))
+        a.update(funcsne_mlp_debug_step(self.h, a))
+        return a
 
     def insert(self, X_new, placement=PLACE_MEAN):
         X_new = _as_f32(X_new)

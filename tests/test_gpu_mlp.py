@@ -1,0 +1,138 @@
+"""GPU parity of the placement MLP (forward, backward, Adam) against the FP64
+oracle on identical bfloat16 operands, and what the trained network gains
+over mean placement of inserted points."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_07681_gb300 import funcsne as F
+from paper_2509_07681_gb300 import synth
+from paper_2509_07681_gb300.quality import recall
+
+from gpu_util import lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lib()
+
+
+def _split_theta(th, D, H, d):
+    o = [0, H * D, H * D + H, H * D + H + H * H, H * D + 2 * H + H * H, H * D + 2 * H + H * H + d * H]
+    return o
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def test_mlp_step_matches_oracle():
+    X = synth.swissroll(n=3000, dim=24, n_clusters=8, seed=30)
+    D, d, H, B = 24, 4, 64, 512
+    m = F.FuncSNE(X, d, 16, 8, 8, 1.0, 10.0, seed=3)
+    m.set_option("mlp_batch", B)
+    m.set_option("mlp_hidden", H)
+    m.step(30)
+    Y = m.embedding().astype(np.float64)
+    for it in range(2):
+        a = m.mlp_debug_step()
+        assert a["step"] == it + 1
+        # the batch: Philox counter (step, b, MLP, 0), word 0 mapped to [0, N)
+        w0 = np.array([O.philox([it, b, 4, 0], [3, 0])[0] for b in range(B)], dtype=np.uint64)
+        np.testing.assert_array_equal(a["batch_idx"], ((w0 * 3000) >> 32).astype(np.int32))
+        idx = a["batch_idx"]
+        # inputs: bfloat16 of the standardised rows (FP64 statistics here)
+        mu, sd = X.astype(np.float64).mean(0), X.astype(np.float64).std(0)
+        ref_x = O.bf16((X[idx] - mu) / sd)
+        assert np.mean(a["xhat"] == ref_x) > 0.995
+        assert np.max(np.abs(a["xhat"] - ref_x) / np.maximum(np.abs(ref_x), 1e-3)) <= 2 ** -7
+        # targets: y / RMS over the batch
+        s = np.sqrt(np.mean(Y[idx] ** 2))
+        assert abs(a["scale"] - s) <= 1e-5 * s
+        np.testing.assert_allclose(a["target"], Y[idx] / a["scale"], rtol=1e-6, atol=1e-7)
+        # forward / backward on the same bfloat16 weights and FP32 biases
+        o = _split_theta(None, D, H, d)
+        th = a["weights_bf16"].astype(np.float64).copy()
+        for lo, hi in [(o[1], o[2]), (o[3], o[4]), (o[5], len(th))]:
+            th[lo:hi] = a["theta_before"][lo:hi]
+        loss, g, out = O.mlp_grad(th, a["xhat"], a["target"], H, round_bf16=True)
+        assert abs(a["loss"] - loss) <= 1e-4 * loss
+        assert _rel(a["output"], out) < 1e-4
+        for lo, hi in zip(o, o[1:] + [len(th)]):
+            assert _rel(a["grad"][lo:hi], g[lo:hi]) < 1e-3, (lo, hi)
+        # Adam from the exported moments' state: first steps from zero moments
+        if it == 0:
+            th0 = a["theta_before"].astype(np.float64)
+            mm = np.zeros_like(th0)
+            vv = np.zeros_like(th0)
+            O.adam(th0, a["grad"].astype(np.float64), mm, vv, 1, lr=1e-3)
+            np.testing.assert_allclose(a["theta_after"], th0, rtol=1e-5, atol=1e-6)
+    m.close()
+
+
+def test_mlp_training_reduces_loss_and_predicts():
+    X = synth.swissroll(n=6000, dim=32, n_clusters=10, seed=31)
+    m = F.FuncSNE(X, 4, 16, 8, 8, 1.0, 10.0, seed=4)
+    m.set_option("mlp_batch", 1024)
+    m.step(200)
+    first = m.mlp_debug_step()["loss"]
+    m.mlp_train(300)
+    last = m.stats()["mlp_loss"]
+    assert last < 0.5 * first
+    pred = m.mlp_predict(X[:500])
+    Y = m.embedding()[:500]
+    # the learned map explains most of the embedding's variance
+    r2 = 1 - np.sum((pred - Y) ** 2) / np.sum((Y - Y.mean(0)) ** 2)
+    assert r2 > 0.5
+    m.close()
+
+
+def _placement_run(base, new, p, place, settle=60):
+    m = F.FuncSNE(base, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=5)
+    m.set_option("surrogate", 1)
+    m.set_option("mlp_batch", 2048)
+    m.step(400)
+    m.mlp_train(200)
+    first = m.insert(new, placement=F.PLACE_MEAN if place == "random" else place)
+    Y0 = m.embedding()[first:].astype(np.float64)
+    if place == "random":
+        # a random existing point's position: the no-information baseline
+        rng = np.random.default_rng(0)
+        Y0 = m.embedding()[rng.integers(0, first, len(new))].astype(np.float64)
+        st = m.export_state()
+        st["Y"][first:] = Y0
+        m.import_state(st)
+    m.step(settle)
+    Y = m.embedding().astype(np.float64)
+    scale = np.sqrt(np.mean(Y[:first] ** 2))
+    move = np.sqrt(np.mean(np.sum((Y[first:] - Y0) ** 2, 1))) / scale
+    hd = m.knn(F.SPACE_HD, with_d2=False)[first:]
+    m.close()
+    return move, Y, hd, first
+
+
+def test_surrogate_placement_against_mean_placement():
+    """Dynamic dataset: 2,000 points inserted into a 10,000-point embedding.
+    Measures, for mean, surrogate and random placement, how far the new
+    points still move over the next 60 iterations (relative to the
+    embedding's RMS) and their LD-neighbourhood recall of the exact HD
+    neighbours afterwards. Informed placements must beat the random one;
+    the two informed ones are reported side by side."""
+    X = synth.swissroll(n=12000, dim=32, n_clusters=16, seed=32)
+    base, new = X[:10000], X[10000:]
+    p = dict(d=4, k_hd=16, k_ld=8, n_neg=8, alpha=1.0, perplexity=10.0)
+    ex, _ = O.query_knn(X, np.arange(10000, 12000), 16)
+    res = {}
+    for place in (F.PLACE_MEAN, F.PLACE_SURROGATE, "random"):
+        move, Y, hd, first = _placement_run(base, new, p, place)
+        d2 = ((Y[first:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+        d2[np.arange(2000), first + np.arange(2000)] = np.inf
+        ld = np.argsort(d2, axis=1)[:, :16]
+        res[place] = (move, recall(ld, ex), recall(hd, ex))
+    for k, (mv, rl, rh) in res.items():
+        print(f"placement {k}: movement {mv:.3f}, LD recall@16 {rl:.3f}, HD recall@16 {rh:.3f}")
+    for place in (F.PLACE_MEAN, F.PLACE_SURROGATE):
+        assert res[place][0] < res["random"][0]
+        assert np.isfinite(res[place][0])
