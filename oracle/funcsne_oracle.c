@@ -1034,3 +1034,69 @@ void oracle_adam(int64_t n, double *theta, const double *g, double *m, double *v
         theta[e] -= lr * (m[e] / c1) / (sqrt(v[e] / c2) + eps);
     }
 }
+
+/*
+ * Forces of selected points only (same definitions as oracle_forces), for
+ * checking a large state on a sample: A and R rows of pts[0..n) in A_out,
+ * R_out (n x d). The reverse attraction of point i sums over every j with i
+ * in N_HD(j), found by one scan of all lists.
+ */
+void oracle_forces_points(const oracle_state *st, uint32_t t, uint32_t neg_stream, double zhat,
+                          const int64_t *pts, int64_t n, double *A_out, double *R_out)
+{
+    int64_t N = st->N;
+    int d = st->d, kh = st->k_hd, kl = st->k_ld;
+    double alpha = st->alpha;
+    memset(A_out, 0, sizeof(double) * (size_t)(n * d));
+    memset(R_out, 0, sizeof(double) * (size_t)(n * d));
+    /* position of each sampled point in the output (or -1) */
+    int64_t *slot = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    for (int64_t i = 0; i < N; ++i) slot[i] = -1;
+    for (int64_t a = 0; a < n; ++a) slot[pts[a]] = a;
+    /* attraction: out-edges of sampled points and in-edges from every point */
+    for (int64_t j = 0; j < N; ++j) {
+        for (int e = 0; e < kh; ++e) {
+            int64_t i = st->hd_idx[j * kh + e];
+            int64_t sj = slot[j], si = slot[i];
+            if (sj < 0 && si < 0) continue;
+            const double *yj = st->Y + j * d, *yi = st->Y + i * d;
+            double r2 = sqdist(yj, yi, d);
+            double coef = 4.0 * (st->P[j * kh + e] / (2.0 * (double)N)) * kernel_w_inv_alpha(r2, alpha);
+            for (int c = 0; c < d; ++c) {
+                double f = coef * (yj[c] - yi[c]); /* force of pair (j, i) on j */
+                if (sj >= 0) A_out[sj * d + c] += f;
+                if (si >= 0) A_out[si * d + c] -= f;
+            }
+        }
+    }
+    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)(kh + kl));
+    for (int64_t a = 0; a < n; ++a) {
+        int64_t i = pts[a];
+        const double *yi = st->Y + i * d;
+        int ns = 0;
+        for (int e = 0; e < kh; ++e) S[ns++] = st->hd_idx[i * kh + e];
+        for (int e = 0; e < kl; ++e) {
+            int32_t j = st->ld_idx[i * kl + e];
+            if (!contains(st->hd_idx + i * kh, kh, j)) S[ns++] = j;
+        }
+        for (int e = 0; e < ns; ++e) {
+            const double *yj = st->Y + (int64_t)S[e] * d;
+            double r2 = sqdist(yi, yj, d);
+            double coef = 4.0 * (kernel_w(r2, alpha) / zhat) * kernel_w_inv_alpha(r2, alpha);
+            for (int c = 0; c < d; ++c) R_out[a * d + c] += coef * (yi[c] - yj[c]);
+        }
+        double scale = (double)(N - 1) / (double)st->n_neg;
+        for (int s = 0; s < st->n_neg; ++s) {
+            uint32_t w4[4];
+            draw4(st->seed, t, (uint32_t)i, neg_stream, (uint32_t)(s % 32), w4);
+            int64_t j = map_other(negative_word(w4[1], w4[3], (uint32_t)(s / 32)), N, i);
+            if (contains(S, ns, j)) continue;
+            const double *yj = st->Y + j * d;
+            double r2 = sqdist(yi, yj, d);
+            double coef = scale * 4.0 * (kernel_w(r2, alpha) / zhat) * kernel_w_inv_alpha(r2, alpha);
+            for (int c = 0; c < d; ++c) R_out[a * d + c] += coef * (yi[c] - yj[c]);
+        }
+    }
+    free(S);
+    free(slot);
+}

@@ -89,6 +89,8 @@ def _declare(L):
     L.oracle_query_knn.restype = None
     L.oracle_insert.argtypes = [sp, C.c_int64, C.c_double, C.c_int]
     L.oracle_insert.restype = None
+    L.oracle_forces_points.argtypes = [sp, C.c_uint32, C.c_uint32, C.c_double, _lp, C.c_int64, _dp, _dp]
+    L.oracle_forces_points.restype = None
     L.oracle_bf16.argtypes = [C.c_double]
     L.oracle_bf16.restype = C.c_double
     L.oracle_mlp_init.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, _dp]
@@ -309,8 +311,9 @@ class OracleState:
             self._s.E = E
         if t is not None:
             self._s.t = t
-        diff = self.X[:, None, :] - self.X[self.hd_idx]
-        self.hd_d2[...] = np.einsum("nkd,nkd->nk", diff, diff)
+        for a in range(0, self.N, 32768):
+            diff = self.X[a:a + 32768, None, :] - self.X[self.hd_idx[a:a + 32768]]
+            self.hd_d2[a:a + 32768] = np.einsum("nkd,nkd->nk", diff, diff)
 
     def coin(self):
         return bool(lib().oracle_coin(C.byref(self._s)))
@@ -334,6 +337,16 @@ class OracleState:
                                  self._s.Zhat if zhat is None else zhat, _p(A, _dp), _p(R, _dp),
                                  _p(z, _dp))
         return A, R, zt, z
+
+    def forces_points(self, pts, zhat=None, t=None, stream=STREAMS["REFINE"]):
+        """(A, R) rows of the points pts only (for a sample of a large state)."""
+        pts = np.ascontiguousarray(pts, dtype=np.int64)
+        A = np.zeros((len(pts), self.d))
+        R = np.zeros((len(pts), self.d))
+        lib().oracle_forces_points(C.byref(self._s), self._s.t if t is None else t, stream,
+                                   self._s.Zhat if zhat is None else zhat, _p(pts, _lp), len(pts),
+                                   _p(A, _dp), _p(R, _dp))
+        return A, R
 
     def step(self, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
         """One iteration. Returns dict(A, R, flags, coin, n_new, z)."""

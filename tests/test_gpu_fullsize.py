@@ -1,0 +1,89 @@
+"""Parity at the benchmark's full size and launch configuration: the 1M-point
+spectrum workload (D=50, d=16, k_hd=k_ld=n_neg=32), BF16 rows, HD refinement
+every iteration. One GPU iteration; on a sample of points (including the
+first and last rows, so the grid's ragged tail), the oracle recomputes each
+point's HD and LD refinement and its forces one by one."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2509_07681_gb300 import funcsne as F
+from paper_2509_07681_gb300 import synth
+
+from gpu_util import fp32_band, lib, oracle_from_state, rel_err_rows
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", [F.BF16])
+def test_full_size_sampled_parity(precision):
+    lib()
+    X, p = synth.make("spectrum-1m")
+    N, D = X.shape
+    m = F.FuncSNE(X, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0)
+    m.set_option("hd_mode", 1)
+    m.set_option("precision", precision)
+    m.step(20)
+    m.sync()
+    st0 = m.export_state()
+    att, rep = m.debug_step()
+    st1 = m.export_state()
+    lr = m.get_option("lr")
+    m.close()
+
+    rng = np.random.default_rng(7)
+    pts = np.unique(np.concatenate([rng.choice(N, 300, replace=False), [0, 1, 7, N - 8, N - 2, N - 1]]))
+    o0 = oracle_from_state(X, st0, p, hd_mode=1)
+    X64 = o0.X
+    Y0 = st0["Y"].astype(np.float64)
+    band = fp32_band(D)
+    hd_new = np.empty((len(pts), p["k_hd"]), np.int32)
+    ld_new = np.empty((len(pts), p["k_ld"]), np.int32)
+    for a, i in enumerate(pts):
+        cand = o0.hd_candidates(i)
+        cd2 = ((X64[cand] - X64[i]) ** 2).sum(1)
+        old = st0["hd_idx"][i]
+        od2 = ((X64[old] - X64[i]) ** 2).sum(1)
+        hd_new[a], _, _ = O.topk_merge(i, old, od2, cand, cd2)
+        cand = o0.ld_candidates(i)
+        cd2 = ((Y0[cand] - Y0[i]) ** 2).sum(1)
+        old = st0["ld_idx"][i]
+        od2 = ((Y0[old] - Y0[i]) ** 2).sum(1)
+        ld_new[a], _, _ = O.topk_merge(i, old, od2, cand, cd2)
+    gpu_hd = st1["hd_idx"][pts]
+    gpu_ld = st1["ld_idx"][pts]
+    bad = amb = 0
+    for a, i in enumerate(pts):
+        s_gpu, s_or = set(gpu_hd[a].tolist()), set(hd_new[a].tolist())
+        if s_gpu != s_or:
+            diff = np.array(sorted(s_gpu ^ s_or))
+            kth = ((X64[hd_new[a]] - X64[i]) ** 2).sum(1).max()
+            dd = ((X64[diff] - X64[i]) ** 2).sum(1)
+            amb += int(np.all(np.abs(dd - kth) <= band * kth))
+            bad += int(not np.all(np.abs(dd - kth) <= band * kth))
+    # differences are allowed only for FP32 / FP64 near-ties at the k-th distance
+    assert bad == 0 and amb <= 2, (bad, amb)
+    badl = 0
+    for a, i in enumerate(pts):
+        s_gpu, s_or = set(gpu_ld[a].tolist()), set(ld_new[a].tolist())
+        if s_gpu != s_or:
+            diff = np.array(sorted(s_gpu ^ s_or))
+            kth = ((Y0[ld_new[a]] - Y0[i]) ** 2).sum(1).max()
+            dd = ((Y0[diff] - Y0[i]) ** 2).sum(1)
+            badl += int(not np.all(np.abs(dd - kth) <= band * kth))
+    assert badl == 0
+
+    # forces of the sampled points over the GPU's lists of t+1 at Y_t
+    mix = dict(st0)
+    mix.update(hd_idx=st1["hd_idx"], ld_idx=st1["ld_idx"], P=st1["P"], beta=st1["beta"])
+    o1 = oracle_from_state(X, mix, p, hd_mode=1)
+    A, R = o1.forces_points(pts, zhat=st0["Zhat"], t=st0["t"])
+    ea = rel_err_rows(att[pts].astype(np.float64), A)
+    er = rel_err_rows(rep[pts].astype(np.float64), R)
+    assert np.quantile(ea, 0.99) < 1e-4 and ea.max() < 1e-3, ea.max()
+    assert er.max() < 1e-4, er.max()
+    # the update of the sampled rows
+    V1 = 0.8 * st0["V"][pts].astype(np.float64) - lr * (att[pts].astype(np.float64) - rep[pts])
+    np.testing.assert_allclose(st1["V"][pts], V1, rtol=1e-4, atol=1e-6 * np.abs(V1).max())
+    np.testing.assert_allclose(st1["Y"][pts], Y0[pts] + st1["V"][pts], rtol=1e-5,
+                               atol=1e-6 * np.abs(Y0).max())

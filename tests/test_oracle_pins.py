@@ -460,3 +460,13 @@ def test_mlp_training_fits_a_smooth_map():
         losses.append(loss)
         O.adam(th, g, m, v, step, lr=3e-3)
     assert np.mean(losses[-20:]) < 0.2 * np.mean(losses[:5])
+
+
+def test_sampled_forces_equal_full_forces():
+    st = _state(N=250, D=8, d=3, kh=12, kl=8, nneg=40, perp=6.0)
+    st.Y[...] = np.random.default_rng(25).standard_normal(st.Y.shape)
+    A, R, _, _ = st.forces(zhat=123.0, t=7)
+    pts = np.array([0, 5, 17, 249, 100])
+    As, Rs = st.forces_points(pts, zhat=123.0, t=7)
+    np.testing.assert_allclose(As, A[pts], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(Rs, R[pts], rtol=1e-12, atol=1e-15)
