@@ -138,6 +138,8 @@ int funcsne_create(const float *X, int64_t N, int32_t D, int32_t d, int32_t k_hd
  *                    (Section 3); 1: every iteration; 2: never
  *   "precision"      FUNCSNE_FP32 / FUNCSNE_BF16 / FUNCSNE_FP8 HD storage
  *   "alpha"          tail parameter (may change between steps)
+ *   "concurrent"     1: the HD and LD refinements (which only read the state
+ *                    of the iteration) run side by side (default 0)
  *   "surrogate"      1: train the placement MLP inside funcsne_step, one
  *                    step before every "mlp_every"-th iteration (default 0)
  *   "mlp_every"      iterations between training steps (default 10)

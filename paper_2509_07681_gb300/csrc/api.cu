@@ -48,6 +48,10 @@ struct funcsne {
     int32_t max_blocks = 0;
     // execution
     cudaStream_t own_stream = nullptr;
+    cudaStream_t side_stream = nullptr;  // second branch of the captured iteration
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    bool concurrent = false;  // run the two refinements side by side in the graph
+    int32_t forces_cw = 8;    // floats of an LD row per lane in the forces kernel
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     int hd_blocks = 0, ld_blocks = 0, fo_blocks = 0, update_blocks = 0;
@@ -200,7 +204,7 @@ cudaError_t launch_phase(const funcsne* h, int phase, const StepParams& p, cudaS
                 default: return hd_refine_launch_fp8(p, h->RH, h->hd_blocks, h->hd_smem, s);
             }
         case 1: return ld_refine_launch(p, h->DP, h->RH, h->ld_blocks, h->ld_smem, s);
-        case 2: return forces_launch(p, h->DP, h->RH, h->fo_blocks, h->fo_smem, s);
+        case 2: return forces_launch(p, h->DP, h->RH, h->forces_cw, h->fo_blocks, h->fo_smem, s);
         default: return update_launch(update_params(h, nullptr, nullptr), h->update_blocks, s);
     }
 }
@@ -225,9 +229,11 @@ int configure_step(funcsne* h) {
         case FUNCSNE_BF16: occ = hd_refine_occupancy_bf16(h->RH, h->hd_smem); break;
         default: occ = hd_refine_occupancy_fp8(h->RH, h->hd_smem); break;
     }
-    h->hd_blocks = grid_for_occupancy(h, occ);
-    h->ld_blocks = grid_for_occupancy(h, ld_refine_occupancy(h->DP, h->RH, h->ld_smem));
-    h->fo_blocks = grid_for_occupancy(h, forces_occupancy(h->DP, h->RH, h->fo_smem));
+    // the two refinements share the SMs when they run side by side
+    const int ld_occ = ld_refine_occupancy(h->DP, h->RH, h->ld_smem);
+    h->hd_blocks = grid_for_occupancy(h, h->concurrent ? (occ + 1) / 2 : occ);
+    h->ld_blocks = grid_for_occupancy(h, h->concurrent ? (ld_occ + 1) / 2 : ld_occ);
+    h->fo_blocks = grid_for_occupancy(h, forces_occupancy(h->DP, h->RH, h->forces_cw, h->fo_smem));
     int64_t ub = (h->yelem / 4 + 255) / 256;
     if (ub > 4L * h->num_sms) ub = 4L * h->num_sms;
     if (ub < 1) ub = 1;
@@ -250,7 +256,18 @@ int build_graph(funcsne* h, int iters, cudaGraphExec_t* out) {
     for (int k = 0; k < iters; ++k) {
         const StepParams p = step_params(h);
         cudaError_t e = cudaSuccess;
-        for (int ph = 0; ph < kPhases && e == cudaSuccess; ++ph) e = launch_phase(h, ph, p, h->own_stream);
+        if (h->concurrent) {
+            // fork: HD refinement here, LD refinement on the side stream; join before the forces
+            e = cudaEventRecord(h->fork_ev, h->own_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side_stream, h->fork_ev, 0);
+            if (e == cudaSuccess) e = launch_phase(h, 0, p, h->own_stream);
+            if (e == cudaSuccess) e = launch_phase(h, 1, p, h->side_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(h->join_ev, h->side_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->own_stream, h->join_ev, 0);
+            for (int ph = 2; ph < kPhases && e == cudaSuccess; ++ph) e = launch_phase(h, ph, p, h->own_stream);
+        } else {
+            for (int ph = 0; ph < kPhases && e == cudaSuccess; ++ph) e = launch_phase(h, ph, p, h->own_stream);
+        }
         if (e != cudaSuccess) {
             cudaStreamEndCapture(h->own_stream, &g);
             if (g) cudaGraphDestroy(g);
@@ -308,6 +325,9 @@ void free_all(funcsne* h) {
                     static_cast<void*>(q.loss), static_cast<void*>(q.step)})
         cudaFree(p);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    if (h->side_stream) cudaStreamDestroy(h->side_stream);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
 }
 
 int quantize(funcsne* h) {
@@ -318,9 +338,10 @@ int quantize(funcsne* h) {
         return FUNCSNE_OK;
     }
     if (h->precision == FUNCSNE_BF16) {
-        h->qpitch = round_up(2 * h->D, 16);
-        h->nq = h->qpitch / 16;
-        h->qscale_off = 0;
+        // data chunks, then a 16-byte chunk holding the row-norm bound
+        h->nq = (2 * h->D + 15) / 16;
+        h->qscale_off = 16 * h->nq;
+        h->qpitch = h->qscale_off + 16;
     } else {
         const int nw = (h->D + 3) / 4;
         h->qpitch = round_up(4 * nw + 4, 16);
@@ -575,6 +596,9 @@ int funcsne_create(const float* X, int64_t N, int32_t D, int32_t d, int32_t k_hd
         }                                                                                           \
     } while (0)
     CREATE_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    CREATE_CUDA(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+    CREATE_CUDA(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+    CREATE_CUDA(cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
     h->stream = h->own_stream;
     const size_t nk_hd = static_cast<size_t>(N) * k_hd, nk_ld = static_cast<size_t>(N) * k_ld;
     CREATE_CUDA(dalloc(&h->X32, static_cast<size_t>(N) * h->xpitch));
@@ -686,6 +710,14 @@ int funcsne_set_option(funcsne_t* h, const char* key, double v) {
     } else if (k == "alpha") {
         if (!(v > 0)) return fail(h, FUNCSNE_E_ARG, "alpha must be > 0");
         h->alpha = static_cast<float>(v);
+    } else if (k == "forces_cw") {
+        if (v != 4 && v != 8 && v != 16) return fail(h, FUNCSNE_E_ARG, "forces_cw must be 4, 8 or 16");
+        h->forces_cw = static_cast<int32_t>(v);
+        configure_step(h);
+    } else if (k == "concurrent") {
+        if (v != 0 && v != 1) return fail(h, FUNCSNE_E_ARG, "concurrent must be 0 or 1");
+        h->concurrent = v != 0;
+        configure_step(h);
     } else if (k == "surrogate") {
         if (v != 0 && v != 1) return fail(h, FUNCSNE_E_ARG, "surrogate must be 0 or 1");
         h->surrogate = v != 0;
@@ -728,6 +760,8 @@ int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
     else if (k == "hd_mode") *v = h->hd_mode;
     else if (k == "alpha") *v = h->alpha;
     else if (k == "precision") *v = h->precision;
+    else if (k == "concurrent") *v = h->concurrent ? 1 : 0;
+    else if (k == "forces_cw") *v = h->forces_cw;
     else if (k == "surrogate") *v = h->surrogate ? 1 : 0;
     else if (k == "mlp_every") *v = h->mlp_every;
     else if (k == "mlp_lr") *v = h->mlp_lr;

@@ -353,27 +353,45 @@ __device__ __forceinline__ ApproxDist finish_band(float acc, float s1, float s2,
     return r;
 }
 
-// BF16 rows: 8 values per 16-byte chunk.
+// BF16 rows: 8 values per 16-byte chunk, nq data chunks, then a 16-byte
+// chunk whose first four bytes hold an upper bound N_c of the row's norm.
+// The candidate's rounding error e satisfies |e_f| <= u |x~_f|, so
+// ||e|| <= u N_c = E and |d~2 - d2| <= 2 ||x_i - x~_c|| E + E^2 (Cauchy-
+// Schwarz), plus the FP32 rounding of both distance evaluations.
 __device__ __forceinline__ ApproxDist dist_bf16(const float* __restrict__ xs,
-                                                const uint16_t* __restrict__ xc, int n8, float u,
+                                                const uint16_t* __restrict__ xc, int nq, float u,
                                                 float gamma) {
     const uint4* b = reinterpret_cast<const uint4*>(xc);
-    float acc = 0.f, s1 = 0.f, s2 = 0.f;
+    float acc = 0.f;
 #pragma unroll 2
-    for (int q = 0; q < n8; ++q) {
+    for (int q = 0; q < nq; ++q) {
         const uint4 raw = __ldg(b + q);
         const float4 x0 = reinterpret_cast<const float4*>(xs)[2 * q];
         const float4 x1 = reinterpret_cast<const float4*>(xs)[2 * q + 1];
-        approx_acc(x0.x, __uint_as_float(raw.x << 16), u, 0.f, acc, s1, s2);
-        approx_acc(x0.y, __uint_as_float(raw.x & 0xffff0000u), u, 0.f, acc, s1, s2);
-        approx_acc(x0.z, __uint_as_float(raw.y << 16), u, 0.f, acc, s1, s2);
-        approx_acc(x0.w, __uint_as_float(raw.y & 0xffff0000u), u, 0.f, acc, s1, s2);
-        approx_acc(x1.x, __uint_as_float(raw.z << 16), u, 0.f, acc, s1, s2);
-        approx_acc(x1.y, __uint_as_float(raw.z & 0xffff0000u), u, 0.f, acc, s1, s2);
-        approx_acc(x1.z, __uint_as_float(raw.w << 16), u, 0.f, acc, s1, s2);
-        approx_acc(x1.w, __uint_as_float(raw.w & 0xffff0000u), u, 0.f, acc, s1, s2);
+        float d = __fsub_rn(x0.x, __uint_as_float(raw.x << 16));
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(x0.y, __uint_as_float(raw.x & 0xffff0000u));
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(x0.z, __uint_as_float(raw.y << 16));
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(x0.w, __uint_as_float(raw.y & 0xffff0000u));
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(x1.x, __uint_as_float(raw.z << 16));
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(x1.y, __uint_as_float(raw.z & 0xffff0000u));
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(x1.z, __uint_as_float(raw.w << 16));
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(x1.w, __uint_as_float(raw.w & 0xffff0000u));
+        acc = __fmaf_rn(d, d, acc);
     }
-    return finish_band(acc, s1, s2, gamma);
+    const float norm = __ldg(reinterpret_cast<const float*>(b + nq));
+    const float E = u * norm;
+    const float b0 = 2.f * sqrtf(acc * (1.f + gamma)) * E + E * E;
+    ApproxDist r;
+    r.d2 = acc;
+    r.band = b0 * (1.f + 4.f * gamma) + gamma * (2.f * acc + 2.f * b0) + 1e-30f;
+    return r;
 }
 
 // FP8-E4M3 rows with a per-row FP32 scale stored after the codes:

@@ -221,17 +221,25 @@ __global__ void zinit_finish_kernel(const double* part, int n, DevScalars* sc) {
     sc->last_Z = s;
 }
 
-// BF16 copy: round to nearest even, zero padding.
+// BF16 copy, one warp per row: round to nearest even, zero padding up to
+// `norm_off`, then an upper bound of the rounded row's norm (FP64 sum,
+// rounded up to FP32) at byte `norm_off`.
 __global__ void quantize_bf16_kernel(const float* __restrict__ X, int64_t N, int D, int xpitch,
-                                     int qpitch, uint8_t* Q) {
-    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int per_row = qpitch / 2;
-    if (e >= N * per_row) return;
-    const int64_t i = e / per_row;
-    const int f = static_cast<int>(e % per_row);
-    const float v = f < D ? X[i * xpitch + f] : 0.f;
-    const __nv_bfloat16 b = __float2bfloat16_rn(v);
-    reinterpret_cast<__nv_bfloat16*>(Q + i * qpitch)[f] = b;
+                                     int qpitch, int norm_off, uint8_t* Q) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= N) return;
+    __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Q + i * qpitch);
+    double s = 0.0;
+    for (int f = lane; f < norm_off / 2; f += 32) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(f < D ? X[i * xpitch + f] : 0.f);
+        row[f] = b;
+        const double v = __bfloat162float(b);
+        s += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if (lane == 0) *reinterpret_cast<float*>(Q + i * qpitch + norm_off) = __double2float_ru(sqrt(s));
 }
 
 // FP8-E4M3 copy with per-row scale s = max|x| / 448 (s = 1 for a zero row),
@@ -342,7 +350,7 @@ cudaError_t launch_zinit(const ZinitParams& z, int DP, int blocks, DevScalars* s
 cudaError_t launch_quantize(const float* X32, int64_t N, int D, int xpitch, int precision, int qpitch,
                             int scale_off, uint8_t* Q, cudaStream_t s) {
     if (precision == 1)
-        quantize_bf16_kernel<<<grid_for(N * (qpitch / 2), 256), 256, 0, s>>>(X32, N, D, xpitch, qpitch, Q);
+        quantize_bf16_kernel<<<grid_for(N * 32, 256), 256, 0, s>>>(X32, N, D, xpitch, qpitch, scale_off, Q);
     else
         quantize_fp8_kernel<<<grid_for(N * 32, 256), 256, 0, s>>>(X32, N, D, xpitch, qpitch, scale_off, Q);
     return cudaGetLastError();

@@ -72,9 +72,9 @@ int hd_refine_occupancy_f32(int RH, size_t smem);
 int hd_refine_occupancy_bf16(int RH, size_t smem);
 int hd_refine_occupancy_fp8(int RH, size_t smem);
 cudaError_t ld_refine_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
-cudaError_t forces_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
+cudaError_t forces_launch(const StepParams& p, int DP, int RH, int CW, int blocks, size_t smem, cudaStream_t s);
 int ld_refine_occupancy(int DP, int RH, size_t smem);
-int forces_occupancy(int DP, int RH, size_t smem);
+int forces_occupancy(int DP, int RH, int CW, size_t smem);
 cudaError_t update_launch(const UpdateParams& u, int blocks, cudaStream_t s);
 
 // set-up

@@ -68,7 +68,7 @@ struct StepParams {
     int32_t xpitch;      // floats per FP32 row
     int32_t nq;          // BF16: 16-byte chunks per row; FP8: 4-byte code words per row
     int32_t qpitch;      // bytes per quantised row
-    int32_t qscale_off;  // byte offset of the FP8 row scale
+    int32_t qscale_off;  // byte offset of the FP8 row scale / the BF16 row-norm bound
     int32_t hd_mode;
     int32_t smem_per_warp;  // bytes
     int32_t xs_floats;      // own-row floats staged per warp

@@ -52,8 +52,14 @@ __device__ __forceinline__ ListView list_view(const StepParams& p, int hc, int l
 }
 
 // ------------------------------------------------------------------ HD refinement
+// Resident blocks per SM the registers are sized for: the kernel waits
+// mostly on memory; the reduced-precision variants fit five blocks (40
+// warps) without spilling, the FP32 one four.
+template <int XM>
+constexpr int hd_refine_min_blocks() { return XM == 0 ? 4 : 5; }
+
 template <int RH, int XM>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, hd_refine_min_blocks<XM>())
 hd_refine_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -196,25 +202,40 @@ hd_refine_kernel(const StepParams p) {
 // 2 when DP = 2): one 16-byte load per lane, R = 32/G rows per warp
 // instruction. Lane l owns components [CW (l mod G), CW (l mod G) + CW) of
 // every row its group touches.
-template <int DP>
+template <int DP, int CWP = 4>
 struct RowSplit {
-    static constexpr int CW = DP >= 4 ? 4 : DP;  // floats per lane
-    static constexpr int G = DP / CW;            // lanes per row
-    static constexpr int R = 32 / G;             // rows per pass
+    static constexpr int CW = DP >= CWP ? CWP : DP;  // floats per lane
+    static constexpr int G = DP / CW;                 // lanes per row
+    static constexpr int R = 32 / G;                  // rows per pass
 };
 
 template <int CW>
 __device__ __forceinline__ void load_chunk(const float* __restrict__ src, float (&v)[CW]) {
-    if constexpr (CW == 4) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(src));
-        v[0] = a.x;
-        v[1] = a.y;
-        v[2] = a.z;
-        v[3] = a.w;
+    if constexpr (CW % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < CW / 4; ++q) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(src) + q);
+            v[4 * q] = a.x;
+            v[4 * q + 1] = a.y;
+            v[4 * q + 2] = a.z;
+            v[4 * q + 3] = a.w;
+        }
     } else {
         const float2 a = __ldg(reinterpret_cast<const float2*>(src));
         v[0] = a.x;
         v[1] = a.y;
+    }
+}
+
+template <int CW>
+__device__ __forceinline__ void atomic_add_chunk(float* dst, const float (&v)[CW], float scale) {
+    if constexpr (CW % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < CW / 4; ++q)
+            atomicAdd(reinterpret_cast<float4*>(dst) + q,
+                      make_float4(scale * v[4 * q], scale * v[4 * q + 1], scale * v[4 * q + 2], scale * v[4 * q + 3]));
+    } else {
+        atomicAdd(reinterpret_cast<float2*>(dst), make_float2(scale * v[0], scale * v[1]));
     }
 }
 
@@ -299,10 +320,10 @@ ld_refine_kernel(const StepParams p) {
 template <int DP>
 constexpr int forces_min_blocks() { return 4; }
 
-template <int DP, int RH>
+template <int DP, int RH, int CWP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, forces_min_blocks<DP>())
 forces_kernel(const StepParams p) {
-    using S = RowSplit<DP>;
+    using S = RowSplit<DP, CWP>;
     constexpr int CW = S::CW, G = S::G, R = S::R;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -397,14 +418,7 @@ forces_kernel(const StepParams p) {
                 rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
             }
             if (lane % G == 0) z += w;
-            if (on) {
-                if constexpr (CW == 4)
-                    atomicAdd(reinterpret_cast<float4*>(p.A + static_cast<int64_t>(j) * DP + co),
-                              make_float4(-fa * dy[0], -fa * dy[1], -fa * dy[2], -fa * dy[3]));
-                else
-                    atomicAdd(reinterpret_cast<float2*>(p.A + static_cast<int64_t>(j) * DP + co),
-                              make_float2(-fa * dy[0], -fa * dy[1]));
-            }
+            if (on) atomic_add_chunk<CW>(p.A + static_cast<int64_t>(j) * DP + co, dy, -fa);
         }
         // LD neighbours outside the HD list: repulsion
         for (int b = 0; b < k_ld; b += R) {
@@ -441,11 +455,13 @@ forces_kernel(const StepParams p) {
                 rep[c] += __shfl_xor_sync(kFull, rep[c], m);
             }
         if (lane < G) {
-            if constexpr (CW == 4) {
-                atomicAdd(reinterpret_cast<float4*>(p.A + gi * DP + co), make_float4(att[0], att[1], att[2], att[3]));
-                *reinterpret_cast<float4*>(p.R + gi * DP + co) = make_float4(rep[0], rep[1], rep[2], rep[3]);
+            atomic_add_chunk<CW>(p.A + gi * DP + co, att, 1.f);
+            if constexpr (CW % 4 == 0) {
+#pragma unroll
+                for (int q = 0; q < CW / 4; ++q)
+                    reinterpret_cast<float4*>(p.R + gi * DP + co)[q] =
+                        make_float4(rep[4 * q], rep[4 * q + 1], rep[4 * q + 2], rep[4 * q + 3]);
             } else {
-                atomicAdd(reinterpret_cast<float2*>(p.A + gi * DP + co), make_float2(att[0], att[1]));
                 *reinterpret_cast<float2*>(p.R + gi * DP + co) = make_float2(rep[0], rep[1]);
             }
         }

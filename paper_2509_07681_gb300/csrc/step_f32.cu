@@ -24,15 +24,20 @@ cudaError_t ld_refine_launch(const StepParams& p, int DP, int RH, int blocks, si
     return cudaErrorInvalidValue;
 }
 
-cudaError_t forces_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s) {
-#define FSNE_CASE(dp, rh)                                                                       \
-    if (DP == dp && RH == rh) {                                                                 \
-        FSNE_SET_SMEM((forces_kernel<dp, rh>), smem);                                           \
-        forces_kernel<dp, rh><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);                     \
+// Lanes per LD row in the forces kernel: cw floats per lane (4, 8 or 16).
+#define FSNE_FORCES_CW(X, dp, rh) X(dp, rh, 4) X(dp, rh, 8) X(dp, rh, 16)
+
+cudaError_t forces_launch(const StepParams& p, int DP, int RH, int CW, int blocks, size_t smem, cudaStream_t s) {
+#define FSNE_CASE3(dp, rh, cw)                                                                  \
+    if (DP == dp && RH == rh && (CW == cw || (cw == 4 && dp < CW))) {                           \
+        FSNE_SET_SMEM((forces_kernel<dp, rh, cw>), smem);                                       \
+        forces_kernel<dp, rh, cw><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);                 \
         return cudaGetLastError();                                                              \
     }
+#define FSNE_CASE(dp, rh) FSNE_FORCES_CW(FSNE_CASE3, dp, rh)
     FSNE_DP_RH(FSNE_CASE)
 #undef FSNE_CASE
+#undef FSNE_CASE3
     return cudaErrorInvalidValue;
 }
 
@@ -48,15 +53,18 @@ int ld_refine_occupancy(int DP, int RH, size_t smem) {
     return n;
 }
 
-int forces_occupancy(int DP, int RH, size_t smem) {
+int forces_occupancy(int DP, int RH, int CW, size_t smem) {
     int n = 0;
-#define FSNE_CASE(dp, rh)                                                                       \
-    if (DP == dp && RH == rh) {                                                                 \
-        FSNE_SET_SMEM((forces_kernel<dp, rh>), smem);                                           \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, forces_kernel<dp, rh>, kWarpsPerBlock * 32, smem); \
+#define FSNE_CASE3(dp, rh, cw)                                                                  \
+    if (DP == dp && RH == rh && (CW == cw || (cw == 4 && dp < CW))) {                           \
+        FSNE_SET_SMEM((forces_kernel<dp, rh, cw>), smem);                                       \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, forces_kernel<dp, rh, cw>, kWarpsPerBlock * 32, smem); \
+        return n;                                                                               \
     }
+#define FSNE_CASE(dp, rh) FSNE_FORCES_CW(FSNE_CASE3, dp, rh)
     FSNE_DP_RH(FSNE_CASE)
 #undef FSNE_CASE
+#undef FSNE_CASE3
     return n;
 }
 
