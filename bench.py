@@ -1,15 +1,22 @@
 #!/usr/bin/env python
-"""Benchmark of the fused FUnc-SNE iteration on GB300.
+"""Benchmark of the FUnc-SNE iteration on GB300.
 
-Workload: the 1M-point spectrum workload (N=1,000,000, D=50 FP32, feature
-variance ~1/j over 50 anisotropic Zipf-sized clusters; d=16, k_hd=32,
-k_ld=32, n_neg=32, alpha=1, perplexity 30; synthetic, seed 0). One step =
-one full iteration: HD refinement (forced every iteration), bandwidth
-bisection for flagged points, LD refinement, attraction / repulsion /
+Default workload: the 1M-point spectrum workload (N=1,000,000, D=50 FP32,
+feature variance ~1/j over 50 anisotropic Zipf-sized clusters; d=16,
+k_hd=32, k_ld=32, n_neg=32, alpha=1, perplexity 30; synthetic, seed 0). One
+step = one full iteration: HD refinement (forced every iteration), bandwidth
+calibration of flagged points, LD refinement, attraction / repulsion /
 normalisation, momentum update. Metric: iterations/s, BF16 HD storage vs
 FP32 at equal KNN recall (the FP32 re-rank makes the neighbour sets equal).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--alpha A] [--mode bench|dynamic|ncu]
+
+--workload picks another synthetic workload (blobs-2k, pixels-70k,
+swissroll-200k, lowrank-2m) for the same measurement. --mode dynamic runs the
+dynamic-dataset protocol (base 200,000 swiss-roll points, 10,000 inserted
+every 50 iterations for 20 rounds) and reports insertion-to-converged time for
+neighbour-mean and surrogate (MLP) placement.
 
 With N > 1 (torchrun) every rank runs an independent replica of the
 workload ("replicas only": the iteration has no cross-GPU step here).
@@ -32,11 +39,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "iters/s at N=1M (KNN refine+gradient), BF16 vs FP32 at equal KNN recall"
+METRIC_OTHER = "iters/s (KNN refine+gradient)"
 UNIT = "iter/s"
 WORKLOAD = "spectrum-1m"
 BURN_IN = 200          # untimed iterations after set-up, so lists are near steady state
 RECALL_QUERIES = 1000  # sampled queries for HD-KNN recall against brute force
 FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 129 * 2 ** 20
+# storage precision each workload is quoted on
+HEADLINE = {"blobs-2k": "fp32", "lowrank-2m": "fp8"}
+# points in the CPU oracle's sample: about 10-30 s of oracle work per workload
+CPU_SAMPLE = {"blobs-2k": 2000, "pixels-70k": 6000, "spectrum-1m": 100000, "swissroll-200k": 40000,
+              "lowrank-2m": 12000}
 
 
 def _env_int(name, default):
@@ -46,9 +60,25 @@ def _env_int(name, default):
         return default
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The maximum of a per-rank scalar over all ranks (every rank gets it);
+    the identity without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Units all ranks processed per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def algorithmic_bytes_per_point(D, d, k_hd, k_ld, n_neg, row_bytes, rerank_rows=0.0):
     """Minimum bytes one point moves in each kernel of one iteration (HD
-    refinement forced), before sector rounding. the design doc derives them."""
+    refinement forced), before sector rounding."""
     y = 4 * d
     hd = ((1 + 32) * row_bytes + rerank_rows * 4 * D   # own row, candidate rows, exact re-ranks
           + 8 * k_hd + 4 * k_ld                        # HD list (index, d2) and LD list of t
@@ -62,6 +92,11 @@ def algorithmic_bytes_per_point(D, d, k_hd, k_ld, n_neg, row_bytes, rerank_rows=
               + k_hd * y + 2 * y)                      # reverse attraction (scatter), A_i and R_i
     update = 7 * y                                     # Y, V, A read+write, R read
     return {"hd_refine": hd, "ld_refine": ld, "forces": forces, "update": update}
+
+
+def row_bytes_of(D):
+    """Bytes of one HD row per storage precision (payload + its scale or norm)."""
+    return {"fp32": 4 * D, "bf16": 2 * D + 4, "fp8": D + 4}
 
 
 def kernel_source_hash():
@@ -83,10 +118,10 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def committed_traffic(kernel_hash, precision, kernel):
+def committed_traffic(kernel_hash, precision, kernel, workload=WORKLOAD):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, valid
     only for the kernel sources it was captured from."""
-    path = os.path.join(ROOT, "profiles", "kernels_spectrum-1m.json")
+    path = os.path.join(ROOT, "profiles", f"kernels_{workload}.json")
     try:
         with open(path) as f:
             js = json.load(f)
@@ -145,10 +180,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def run_ours(args, rank, world):
+def workload_params(args):
+    from paper_2509_07681_gb300 import synth
+    X, p = synth.make(args.workload, n=args.n)
+    if args.alpha is not None:
+        p = dict(p, alpha=args.alpha)
+    return X, p
+
+
+def _setup_gpu(world):
     import torch
     from paper_2509_07681_gb300 import funcsne as F
-    from paper_2509_07681_gb300 import synth
     from paper_2509_07681_gb300.build import build
 
     local = _env_int("LOCAL_RANK", 0)
@@ -159,10 +201,19 @@ def run_ours(args, rank, world):
         dist.init_process_group("nccl")
     build()
     F.load()
-    X, p = synth.make(WORKLOAD, n=args.n)
+    return local, dist
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2509_07681_gb300 import funcsne as F
+
+    local, dist = _setup_gpu(world)
+    X, p = workload_params(args)
     N, D = X.shape
     K, W = args.steps, args.warmup
     stream = torch.cuda.Stream()
+    headline = HEADLINE.get(args.workload, "bf16")
 
     def barrier():
         torch.cuda.synchronize()
@@ -172,7 +223,7 @@ def run_ours(args, rank, world):
     m = F.FuncSNE(X, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0)
     m.set_stream(stream)
     m.set_option("hd_mode", 1)
-    m.step(BURN_IN)
+    m.step(args.burn_in if args.burn_in else BURN_IN)
     m.sync()
     base = m.export_state()
 
@@ -196,13 +247,9 @@ def run_ours(args, rank, world):
         m.step(K)
         e1.record(stream)
         barrier()
-        total_ms = e0.elapsed_time(e1)
+        total_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         s1 = m.stats()
         m.sync()
-        if dist is not None:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
         # per-kernel device times: the same iterations again with events
         # between the kernels (sequential launches), from the same state
         m.import_state(st_w)
@@ -233,49 +280,53 @@ def run_ours(args, rank, world):
     barrier()
     t0 = time.perf_counter()
     m2 = F.FuncSNE(Xp, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0,
-                   hd_mode=1, precision=F.BF16)
+                   hd_mode=1, precision={"fp32": F.FP32, "bf16": F.BF16, "fp8": F.FP8}[headline])
     for _ in range(K):
         m2.step(1)
         m2.embedding(out=Yp)
     m2.sync()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     m2.close()
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return None
-    head = results["bf16"]
-    value = world * K / (head["total_ms"] / 1e3)
+    head = results[headline]
+    value = whole_job_rate(world, K, head["total_ms"] / 1e3)
     peak, peak_kind = measured_peaks()
     khash = kernel_source_hash()
-    row_bytes = {"fp32": 4 * D, "bf16": 2 * D + 4, "fp8": D + 4}
+    rbytes = row_bytes_of(D)
     for name in results:
         r = results[name]
-        per = algorithmic_bytes_per_point(D, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], row_bytes[name],
+        per = algorithmic_bytes_per_point(D, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], rbytes[name],
                                           r["rerank_rows"])
         r["alg_bytes"] = {k: N * v for k, v in per.items()}
         r["achieved_gbs"] = {k: r["alg_bytes"][k] / (r["kernel_ms"][k] / 1e3) / 1e9 for k in per}
     top = max(head["kernel_ms"], key=head["kernel_ms"].get)
-    traffic = committed_traffic(khash, "bf16", top)
+    traffic = committed_traffic(khash, headline, top, args.workload)
     roofline = {"bound": "hbm", "achieved": round(head["achieved_gbs"][top], 1), "peak": peak, "unit": "GB/s",
                 "frac": round(head["achieved_gbs"][top] / peak, 4), "traffic": traffic,
-                "kernel": f"{top} (BF16 rows)", "peak_source": peak_kind,
+                "kernel": f"{top} ({headline} rows)", "peak_source": peak_kind,
                 "alg_bytes_per_launch": int(head["alg_bytes"][top]),
                 "step_frac": round(sum(head["alg_bytes"].values()) / (head["total_ms"] / K / 1e3) / 1e9 / peak, 4)}
-    cpu = cpu_baseline(args, X, p, sample_n=100000, steps=2) if world == 1 else None
+    cpu = None
+    if world == 1:
+        cpu = cpu_baseline(args, X, p, sample_n=min(N, CPU_SAMPLE.get(args.workload, 20000)), steps=2)
+    xq = {"fp32": 4 * D, "bf16": 2 * D + 16, "fp8": D + 4}[headline]
+    ws = N * (4 * D + xq + 8 * p["k_hd"] * 2 + 4 * p["k_ld"] * 2 + 4 * p["k_hd"] + 16 * p["d"])
+    l2 = ("working set > L2 (%.0f MB vs 129 MB), no flush" % (ws / 1e6) if ws > L2_BYTES else
+          "working set fits in L2 (%.1f MB): L2-resident by design, no flush" % (ws / 1e6))
     line = {
-        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "metric": METRIC if args.workload == WORKLOAD else METRIC_OTHER, "value": round(value, 2), "unit": UNIT,
+        "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(head["total_ms"] / K, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "D": D, "d": p["d"], "k_hd": p["k_hd"], "k_ld": p["k_ld"],
+        "config": {"workload": args.workload, "N": N, "D": D, "d": p["d"], "k_hd": p["k_hd"], "k_ld": p["k_ld"],
                    "n_neg": p["n_neg"], "alpha": p["alpha"], "perplexity": p["perplexity"],
-                   "hd_refine": "every iteration", "storage": "bf16 rows + fp32 boundary re-rank",
-                   "burn_in": BURN_IN, "l2": "working set > L2 (X 208 MB + lists 768 MB)",
+                   "hd_refine": "every iteration",
+                   "storage": f"{headline} rows" + ("" if headline == "fp32" else " + fp32 boundary re-rank"),
+                   "burn_in": args.burn_in if args.burn_in else BURN_IN, "l2": l2,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "precisions": {n: {"iters_per_s": round(K / (r["total_ms"] / 1e3), 2),
                            "kernel_ms": {k: round(v, 4) for k, v in r["kernel_ms"].items()},
@@ -286,10 +337,11 @@ def run_ours(args, rank, world):
                        for n, r in results.items()},
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": round(world * K / e2e_s, 3), "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes / K),
-                "d2h_bytes_per_step": int(N * p["d"] * 4),
-                "note": "create from pinned host X (H2D, init) + K x (step + embedding read-back), BF16"},
-        "gpu_launches": 4 * K * len(results),
+        "e2e": {"value": round(whole_job_rate(world, K, e2e_s), 3), "unit": UNIT,
+                "h2d_bytes_per_step": int(X.nbytes / K), "d2h_bytes_per_step": int(N * p["d"] * 4),
+                "note": f"create from pinned host X (H2D, init) + K x (step + embedding read-back), {headline}"},
+        # kernels of the headline precision's timed region: 4 per iteration
+        "gpu_launches": 4 * K,
         "clocks": clk,
         "kernel_hash": khash,
     }
@@ -299,15 +351,127 @@ def run_ours(args, rank, world):
     return line
 
 
+def run_dynamic(args, rank, world):
+    """Dynamic dataset: a 200,000-point swiss-roll base, then `rounds` times
+    insert `insert_n` points of a fresh draw of the same generator and run
+    `every` iterations. After each insertion the LD lists of the new points
+    are checked every `check` iterations against their exact HD neighbours
+    (recall@k_ld); a round has converged once the new points' recall is
+    within 0.5 points of that of 2,000 established points. Reported per
+    placement (neighbour mean, surrogate MLP): insertion-to-converged
+    iterations and milliseconds (insertion + iterations, surrogate training
+    included), recall right after insertion and at the round's end."""
+    import torch
+    from paper_2509_07681_gb300 import funcsne as F
+    from paper_2509_07681_gb300 import synth
+    from paper_2509_07681_gb300.quality import recall
+
+    local, dist = _setup_gpu(world)
+    name = "swissroll-200k"
+    base_n = args.n or 200_000
+    X0, p = synth.make(name, n=base_n)
+    D = X0.shape[1]
+    n_new, rounds, every, check = args.insert_n, args.rounds, 50, 5
+    batches = [synth.swissroll(n=n_new, dim=D, n_clusters=32, seed=0, batch=r + 1) for r in range(rounds)]
+    rng = np.random.default_rng(1)
+    q_old = np.sort(rng.choice(base_n, 2000, replace=False)).astype(np.int32)
+    k = p["k_ld"]
+    stream = torch.cuda.Stream()
+    arms = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for arm, place in (("mean", F.PLACE_MEAN), ("surrogate", F.PLACE_SURROGATE)):
+        m = F.FuncSNE(X0, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0,
+                      precision=F.BF16)
+        m.set_stream(stream)
+        if arm == "surrogate":
+            m.set_option("surrogate", 1)
+        m.step(args.burn_in if args.burn_in else 300)
+        m.sync()
+        t_pre = 0.0
+        if arm == "surrogate" and args.mlp_pretrain:
+            t0 = time.perf_counter()
+            m.mlp_train(args.mlp_pretrain)
+            m.sync()
+            t_pre = time.perf_counter() - t0
+        per_round = []
+        step_s = 0.0
+        n_steps = 0
+        for r in range(rounds):
+            t0 = time.perf_counter()
+            first = m.insert(batches[r], placement=place)
+            m.sync()
+            t_ins = time.perf_counter() - t0
+            q_new = np.arange(first, first + n_new, dtype=np.int32)
+            ex_new, _ = m.exact_knn(q_new, k)
+            ex_old, _ = m.exact_knn(q_old, k)
+            Y_ins = m.embedding()[first:].astype(np.float64)
+            ld = m.knn(F.SPACE_LD, with_d2=False)
+            rec0 = recall(ld[q_new], ex_new)
+            it, t_steps, conv_it, conv_ms = 0, 0.0, None, None
+            while it < every:
+                t0 = time.perf_counter()
+                m.step(check)
+                m.sync()
+                t_steps += time.perf_counter() - t0
+                it += check
+                ld = m.knn(F.SPACE_LD, with_d2=False)
+                rn, ro = recall(ld[q_new], ex_new), recall(ld[q_old], ex_old)
+                if conv_it is None and rn >= ro - 0.005:
+                    conv_it, conv_ms = it, (t_ins + t_steps) * 1e3
+            Y = m.embedding().astype(np.float64)
+            scale = np.sqrt(np.mean(Y[:first] ** 2))
+            move = float(np.sqrt(np.mean(np.sum((Y[first:] - Y_ins) ** 2, 1))) / scale)
+            step_s += t_steps
+            n_steps += every
+            per_round.append(dict(insert_ms=round(t_ins * 1e3, 3), recall_new_at_insert=round(rec0, 4),
+                                  converged_iters=conv_it, converged_ms=None if conv_ms is None else round(conv_ms, 3),
+                                  recall_new_end=round(rn, 4), recall_old_end=round(ro, 4),
+                                  movement=round(move, 4)))
+        st = m.stats()
+        m.close()
+        conv = [x["converged_iters"] for x in per_round if x["converged_iters"] is not None]
+        conv_ms = [x["converged_ms"] for x in per_round if x["converged_ms"] is not None]
+        arms[arm] = {
+            "rounds_converged": len(conv), "rounds": rounds,
+            "median_converged_iters": statistics.median(conv) if conv else None,
+            "median_converged_ms": round(statistics.median(conv_ms), 3) if conv_ms else None,
+            "median_insert_ms": round(statistics.median(x["insert_ms"] for x in per_round), 3),
+            "mean_recall_new_at_insert": round(float(np.mean([x["recall_new_at_insert"] for x in per_round])), 4),
+            "mean_recall_new_end": round(float(np.mean([x["recall_new_end"] for x in per_round])), 4),
+            "mean_recall_old_end": round(float(np.mean([x["recall_old_end"] for x in per_round])), 4),
+            "mean_movement": round(float(np.mean([x["movement"] for x in per_round])), 4),
+            "ms_per_iter": round(step_s * 1e3 / n_steps, 4), "mlp_pretrain_ms": round(t_pre * 1e3, 1),
+            "mlp_steps": st["mlp_steps"], "final_N": base_n + rounds * n_new, "per_round": per_round}
+    clk = clocks.stop()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+    line = {"metric": "insertion-to-converged ms (dynamic dataset, recall within 0.5 points)",
+            "value": arms["surrogate"]["median_converged_ms"], "unit": "ms", "higher_is_better": False,
+            "n_gpus": world, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": f"{name} dynamic", "base_N": base_n, "D": D, "d": p["d"], "k_hd": p["k_hd"],
+                       "k_ld": k, "n_neg": p["n_neg"], "insert": n_new, "rounds": rounds, "every": every,
+                       "check_every": check, "storage": "bf16 rows + fp32 boundary re-rank",
+                       "hd_refine": "adaptive coin", "mlp": f"{D}-256-256-{p['d']}, batch 4096, every 10 iters",
+                       "mlp_pretrain_steps": args.mlp_pretrain},
+            "arms": arms, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
 def cpu_baseline(args, X, p, sample_n=None, steps=1):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of the
-    workload (the same generator at N=sample_n), one timed iteration after its
-    own initialisation, scaled linearly to N=1M (the iteration is O(N))."""
+    workload (the same generator at N=sample_n), timed iterations after its
+    own initialisation, scaled linearly to the full N (the iteration is O(N))."""
     import oracle as O
     from paper_2509_07681_gb300 import synth
 
     n = sample_n or args.cpu_sample
-    Xs, _ = synth.make(WORKLOAD, n=n)
+    Xs, _ = synth.make(args.workload, n=n)
     o = O.OracleState(Xs, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0,
                       hd_mode=1)
     t0 = time.perf_counter()
@@ -316,8 +480,8 @@ def cpu_baseline(args, X, p, sample_n=None, steps=1):
     dt = (time.perf_counter() - t0) / steps
     scale = X.shape[0] / n
     return {"value": round(1.0 / (dt * scale), 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{WORKLOAD} generator at N={n} (same D, d, k, n_neg), {steps} oracle iteration(s) "
-                      f"after its own init, {dt:.2f} s/iter scaled x{scale:.0f} to N={X.shape[0]}"}
+            "sample": f"{args.workload} generator at N={n} (same D, d, k, n_neg), {steps} oracle iteration(s) "
+                      f"after its own init, {dt:.2f} s/iter scaled x{scale:.1f} to N={X.shape[0]}"}
 
 
 def run_reference(args, rank, world):
@@ -329,9 +493,12 @@ def run_reference(args, rank, world):
     from paper_2509_07681_gb300 import synth
 
     build_oracle()
-    Xfull_n = 1_000_000 if args.n is None else args.n
-    n = args.cpu_sample
-    Xs, p = synth.make(WORKLOAD, n=n)
+    _, kw, _ = synth.WORKLOADS[args.workload]
+    Xfull_n = kw["n"] if args.n is None else args.n
+    n = min(args.cpu_sample, Xfull_n)
+    Xs, p = synth.make(args.workload, n=n)
+    if args.alpha is not None:
+        p = dict(p, alpha=args.alpha)
     o = O.OracleState(Xs, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0, hd_mode=1)
     for _ in range(args.warmup):
         o.step()
@@ -341,12 +508,14 @@ def run_reference(args, rank, world):
     dt = (time.perf_counter() - t0) / args.steps
     scale = Xfull_n / n
     value = 1.0 / (dt * scale)
-    sample = (f"{WORKLOAD} generator at N={n}, {args.steps} timed oracle iterations after {args.warmup} "
-              f"warm-up, {dt:.3f} s/iter scaled x{scale:.0f} to N={Xfull_n}")
-    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+    sample = (f"{args.workload} generator at N={n}, {args.steps} timed oracle iterations after {args.warmup} "
+              f"warm-up, {dt:.3f} s/iter scaled x{scale:.1f} to N={Xfull_n}")
+    line = {"impl": "reference", "metric": METRIC if args.workload == WORKLOAD else METRIC_OTHER,
+            "value": round(value, 6), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * scale * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "N": Xfull_n, "hd_refine": "every iteration"},
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": Xfull_n, "hd_refine": "every iteration"},
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -356,14 +525,14 @@ def run_reference(args, rank, world):
 
 def run_profile_case(args):
     """A short, fixed sequence of launches for ncu: create the workload at N
-    (default 1M), then for each precision `warmup` + `steps` iterations with
-    HD refinement every iteration. Prints one line per precision."""
+    (default: the workload's own N), then for each precision `warmup` +
+    `steps` iterations with HD refinement every iteration. Prints one line
+    per precision."""
     from paper_2509_07681_gb300 import funcsne as F
-    from paper_2509_07681_gb300 import synth
     from paper_2509_07681_gb300.build import build
 
     build()
-    X, p = synth.make(WORKLOAD, n=args.n)
+    X, p = workload_params(args)
     m = F.FuncSNE(X, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0)
     m.set_option("hd_mode", 1)
     if args.burn_in:
@@ -379,19 +548,30 @@ def run_profile_case(args):
     m.close()
 
 
-def main():
+def parse_args(argv=None):
+    from paper_2509_07681_gb300.synth import WORKLOADS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=None, help="override N (default: the workload's 1,000,000)")
-    ap.add_argument("--cpu-sample", type=int, default=20000, help="points in the CPU oracle sample")
-    ap.add_argument("--mode", choices=["bench", "ncu"], default="bench",
-                    help="ncu: the short fixed launch sequence used for profiling")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
+    ap.add_argument("--alpha", type=float, default=None, help="override the workload's alpha")
+    ap.add_argument("--n", type=int, default=None, help="override N (default: the workload's own)")
+    ap.add_argument("--cpu-sample", type=int, default=20000, help="points in the reference arm's oracle sample")
+    ap.add_argument("--mode", choices=["bench", "dynamic", "ncu"], default="bench",
+                    help="dynamic: insertion protocol; ncu: the short fixed launch sequence used for profiling")
     ap.add_argument("--precisions", default="fp32,bf16,fp8", help="precisions of --mode ncu")
-    ap.add_argument("--burn-in", type=int, default=0, help="--mode ncu: untimed iterations first")
-    args = ap.parse_args()
+    ap.add_argument("--burn-in", type=int, default=0, help="untimed iterations first (0: the mode's default)")
+    ap.add_argument("--insert-n", type=int, default=10000, help="--mode dynamic: points per insertion")
+    ap.add_argument("--rounds", type=int, default=20, help="--mode dynamic: insertion rounds")
+    ap.add_argument("--mlp-pretrain", type=int, default=0,
+                    help="--mode dynamic: extra MLP steps before the first insertion (timed, reported)")
+    return ap.parse_args(argv)
+
+
+def main():
+    args = parse_args()
     if args.mode == "ncu":
         run_profile_case(args)
         return
@@ -401,6 +581,8 @@ def main():
     world = _env_int("WORLD_SIZE", 1)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.mode == "dynamic":
+        run_dynamic(args, rank, world)
     else:
         run_ours(args, rank, world)
 

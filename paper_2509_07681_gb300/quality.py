@@ -1,4 +1,4 @@
-"""Neighbourhood-quality measures used to judge whole runs (host-side numpy).
+"""Neighbourhood-quality measures used to assess whole runs (host-side numpy).
 
 * ``recall``: mean fraction of the exact k nearest neighbours found.
 * ``rnx_curve`` / ``rnx_auc``: R_NX(K) and its area under the log-K curve
