@@ -140,6 +140,12 @@ int funcsne_create(const float *X, int64_t N, int32_t D, int32_t d, int32_t k_hd
  *   "alpha"          tail parameter (may change between steps)
  *   "concurrent"     1: the HD and LD refinements (which only read the state
  *                    of the iteration) run side by side (default 0)
+ *   "forces_cw"      floats of an LD row each lane reads in the forces
+ *                    kernel: 4, 8 (default) or 16 (a tuning knob)
+ *   "hd_lanes"       lanes that read one gathered HD row in the refinement:
+ *                    1, 2, 4 or 8, or 0 (default) to choose from the row
+ *                    bytes. A tuning knob; it fixes the FP32 summation order,
+ *                    so results depend on it (bit for bit)
  *   "surrogate"      1: train the placement MLP inside funcsne_step, one
  *                    step before every "mlp_every"-th iteration (default 0)
  *   "mlp_every"      iterations between training steps (default 10)

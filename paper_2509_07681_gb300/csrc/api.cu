@@ -52,6 +52,7 @@ struct funcsne {
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     bool concurrent = false;  // run the two refinements side by side in the graph
     int32_t forces_cw = 8;    // floats of an LD row per lane in the forces kernel
+    int32_t hd_lanes_opt = 0; // lanes per gathered HD row (0: chosen from the row bytes)
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     int hd_blocks = 0, ld_blocks = 0, fo_blocks = 0, update_blocks = 0;
@@ -117,6 +118,19 @@ void drop_graphs(funcsne* h) {
     h->graph1 = h->graph8 = nullptr;
 }
 
+// Lanes per gathered HD row in the refinement: of the FP32 rows, or of the
+// BF16 / FP8 rows in reduced-precision modes.
+int hd_lanes(const funcsne* h) {
+    if (h->hd_lanes_opt) return h->hd_lanes_opt;
+    return lanes_per_row(h->precision == FUNCSNE_FP32 || h->qpitch == 0 ? 4 * h->xpitch : h->qpitch);
+}
+
+// Lanes per FP32 row: the FP32 path's grouping, which the exact re-rank of
+// the reduced-precision modes repeats.
+int hd_lanes_f32(const funcsne* h) {
+    return h->hd_lanes_opt ? h->hd_lanes_opt : lanes_per_row(4 * h->xpitch);
+}
+
 StepParams step_params(const funcsne* h) {
     StepParams p{};
     p.N = h->N;
@@ -131,6 +145,8 @@ StepParams step_params(const funcsne* h) {
     p.hd_mode = h->hd_mode;
     p.xs_floats = h->xs_floats;
     p.smem_per_warp = h->xs_floats * 4 + kHashSlots * 4;
+    p.gf = hd_lanes_f32(h);
+    p.ga = hd_lanes(h);
     p.alpha = h->alpha;
     p.inv_alpha = 1.f / h->alpha;
     p.inv2N = static_cast<float>(1.0 / (2.0 * static_cast<double>(h->N)));
@@ -199,9 +215,9 @@ cudaError_t launch_phase(const funcsne* h, int phase, const StepParams& p, cudaS
     switch (phase) {
         case 0:
             switch (h->precision) {
-                case FUNCSNE_FP32: return hd_refine_launch_f32(p, h->RH, h->hd_blocks, h->hd_smem, s);
-                case FUNCSNE_BF16: return hd_refine_launch_bf16(p, h->RH, h->hd_blocks, h->hd_smem, s);
-                default: return hd_refine_launch_fp8(p, h->RH, h->hd_blocks, h->hd_smem, s);
+                case FUNCSNE_FP32: return hd_refine_launch_f32(p, h->RH, p.ga, h->hd_blocks, h->hd_smem, s);
+                case FUNCSNE_BF16: return hd_refine_launch_bf16(p, h->RH, p.ga, h->hd_blocks, h->hd_smem, s);
+                default: return hd_refine_launch_fp8(p, h->RH, p.ga, h->hd_blocks, h->hd_smem, s);
             }
         case 1: return ld_refine_launch(p, h->DP, h->RH, h->ld_blocks, h->ld_smem, s);
         case 2: return forces_launch(p, h->DP, h->RH, h->forces_cw, h->fo_blocks, h->fo_smem, s);
@@ -225,9 +241,9 @@ int configure_step(funcsne* h) {
     h->ld_smem = h->fo_smem = static_cast<size_t>(8) * kHashSlots * 4;
     int occ = 0;
     switch (h->precision) {
-        case FUNCSNE_FP32: occ = hd_refine_occupancy_f32(h->RH, h->hd_smem); break;
-        case FUNCSNE_BF16: occ = hd_refine_occupancy_bf16(h->RH, h->hd_smem); break;
-        default: occ = hd_refine_occupancy_fp8(h->RH, h->hd_smem); break;
+        case FUNCSNE_FP32: occ = hd_refine_occupancy_f32(h->RH, hd_lanes(h), h->hd_smem); break;
+        case FUNCSNE_BF16: occ = hd_refine_occupancy_bf16(h->RH, hd_lanes(h), h->hd_smem); break;
+        default: occ = hd_refine_occupancy_fp8(h->RH, hd_lanes(h), h->hd_smem); break;
     }
     // the two refinements share the SMs when they run side by side
     const int ld_occ = ld_refine_occupancy(h->DP, h->RH, h->ld_smem);
@@ -646,6 +662,7 @@ int funcsne_create(const float* X, int64_t N, int32_t D, int32_t d, int32_t k_hd
         f.N = N;
         f.k_hd = k_hd;
         f.n4 = h->n4;
+        f.g = hd_lanes_f32(h);
         f.xpitch = h->xpitch;
         f.log_perp = std::log(perplexity);
         f.X32 = h->X32;
@@ -714,6 +731,11 @@ int funcsne_set_option(funcsne_t* h, const char* key, double v) {
         if (v != 4 && v != 8 && v != 16) return fail(h, FUNCSNE_E_ARG, "forces_cw must be 4, 8 or 16");
         h->forces_cw = static_cast<int32_t>(v);
         configure_step(h);
+    } else if (k == "hd_lanes") {
+        if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8)
+            return fail(h, FUNCSNE_E_ARG, "hd_lanes must be 0, 1, 2, 4 or 8");
+        h->hd_lanes_opt = static_cast<int32_t>(v);
+        configure_step(h);
     } else if (k == "concurrent") {
         if (v != 0 && v != 1) return fail(h, FUNCSNE_E_ARG, "concurrent must be 0 or 1");
         h->concurrent = v != 0;
@@ -762,6 +784,7 @@ int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
     else if (k == "precision") *v = h->precision;
     else if (k == "concurrent") *v = h->concurrent ? 1 : 0;
     else if (k == "forces_cw") *v = h->forces_cw;
+    else if (k == "hd_lanes") *v = hd_lanes(h);
     else if (k == "surrogate") *v = h->surrogate ? 1 : 0;
     else if (k == "mlp_every") *v = h->mlp_every;
     else if (k == "mlp_lr") *v = h->mlp_lr;
@@ -943,6 +966,7 @@ int funcsne_insert(funcsne_t* h, const float* X_new, int64_t n_new, int32_t plac
     q.k_hd = h->k_hd;
     q.k_ld = h->k_ld;
     q.n4 = h->n4;
+    q.g = hd_lanes_f32(h);
     q.xpitch = h->xpitch;
     q.log_perp = std::log(h->perplexity);
     q.t = s.t;
@@ -1102,6 +1126,7 @@ int funcsne_import_state(funcsne_t* h, const funcsne_state_t* st) {
         f.N = h->N;
         f.k_hd = h->k_hd;
         f.n4 = h->n4;
+        f.g = hd_lanes_f32(h);
         f.xpitch = h->xpitch;
         f.log_perp = std::log(h->perplexity);
         f.X32 = h->X32;

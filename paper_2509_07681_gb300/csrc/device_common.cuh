@@ -435,6 +435,199 @@ __device__ __forceinline__ ApproxDist dist_fp8(const float* __restrict__ xs,
     return finish_band(acc, s1, s2, gamma);
 }
 
+// ------------------------------------------------------- row-group distances
+// A warp scores the candidates of its 32 lanes (lane l owns candidate l) by
+// groups of G lanes per row (G = 1, 2, 4 or 8): R = 32 / G rows per pass. Lane l works in group l / G on the
+// 16-byte chunks s, s + G, s + 2G, ... of the row, s = l mod G, and an xor
+// butterfly inside the group adds the partial sums (the butterfly is
+// symmetric, so every lane of the group holds the same bits). G = 1 is the
+// plain lane-per-row loop of dist_f32. Narrow rows are gathered fastest one
+// lane per row, 128-byte rows four lanes per row, rows of several hundred
+// bytes eight lanes per row (wide lane-per-row gathers thrash L1).
+constexpr uint32_t kNoRow = 0xffffffffu;
+
+__device__ __forceinline__ float group_sum_rt(float v, int G) {
+    for (int m = 1; m < G; m <<= 1) v += __shfl_xor_sync(kFull, v, m);
+    return v;
+}
+
+__device__ __forceinline__ float part_f32(const float* __restrict__ xs, const float* __restrict__ xc, int n4,
+                                          int s, int G) {
+    const float4* a = reinterpret_cast<const float4*>(xs);
+    const float4* b = reinterpret_cast<const float4*>(xc);
+    float acc = 0.f;
+#pragma unroll 4
+    for (int q = s; q < n4; q += G) {
+        const float4 u = a[q];
+        const float4 v = __ldg(b + q);
+        float d = __fsub_rn(u.x, v.x);
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(u.y, v.y);
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(u.z, v.z);
+        acc = __fmaf_rn(d, d, acc);
+        d = __fsub_rn(u.w, v.w);
+        acc = __fmaf_rn(d, d, acc);
+    }
+    return acc;
+}
+
+// FP32 squared distance from the staged own row xs to row cv of X32, for the
+// candidate of every lane (0 where cv == kNoRow). All lanes must call it.
+template <int G>
+__device__ __forceinline__ float group_dist_f32(const float* __restrict__ xs, const float* __restrict__ X32,
+                                                int xpitch, int n4, uint32_t cv, int lane) {
+    constexpr int R = 32 / G;
+    const int g = lane / G, s = lane & (G - 1);
+    float mine = 0.f;
+#pragma unroll
+    for (int p = 0; p < G; ++p) {
+        const uint32_t cj = __shfl_sync(kFull, cv, p * R + g);
+        float acc = 0.f;
+        if (cj != kNoRow) acc = part_f32(xs, X32 + static_cast<int64_t>(cj) * xpitch, n4, s, G);
+        acc = group_sum_rt(acc, G);
+        const float v = __shfl_sync(kFull, acc, (lane & (R - 1)) * G);
+        if (lane / R == p) mine = v;
+    }
+    return mine;
+}
+
+// The same FP32 distances (same grouping, hence the same bits) for only the
+// lanes with need == true, packed R to a pass. All lanes must call it.
+__device__ __forceinline__ float group_rerank_f32(const float* __restrict__ xs, const float* __restrict__ X32,
+                                                  int xpitch, int n4, uint32_t c, bool need, int lane, int G) {
+    const uint32_t m = __ballot_sync(kFull, need);
+    const int nn = __popc(m);
+    const int R = 32 / G, g = lane / G, s = lane & (G - 1);
+    const int rank = __popc(m & ((1u << lane) - 1u));
+    float mine = 0.f;
+    for (int base = 0; base < nn; base += R) {
+        const int k = base + g;  // this group scores the k-th flagged lane's row
+        uint32_t mk = m;
+        for (int j = 0; j < k && mk; ++j) mk &= mk - 1u;
+        const int src = (k < nn) ? (__ffs(static_cast<int>(mk)) - 1) : 0;
+        const uint32_t cj = __shfl_sync(kFull, c, src);
+        float acc = 0.f;
+        if (k < nn) acc = part_f32(xs, X32 + static_cast<int64_t>(cj) * xpitch, n4, s, G);
+        acc = group_sum_rt(acc, G);
+        const int r = rank - base;
+        const bool mine_here = need && r >= 0 && r < R;
+        const float v = __shfl_sync(kFull, acc, (mine_here ? r : 0) * G);
+        if (mine_here) mine = v;
+    }
+    return mine;
+}
+
+// BF16 rows by groups: the distance to the dequantised row and the
+// Cauchy-Schwarz band of dist_bf16, for the candidate of every lane.
+template <int G>
+__device__ __forceinline__ ApproxDist group_dist_bf16(const float* __restrict__ xs,
+                                                      const uint8_t* __restrict__ Xq, int qpitch, int nq,
+                                                      uint32_t cv, int lane, float u, float gamma) {
+    constexpr int R = 32 / G;
+    const int g = lane / G, s = lane & (G - 1);
+    const int sn = nq & (G - 1);  // the lane of a group that reads the norm chunk
+    float my_acc = 0.f, my_nrm = 0.f;
+#pragma unroll
+    for (int p = 0; p < G; ++p) {
+        const uint32_t cj = __shfl_sync(kFull, cv, p * R + g);
+        float acc = 0.f, nrm = 0.f;
+        if (cj != kNoRow) {
+            const uint4* b = reinterpret_cast<const uint4*>(Xq + static_cast<int64_t>(cj) * qpitch);
+#pragma unroll 2
+            for (int q = s; q < nq; q += G) {
+                const uint4 raw = __ldg(b + q);
+                const float4 x0 = reinterpret_cast<const float4*>(xs)[2 * q];
+                const float4 x1 = reinterpret_cast<const float4*>(xs)[2 * q + 1];
+                float d = __fsub_rn(x0.x, __uint_as_float(raw.x << 16));
+                acc = __fmaf_rn(d, d, acc);
+                d = __fsub_rn(x0.y, __uint_as_float(raw.x & 0xffff0000u));
+                acc = __fmaf_rn(d, d, acc);
+                d = __fsub_rn(x0.z, __uint_as_float(raw.y << 16));
+                acc = __fmaf_rn(d, d, acc);
+                d = __fsub_rn(x0.w, __uint_as_float(raw.y & 0xffff0000u));
+                acc = __fmaf_rn(d, d, acc);
+                d = __fsub_rn(x1.x, __uint_as_float(raw.z << 16));
+                acc = __fmaf_rn(d, d, acc);
+                d = __fsub_rn(x1.y, __uint_as_float(raw.z & 0xffff0000u));
+                acc = __fmaf_rn(d, d, acc);
+                d = __fsub_rn(x1.z, __uint_as_float(raw.w << 16));
+                acc = __fmaf_rn(d, d, acc);
+                d = __fsub_rn(x1.w, __uint_as_float(raw.w & 0xffff0000u));
+                acc = __fmaf_rn(d, d, acc);
+            }
+            if (s == sn) nrm = __ldg(reinterpret_cast<const float*>(b + nq));
+        }
+        acc = group_sum_rt(acc, G);
+        const int src = (lane & (R - 1)) * G;
+        const float va = __shfl_sync(kFull, acc, src);
+        const float vn = __shfl_sync(kFull, nrm, src + sn);
+        if (lane / R == p) {
+            my_acc = va;
+            my_nrm = vn;
+        }
+    }
+    const float E = u * my_nrm;
+    const float b0 = 2.f * sqrtf(my_acc * (1.f + gamma)) * E + E * E;
+    ApproxDist r;
+    r.d2 = my_acc;
+    r.band = b0 * (1.f + 4.f * gamma) + gamma * (2.f * my_acc + 2.f * b0) + 1e-30f;
+    return r;
+}
+
+// FP8-E4M3 rows by groups: distance to the dequantised row and the
+// element-wise band of dist_fp8, for the candidate of every lane.
+template <int G>
+__device__ __forceinline__ ApproxDist group_dist_fp8(const float* __restrict__ xs,
+                                                     const uint8_t* __restrict__ Xq, int qpitch, int nw,
+                                                     int scale_off, uint32_t cv, int lane, float u,
+                                                     float a_rel, float gamma) {
+    constexpr int R = 32 / G;
+    const int g = lane / G, s = lane & (G - 1);
+    const int nch = (nw + 3) >> 2;
+    float my_acc = 0.f, my_s1 = 0.f, my_s2 = 0.f;
+#pragma unroll
+    for (int p = 0; p < G; ++p) {
+        const uint32_t cj = __shfl_sync(kFull, cv, p * R + g);
+        float acc = 0.f, s1 = 0.f, s2 = 0.f;
+        if (cj != kNoRow) {
+            const uint8_t* row = Xq + static_cast<int64_t>(cj) * qpitch;
+            const float sc = __ldg(reinterpret_cast<const float*>(row + scale_off));
+            const float a = a_rel * sc;
+            const uint4* b = reinterpret_cast<const uint4*>(row);
+            for (int q = s; q < nch; q += G) {
+                const uint4 raw = __ldg(b + q);
+                const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (4 * q + m < nw) {
+                        float v[4];
+                        fp8x4_to_float(w4[m], sc, v);
+                        const float4 xi = reinterpret_cast<const float4*>(xs)[4 * q + m];
+                        approx_acc(xi.x, v[0], u, a, acc, s1, s2);
+                        approx_acc(xi.y, v[1], u, a, acc, s1, s2);
+                        approx_acc(xi.z, v[2], u, a, acc, s1, s2);
+                        approx_acc(xi.w, v[3], u, a, acc, s1, s2);
+                    }
+                }
+            }
+        }
+        acc = group_sum_rt(acc, G);
+        s1 = group_sum_rt(s1, G);
+        s2 = group_sum_rt(s2, G);
+        const int src = (lane & (R - 1)) * G;
+        const float va = __shfl_sync(kFull, acc, src);
+        const float v1 = __shfl_sync(kFull, s1, src);
+        const float v2 = __shfl_sync(kFull, s2, src);
+        if (lane / R == p) {
+            my_acc = va;
+            my_s1 = v1;
+            my_s2 = v2;
+        }
+    }
+    return finish_band(my_acc, my_s1, my_s2, gamma);
+}
+
 // ---------------------------------------------------------------- warp hash sets
 // Open-addressing set of point indices in shared memory (256 slots, linear
 // probing, EMPTY = 0xffffffff). At most 96 entries are ever inserted, so an

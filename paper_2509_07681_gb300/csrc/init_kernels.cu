@@ -29,7 +29,8 @@ __global__ void init_lists_kernel(int64_t N, int k, uint32_t stream, uint64_t se
     }
 }
 
-// Warp per point: FP32 distances of the listed HD neighbours, order by
+// Warp per point: FP32 distances of the listed HD neighbours (grouped as in
+// the iteration, so stored and freshly scored distances agree bit for bit), order by
 // (d2, idx), then either a cold-start bisection (Pin == nullptr) or the
 // imported P row permuted along with the entries. Lists must be valid.
 template <int RH>
@@ -54,11 +55,12 @@ __global__ void __launch_bounds__(256) hd_finalize_kernel(FinalizeParams f) {
             pin[r] = 0.f;
             idx0[r] = 0xffffffffu;
             if (e < k) {
-                const uint32_t j = static_cast<uint32_t>(f.idx[gi * k + e]);
-                idx0[r] = j;
-                key[r] = make_key(dist_f32(xs, f.X32 + static_cast<int64_t>(j) * f.xpitch, f.n4), j);
+                idx0[r] = static_cast<uint32_t>(f.idx[gi * k + e]);
                 if (f.Pin) pin[r] = f.Pin[gi * k + e];
             }
+            // the same FP32 grouping as the iteration's distances
+            const float d = group_rerank_f32(xs, f.X32, f.xpitch, f.n4, idx0[r], e < k, lane, f.g);
+            if (e < k) key[r] = make_key(d, idx0[r]);
         }
         warp_sort<RH>(key, lane);
         float d2[RH], pv[RH];

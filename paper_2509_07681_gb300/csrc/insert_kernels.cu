@@ -58,10 +58,9 @@ __global__ void __launch_bounds__(256) insert_refine_kernel(InsertParams q) {
     for (int r = 0; r < RH; ++r) {
         const int e = r * 32 + lane;
         key[r] = kSentinel;
-        if (e < k) {
-            const uint32_t j = static_cast<uint32_t>(q.hd_idx[gi * k + e]);
-            key[r] = make_key(dist_f32(xs, q.X32 + static_cast<int64_t>(j) * q.xpitch, q.n4), j);
-        }
+        const uint32_t j = e < k ? static_cast<uint32_t>(q.hd_idx[gi * k + e]) : kNoRow;
+        const float d = group_rerank_f32(xs, q.X32, q.xpitch, q.n4, j, e < k, lane, q.g);
+        if (e < k) key[r] = make_key(d, j);
     }
     warp_sort<RH>(key, lane);
     const uint32_t m = static_cast<uint32_t>(q.n_old);
@@ -82,8 +81,8 @@ __global__ void __launch_bounds__(256) insert_refine_kernel(InsertParams q) {
             for (int s = 0; s < 32; ++s) valid &= (__shfl_sync(kFull, li[r], s) != c);
         const unsigned same = __match_any_sync(kFull, c);
         valid &= (same & ((1u << lane) - 1u)) == 0u;
-        const uint64_t ck = valid ? make_key(dist_f32(xs, q.X32 + static_cast<int64_t>(c) * q.xpitch, q.n4), c)
-                                  : kSentinel;
+        const float dc = group_rerank_f32(xs, q.X32, q.xpitch, q.n4, c, valid, lane, q.g);
+        const uint64_t ck = valid ? make_key(dc, c) : kSentinel;
         merge_candidates<RH>(key, ck, lane);
     }
     float d2[RH], pv[RH];

@@ -13,6 +13,7 @@ namespace fsne {
 struct FinalizeParams {
     int64_t N;
     int32_t k_hd, n4, xpitch;
+    int32_t g;        // lanes per FP32 row (the iteration's grouping)
     float log_perp;
     const float* X32;
     int32_t* idx;     // N x k_hd, sorted in place
@@ -48,6 +49,7 @@ struct KnnParams {
 struct InsertParams {
     int64_t N, n_old;
     int32_t k_hd, k_ld, n4, xpitch;
+    int32_t g;         // lanes per FP32 row (the iteration's grouping)
     float log_perp;
     uint32_t t;
     uint64_t seed;
@@ -65,12 +67,12 @@ struct InsertParams {
 
 // phase kernels of the iteration (HD refinement: one translation unit per
 // HD storage precision)
-cudaError_t hd_refine_launch_f32(const StepParams& p, int RH, int blocks, size_t smem, cudaStream_t s);
-cudaError_t hd_refine_launch_bf16(const StepParams& p, int RH, int blocks, size_t smem, cudaStream_t s);
-cudaError_t hd_refine_launch_fp8(const StepParams& p, int RH, int blocks, size_t smem, cudaStream_t s);
-int hd_refine_occupancy_f32(int RH, size_t smem);
-int hd_refine_occupancy_bf16(int RH, size_t smem);
-int hd_refine_occupancy_fp8(int RH, size_t smem);
+cudaError_t hd_refine_launch_f32(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s);
+cudaError_t hd_refine_launch_bf16(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s);
+cudaError_t hd_refine_launch_fp8(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s);
+int hd_refine_occupancy_f32(int RH, int G, size_t smem);
+int hd_refine_occupancy_bf16(int RH, int G, size_t smem);
+int hd_refine_occupancy_fp8(int RH, int G, size_t smem);
 cudaError_t ld_refine_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
 cudaError_t forces_launch(const StepParams& p, int DP, int RH, int CW, int blocks, size_t smem, cudaStream_t s);
 int ld_refine_occupancy(int DP, int RH, size_t smem);

@@ -61,6 +61,16 @@ struct DevScalars {
 constexpr uint32_t kErrNonFinite = 1u;
 constexpr uint32_t kErrIndex = 2u;
 
+// Lanes per row for gathering rows of `bytes` bytes in the HD refinement
+// (measured on GB300 over 1M-2M points, rows of 64 to 3136 bytes): two lanes
+// up to 224 bytes, four up to 800, eight beyond. Wide rows read one lane per
+// row thrash L1 (44 ms against 7.6 ms at 1 KB rows and 2M points).
+inline int lanes_per_row(int bytes) {
+    if (bytes <= 224) return 2;
+    if (bytes <= 800) return 4;
+    return 8;
+}
+
 struct StepParams {
     int64_t N;
     int32_t k_hd, k_ld, n_neg;
@@ -72,6 +82,7 @@ struct StepParams {
     int32_t hd_mode;
     int32_t smem_per_warp;  // bytes
     int32_t xs_floats;      // own-row floats staged per warp
+    int32_t gf, ga;         // lanes per row: FP32 rows, reduced-precision rows (1, 2, 4 or 8)
     float alpha, inv_alpha, inv2N, neg_scale, log_perp;
     float q_u, q_a, q_gamma;  // dequantisation error model (see dist_bf16 / dist_fp8)
     uint64_t seed;

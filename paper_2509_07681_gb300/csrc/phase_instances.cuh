@@ -10,29 +10,34 @@ namespace fsne {
 #define FSNE_SET_SMEM(kern, smem) \
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))
 
+// RH in {1, 2} (k_hd up to 32 or 64), G in {1, 2, 4, 8} lanes per gathered row.
+#define FSNE_HD_CASES(X) X(1, 1) X(1, 2) X(1, 4) X(1, 8) X(2, 1) X(2, 2) X(2, 4) X(2, 8)
+
 template <int XM>
-cudaError_t hd_refine_launch_xm(const StepParams& p, int RH, int blocks, size_t smem, cudaStream_t s) {
-    if (RH == 1) {
-        FSNE_SET_SMEM((hd_refine_kernel<1, XM>), smem);
-        hd_refine_kernel<1, XM><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);
-    } else {
-        FSNE_SET_SMEM((hd_refine_kernel<2, XM>), smem);
-        hd_refine_kernel<2, XM><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);
+cudaError_t hd_refine_launch_xm(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s) {
+#define FSNE_CASE(rh, g)                                                                \
+    if (RH == rh && G == g) {                                                           \
+        FSNE_SET_SMEM((hd_refine_kernel<rh, XM, g>), smem);                             \
+        hd_refine_kernel<rh, XM, g><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);       \
+        return cudaGetLastError();                                                      \
     }
-    return cudaGetLastError();
+    FSNE_HD_CASES(FSNE_CASE)
+#undef FSNE_CASE
+    return cudaErrorInvalidValue;
 }
 
 template <int XM>
-int hd_refine_occupancy_xm(int RH, size_t smem) {
+int hd_refine_occupancy_xm(int RH, int G, size_t smem) {
     int n = 0;
-    if (RH == 1) {
-        FSNE_SET_SMEM((hd_refine_kernel<1, XM>), smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hd_refine_kernel<1, XM>, kWarpsPerBlock * 32, smem);
-    } else {
-        FSNE_SET_SMEM((hd_refine_kernel<2, XM>), smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hd_refine_kernel<2, XM>, kWarpsPerBlock * 32, smem);
+#define FSNE_CASE(rh, g)                                                                           \
+    if (RH == rh && G == g) {                                                                      \
+        FSNE_SET_SMEM((hd_refine_kernel<rh, XM, g>), smem);                                        \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hd_refine_kernel<rh, XM, g>, kWarpsPerBlock * 32, smem); \
+        return n;                                                                                  \
     }
-    return n;
+    FSNE_HD_CASES(FSNE_CASE)
+#undef FSNE_CASE
+    return 0;
 }
 
 }  // namespace fsne

@@ -53,13 +53,15 @@ __device__ __forceinline__ ListView list_view(const StepParams& p, int hc, int l
 
 // ------------------------------------------------------------------ HD refinement
 // Resident blocks per SM the registers are sized for: the kernel waits
-// mostly on memory; the reduced-precision variants fit five blocks (40
-// warps) without spilling, the FP32 one four.
-template <int XM>
-constexpr int hd_refine_min_blocks() { return XM == 0 ? 4 : 5; }
+// mostly on memory; the reduced-precision variants with k_hd <= 32 fit five
+// blocks (40 warps) with little spilling, the others four.
+template <int XM, int RH>
+constexpr int hd_refine_min_blocks() { return (XM != 0 && RH == 1) ? 5 : 4; }
 
-template <int RH, int XM>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, hd_refine_min_blocks<XM>())
+// G: lanes per gathered row, of the FP32 rows (XM = 0) or of the BF16 / FP8
+// rows (the exact re-rank then takes the FP32 rows' p.gf at run time).
+template <int RH, int XM, int G>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, hd_refine_min_blocks<XM, RH>())
 hd_refine_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -117,26 +119,25 @@ hd_refine_kernel(const StepParams p) {
         valid &= (__match_any_sync(kFull, c) & ((1u << lane) - 1u)) == 0u;
 
         uint64_t ck = kSentinel;
+        const uint32_t cv = valid ? c : kNoRow;
         if constexpr (XM == 0) {
-            if (valid) ck = make_key(dist_f32(xs, p.X32 + static_cast<int64_t>(c) * p.xpitch, p.n4), c);
+            const float d = group_dist_f32<G>(xs, p.X32, p.xpitch, p.n4, cv, lane);
+            if (valid) ck = make_key(d, c);
         } else {
             const float thr = warp_get<RH>(hd2, static_cast<uint32_t>(k_hd - 1));
-            bool need = false;
-            if (valid) {
-                ApproxDist a;
-                if constexpr (XM == 1)
-                    a = dist_bf16(xs, reinterpret_cast<const uint16_t*>(p.Xq + static_cast<int64_t>(c) * p.qpitch),
-                                  p.nq, p.q_u, p.q_gamma);
-                else
-                    a = dist_fp8(xs, p.Xq + static_cast<int64_t>(c) * p.qpitch, p.nq, p.qscale_off, p.q_u,
-                                 p.q_a, p.q_gamma);  // nq = code words for FP8
-                need = __fsub_rd(a.d2, a.band) <= thr;
-                ++c_scored;
-            }
-            if (need) {
-                ++c_rerank;
-                ck = make_key(dist_f32(xs, p.X32 + static_cast<int64_t>(c) * p.xpitch, p.n4), c);
-            }
+            ApproxDist a;
+            if constexpr (XM == 1)
+                a = group_dist_bf16<G>(xs, p.Xq, p.qpitch, p.nq, cv, lane, p.q_u, p.q_gamma);
+            else  // nq = code words for FP8
+                a = group_dist_fp8<G>(xs, p.Xq, p.qpitch, p.nq, p.qscale_off, cv, lane, p.q_u, p.q_a,
+                                      p.q_gamma);
+            const bool need = valid && __fsub_rd(a.d2, a.band) <= thr;
+            c_scored += valid ? 1 : 0;
+            c_rerank += need ? 1 : 0;
+            // candidates that can enter: the exact FP32 distance, computed as
+            // in FP32 mode (same grouping), so the lists equal FP32 mode's
+            const float d = group_rerank_f32(xs, p.X32, p.xpitch, p.n4, c, need, lane, p.gf);
+            if (need) ck = make_key(d, c);
         }
         // flag: some candidate precedes the old k-th entry
         uint64_t keys[RH];

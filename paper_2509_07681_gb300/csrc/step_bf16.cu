@@ -3,9 +3,9 @@
 
 namespace fsne {
 
-cudaError_t hd_refine_launch_bf16(const StepParams& p, int RH, int blocks, size_t smem, cudaStream_t s) {
-    return hd_refine_launch_xm<1>(p, RH, blocks, smem, s);
+cudaError_t hd_refine_launch_bf16(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s) {
+    return hd_refine_launch_xm<1>(p, RH, G, blocks, smem, s);
 }
-int hd_refine_occupancy_bf16(int RH, size_t smem) { return hd_refine_occupancy_xm<1>(RH, smem); }
+int hd_refine_occupancy_bf16(int RH, int G, size_t smem) { return hd_refine_occupancy_xm<1>(RH, G, smem); }
 
 }  // namespace fsne

@@ -4,10 +4,10 @@
 
 namespace fsne {
 
-cudaError_t hd_refine_launch_f32(const StepParams& p, int RH, int blocks, size_t smem, cudaStream_t s) {
-    return hd_refine_launch_xm<0>(p, RH, blocks, smem, s);
+cudaError_t hd_refine_launch_f32(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s) {
+    return hd_refine_launch_xm<0>(p, RH, G, blocks, smem, s);
 }
-int hd_refine_occupancy_f32(int RH, size_t smem) { return hd_refine_occupancy_xm<0>(RH, smem); }
+int hd_refine_occupancy_f32(int RH, int G, size_t smem) { return hd_refine_occupancy_xm<0>(RH, G, smem); }
 
 #define FSNE_DP_RH(X)                                                                           \
     X(2, 1) X(4, 1) X(8, 1) X(16, 1) X(32, 1) X(2, 2) X(4, 2) X(8, 2) X(16, 2) X(32, 2)

@@ -117,10 +117,13 @@ def test_one_iteration_matches_oracle(case):
     m.close()
 
 
+@pytest.mark.parametrize("dim", [50, 200])
 @pytest.mark.parametrize("precision", [F.BF16, F.FP8])
-def test_reduced_precision_sets_equal_fp32(precision):
-    """BF16 / FP8 rows with the exact FP32 re-rank give the FP32 path's sets."""
-    X = synth.spectrum(n=4000, dim=50, n_clusters=12, seed=7)
+def test_reduced_precision_sets_equal_fp32(precision, dim):
+    """BF16 / FP8 rows with the exact FP32 re-rank give the FP32 path's sets
+    and distances bit for bit (D = 200: the reduced-precision rows and the
+    FP32 rows are read by different numbers of lanes per row)."""
+    X = synth.spectrum(n=4000, dim=dim, n_clusters=12, seed=7)
     p = CASES["spectrum-shape"][1]
     m = _make(X, p, hd_mode=1)
     m.step(3)
