@@ -354,13 +354,15 @@ def run_ours(args, rank, world):
 def run_dynamic(args, rank, world):
     """Dynamic dataset: a 200,000-point swiss-roll base, then `rounds` times
     insert `insert_n` points of a fresh draw of the same generator and run
-    `every` iterations. After each insertion the LD lists of the new points
-    are checked every `check` iterations against their exact HD neighbours
-    (recall@k_ld); a round has converged once the new points' recall is
-    within 0.5 points of that of 2,000 established points. Reported per
-    placement (neighbour mean, surrogate MLP): insertion-to-converged
-    iterations and milliseconds (insertion + iterations, surrogate training
-    included), recall right after insertion and at the round's end."""
+    `every` iterations. Every `check` iterations after an insertion the HD
+    lists of the new points are compared with their exact HD neighbours
+    (recall@k_hd) and so are those of 2,000 established points; a round has
+    converged once the new points' recall is within 0.5 points of the
+    established points' (and has reached 90% once it is 0.9 times theirs). The LD lists' recall of the exact HD neighbours
+    (recall@k_ld, the embedding's neighbourhood preservation) is reported the
+    same way. Per placement (neighbour mean, surrogate MLP): insertion-to-
+    converged iterations and milliseconds (insertion + iterations, surrogate
+    training included), recall right after insertion and at each round's end."""
     import torch
     from paper_2509_07681_gb300 import funcsne as F
     from paper_2509_07681_gb300 import synth
@@ -371,18 +373,18 @@ def run_dynamic(args, rank, world):
     base_n = args.n or 200_000
     X0, p = synth.make(name, n=base_n)
     D = X0.shape[1]
-    n_new, rounds, every, check = args.insert_n, args.rounds, 50, 5
+    n_new, rounds, every, check = args.insert_n, args.rounds, args.every, 5
     batches = [synth.swissroll(n=n_new, dim=D, n_clusters=32, seed=0, batch=r + 1) for r in range(rounds)]
     rng = np.random.default_rng(1)
     q_old = np.sort(rng.choice(base_n, 2000, replace=False)).astype(np.int32)
-    k = p["k_ld"]
+    kh, kl = p["k_hd"], p["k_ld"]
     stream = torch.cuda.Stream()
     arms = {}
     clocks = ClockSampler(local)
     clocks.start()
     for arm, place in (("mean", F.PLACE_MEAN), ("surrogate", F.PLACE_SURROGATE)):
-        m = F.FuncSNE(X0, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0,
-                      precision=F.BF16)
+        m = F.FuncSNE(X0, p["d"], kh, kl, p["n_neg"], p["alpha"], p["perplexity"], seed=0, precision=F.BF16,
+                      hd_mode=args.hd_mode, insert_rounds=args.insert_rounds)
         m.set_stream(stream)
         if arm == "surrogate":
             m.set_option("surrogate", 1)
@@ -403,44 +405,69 @@ def run_dynamic(args, rank, world):
             m.sync()
             t_ins = time.perf_counter() - t0
             q_new = np.arange(first, first + n_new, dtype=np.int32)
-            ex_new, _ = m.exact_knn(q_new, k)
-            ex_old, _ = m.exact_knn(q_old, k)
+            ex_new, _ = m.exact_knn(q_new, kh)
+            ex_old, _ = m.exact_knn(q_old, kh)
             Y_ins = m.embedding()[first:].astype(np.float64)
-            ld = m.knn(F.SPACE_LD, with_d2=False)
-            rec0 = recall(ld[q_new], ex_new)
-            it, t_steps, conv_it, conv_ms = 0, 0.0, None, None
+
+            def measure():
+                hd = m.knn(F.SPACE_HD, with_d2=False)
+                ld = m.knn(F.SPACE_LD, with_d2=False)
+                return (recall(hd[q_new], ex_new), recall(hd[q_old], ex_old),
+                        recall(ld[q_new], ex_new[:, :kl]), recall(ld[q_old], ex_old[:, :kl]))
+
+            h0, _, l0, _ = measure()
+            it, t_steps, conv_it, conv_ms, curve = 0, 0.0, None, None, []
+            c90_it, c90_ms = None, None
             while it < every:
                 t0 = time.perf_counter()
                 m.step(check)
                 m.sync()
                 t_steps += time.perf_counter() - t0
                 it += check
-                ld = m.knn(F.SPACE_LD, with_d2=False)
-                rn, ro = recall(ld[q_new], ex_new), recall(ld[q_old], ex_old)
-                if conv_it is None and rn >= ro - 0.005:
+                hn, ho, ln, lo = measure()
+                curve.append(round(hn, 4))
+                if conv_it is None and hn >= ho - 0.005:
                     conv_it, conv_ms = it, (t_ins + t_steps) * 1e3
+                if c90_it is None and hn >= 0.9 * ho:
+                    c90_it, c90_ms = it, (t_ins + t_steps) * 1e3
             Y = m.embedding().astype(np.float64)
             scale = np.sqrt(np.mean(Y[:first] ** 2))
             move = float(np.sqrt(np.mean(np.sum((Y[first:] - Y_ins) ** 2, 1))) / scale)
             step_s += t_steps
             n_steps += every
-            per_round.append(dict(insert_ms=round(t_ins * 1e3, 3), recall_new_at_insert=round(rec0, 4),
-                                  converged_iters=conv_it, converged_ms=None if conv_ms is None else round(conv_ms, 3),
-                                  recall_new_end=round(rn, 4), recall_old_end=round(ro, 4),
-                                  movement=round(move, 4)))
+            per_round.append(dict(insert_ms=round(t_ins * 1e3, 3), hd_recall_new_at_insert=round(h0, 4),
+                                  ld_recall_new_at_insert=round(l0, 4), converged_iters=conv_it,
+                                  converged_ms=None if conv_ms is None else round(conv_ms, 3),
+                                  reach90_iters=c90_it, reach90_ms=None if c90_ms is None else round(c90_ms, 3),
+                                  hd_recall_new_end=round(hn, 4), hd_recall_old_end=round(ho, 4),
+                                  ld_recall_new_end=round(ln, 4), ld_recall_old_end=round(lo, 4),
+                                  movement=round(move, 4), hd_recall_new_curve=curve))
         st = m.stats()
         m.close()
         conv = [x["converged_iters"] for x in per_round if x["converged_iters"] is not None]
         conv_ms = [x["converged_ms"] for x in per_round if x["converged_ms"] is not None]
+        r90 = [x["reach90_ms"] for x in per_round if x["reach90_ms"] is not None]
+        r90i = [x["reach90_iters"] for x in per_round if x["reach90_iters"] is not None]
+
+        def mean_of(key):
+            return round(float(np.mean([x[key] for x in per_round])), 4)
+
         arms[arm] = {
             "rounds_converged": len(conv), "rounds": rounds,
             "median_converged_iters": statistics.median(conv) if conv else None,
             "median_converged_ms": round(statistics.median(conv_ms), 3) if conv_ms else None,
+            "rounds_reached_90pct": len(r90),
+            "median_reach90_iters": statistics.median(r90i) if r90i else None,
+            "median_reach90_ms": round(statistics.median(r90), 3) if r90 else None,
             "median_insert_ms": round(statistics.median(x["insert_ms"] for x in per_round), 3),
-            "mean_recall_new_at_insert": round(float(np.mean([x["recall_new_at_insert"] for x in per_round])), 4),
-            "mean_recall_new_end": round(float(np.mean([x["recall_new_end"] for x in per_round])), 4),
-            "mean_recall_old_end": round(float(np.mean([x["recall_old_end"] for x in per_round])), 4),
-            "mean_movement": round(float(np.mean([x["movement"] for x in per_round])), 4),
+            "mean_hd_recall_new_at_insert": mean_of("hd_recall_new_at_insert"),
+            "mean_hd_recall_new_end": mean_of("hd_recall_new_end"),
+            "mean_hd_recall_old_end": mean_of("hd_recall_old_end"),
+            "mean_ld_recall_new_end": mean_of("ld_recall_new_end"),
+            "mean_ld_recall_old_end": mean_of("ld_recall_old_end"),
+            "mean_hd_recall_new_curve": [round(float(v), 4) for v in
+                                         np.mean([x["hd_recall_new_curve"] for x in per_round], axis=0)],
+            "mean_movement": mean_of("movement"),
             "ms_per_iter": round(step_s * 1e3 / n_steps, 4), "mlp_pretrain_ms": round(t_pre * 1e3, 1),
             "mlp_steps": st["mlp_steps"], "final_N": base_n + rounds * n_new, "per_round": per_round}
     clk = clocks.stop()
@@ -448,14 +475,15 @@ def run_dynamic(args, rank, world):
         if dist is not None:
             dist.destroy_process_group()
         return None
-    line = {"metric": "insertion-to-converged ms (dynamic dataset, recall within 0.5 points)",
+    line = {"metric": "insertion-to-converged ms (dynamic dataset, HD-KNN recall within 0.5 points)",
             "value": arms["surrogate"]["median_converged_ms"], "unit": "ms", "higher_is_better": False,
             "n_gpus": world, "data": "synthetic", "dtype": "f32",
-            "config": {"workload": f"{name} dynamic", "base_N": base_n, "D": D, "d": p["d"], "k_hd": p["k_hd"],
-                       "k_ld": k, "n_neg": p["n_neg"], "insert": n_new, "rounds": rounds, "every": every,
+            "config": {"workload": f"{name} dynamic", "base_N": base_n, "D": D, "d": p["d"], "k_hd": kh,
+                       "k_ld": kl, "n_neg": p["n_neg"], "insert": n_new, "rounds": rounds, "every": every,
                        "check_every": check, "storage": "bf16 rows + fp32 boundary re-rank",
-                       "hd_refine": "adaptive coin", "mlp": f"{D}-256-256-{p['d']}, batch 4096, every 10 iters",
-                       "mlp_pretrain_steps": args.mlp_pretrain},
+                       "hd_refine": {0: "adaptive coin", 1: "every iteration", 2: "never"}[args.hd_mode],
+                       "mlp": f"{D}-256-256-{p['d']}, batch 4096, every 10 iters",
+                       "mlp_pretrain_steps": args.mlp_pretrain, "insert_rounds": args.insert_rounds},
             "arms": arms, "clocks": clk}
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -565,6 +593,11 @@ def parse_args(argv=None):
     ap.add_argument("--burn-in", type=int, default=0, help="untimed iterations first (0: the mode's default)")
     ap.add_argument("--insert-n", type=int, default=10000, help="--mode dynamic: points per insertion")
     ap.add_argument("--rounds", type=int, default=20, help="--mode dynamic: insertion rounds")
+    ap.add_argument("--every", type=int, default=50, help="--mode dynamic: iterations between insertions")
+    ap.add_argument("--insert-rounds", type=int, default=16,
+                    help="--mode dynamic: neighbour-of-neighbour rounds of each insertion")
+    ap.add_argument("--hd-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="--mode dynamic: 0 adaptive HD refinement, 1 every iteration, 2 never")
     ap.add_argument("--mlp-pretrain", type=int, default=0,
                     help="--mode dynamic: extra MLP steps before the first insertion (timed, reported)")
     return ap.parse_args(argv)

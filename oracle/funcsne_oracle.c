@@ -94,7 +94,6 @@ enum {
 #define GAMMA_E 0.1            /* smoothing of E[N_new/N]                   */
 #define GAMMA_Z 0.1            /* smoothing of the normalisation estimate   */
 #define INIT_Y_STD 1e-4        /* per-dimension std of the initial layout   */
-#define INSERT_ROUNDS 4        /* neighbour-of-neighbour rounds per insertion */
 #define INSERT_SLOTS_NN 24     /* insertion slots 0..23: neighbour of neighbour */
                                /* insertion slots 24..31: random existing point */
 
@@ -794,18 +793,19 @@ static void place_mean(oracle_state *st, int64_t i)
  *   1. HD list: k_hd distinct existing points, slot l drawing an offset in
  *      [0, n_old) from counter (t, i, INSERT, l), linear probing mod n_old;
  *      ordered by (d2, idx);
- *   2. INSERT_ROUNDS rounds of 32 candidates, round r slot s from counter
+ *   2. `rounds` rounds of 32 candidates, round r slot s from counter
  *      (t, i, INSERT, 64 + 32 r + s): slots 0..23 a = list(i)[w0 * k_hd],
  *      c = list(a)[w1 * k_hd] (a is an existing point, its list of
  *      iteration t); slots 24..31 a uniform existing point; top-k merge;
  *   3. cold-start bisection for beta and P;
  *   4. Y = mean of the HD neighbours' Y (placement 0); V = 0;
  *   5. LD list = the first k_ld HD neighbours, completed (when k_ld > k_hd)
- *      by distinct random existing points from counter (t, i, INSERT, 256 + l);
+ *      by distinct random existing points from counter (t, i, INSERT, 2^30 + l)
+ *      (above every round's slots);
  *   6. Zhat scaled by the ratio of ordered pair counts, E = max(E, n_new/N).
  * Placement 1 (a learned map) is handled by the caller, which overwrites Y.
  */
-void oracle_insert(oracle_state *st, int64_t n_old, double bisect_tol, int bisect_maxit)
+void oracle_insert(oracle_state *st, int64_t n_old, int rounds, double bisect_tol, int bisect_maxit)
 {
     int64_t N = st->N;
     int D = st->D, kh = st->k_hd, kl = st->k_ld;
@@ -832,7 +832,7 @@ void oracle_insert(oracle_state *st, int64_t n_old, double bisect_tol, int bisec
             st->hd_idx[i * kh + l] = (int32_t)o;
         }
         sort_hd_list(st, i);
-        for (int r = 0; r < INSERT_ROUNDS; ++r) {
+        for (int r = 0; r < rounds; ++r) {
             for (int a = 0; a < kh; ++a) {
                 list[a] = st->hd_idx[i * kh + a];
                 ld2[a] = st->hd_d2[i * kh + a];
@@ -864,7 +864,7 @@ void oracle_insert(oracle_state *st, int64_t n_old, double bisect_tol, int bisec
         for (int a = 0; a < m; ++a) st->ld_idx[i * kl + a] = st->hd_idx[i * kh + a];
         for (int l = m; l < kl; ++l) {
             uint32_t w[4];
-            draw4(st->seed, st->t, (uint32_t)i, STREAM_INSERT, (uint32_t)(256 + l), w);
+            draw4(st->seed, st->t, (uint32_t)i, STREAM_INSERT, (uint32_t)(0x40000000 + l), w);
             int64_t o = map_index(w[0], n_old);
             for (;;) {
                 if (!contains(st->ld_idx + i * kl, l, o)) break;

@@ -87,7 +87,7 @@ def _declare(L):
     L.oracle_bruteforce_knn.restype = None
     L.oracle_query_knn.argtypes = [_dp, C.c_int64, C.c_int, _lp, C.c_int64, C.c_int, _ip, _dp]
     L.oracle_query_knn.restype = None
-    L.oracle_insert.argtypes = [sp, C.c_int64, C.c_double, C.c_int]
+    L.oracle_insert.argtypes = [sp, C.c_int64, C.c_int, C.c_double, C.c_int]
     L.oracle_insert.restype = None
     L.oracle_forces_points.argtypes = [sp, C.c_uint32, C.c_uint32, C.c_double, _lp, C.c_int64, _dp, _dp]
     L.oracle_forces_points.restype = None
@@ -359,8 +359,9 @@ class OracleState:
                           _p(flags, _bp), _p(info, _lp), _p(z, _dp))
         return dict(A=A, R=R, flags=flags, coin=bool(info[0]), n_new=int(info[1]), z=z)
 
-    def insert(self, X_new, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
-        """Append the rows of X_new (mean placement). Returns the first new index."""
+    def insert(self, X_new, rounds=16, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
+        """Append the rows of X_new (mean placement) after `rounds`
+        neighbour-of-neighbour rounds. Returns the first new index."""
         X_new = _f64(X_new)
         n_old, n_new = self.N, X_new.shape[0]
         N = n_old + n_new
@@ -376,7 +377,7 @@ class OracleState:
         self.N = N
         self._s.N = N
         self._bind()
-        lib().oracle_insert(C.byref(self._s), n_old, float(tol), int(maxit))
+        lib().oracle_insert(C.byref(self._s), n_old, int(rounds), float(tol), int(maxit))
         return n_old
 
     def dense_p(self):

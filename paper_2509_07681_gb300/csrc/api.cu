@@ -53,6 +53,7 @@ struct funcsne {
     bool concurrent = false;  // run the two refinements side by side in the graph
     int32_t forces_cw = 8;    // floats of an LD row per lane in the forces kernel
     int32_t hd_lanes_opt = 0; // lanes per gathered HD row (0: chosen from the row bytes)
+    int32_t insert_rounds = 16; // neighbour-of-neighbour rounds of an insertion
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     int hd_blocks = 0, ld_blocks = 0, fo_blocks = 0, update_blocks = 0;
@@ -731,6 +732,10 @@ int funcsne_set_option(funcsne_t* h, const char* key, double v) {
         if (v != 4 && v != 8 && v != 16) return fail(h, FUNCSNE_E_ARG, "forces_cw must be 4, 8 or 16");
         h->forces_cw = static_cast<int32_t>(v);
         configure_step(h);
+    } else if (k == "insert_rounds") {
+        if (v < 0 || v > 64 || v != static_cast<int>(v))
+            return fail(h, FUNCSNE_E_ARG, "insert_rounds must be an integer in [0, 64]");
+        h->insert_rounds = static_cast<int32_t>(v);
     } else if (k == "hd_lanes") {
         if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8)
             return fail(h, FUNCSNE_E_ARG, "hd_lanes must be 0, 1, 2, 4 or 8");
@@ -785,6 +790,7 @@ int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
     else if (k == "concurrent") *v = h->concurrent ? 1 : 0;
     else if (k == "forces_cw") *v = h->forces_cw;
     else if (k == "hd_lanes") *v = hd_lanes(h);
+    else if (k == "insert_rounds") *v = h->insert_rounds;
     else if (k == "surrogate") *v = h->surrogate ? 1 : 0;
     else if (k == "mlp_every") *v = h->mlp_every;
     else if (k == "mlp_lr") *v = h->mlp_lr;
@@ -967,6 +973,7 @@ int funcsne_insert(funcsne_t* h, const float* X_new, int64_t n_new, int32_t plac
     q.k_ld = h->k_ld;
     q.n4 = h->n4;
     q.g = hd_lanes_f32(h);
+    q.rounds = h->insert_rounds;
     q.xpitch = h->xpitch;
     q.log_perp = std::log(h->perplexity);
     q.t = s.t;

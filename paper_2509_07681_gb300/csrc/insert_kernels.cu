@@ -17,7 +17,6 @@
 
 namespace fsne {
 
-constexpr int kInsertRounds = 4;
 constexpr int kInsertNnSlots = 24;
 
 __global__ void insert_lists_kernel(InsertParams q) {
@@ -64,7 +63,7 @@ __global__ void __launch_bounds__(256) insert_refine_kernel(InsertParams q) {
     }
     warp_sort<RH>(key, lane);
     const uint32_t m = static_cast<uint32_t>(q.n_old);
-    for (int round = 0; round < kInsertRounds; ++round) {
+    for (int round = 0; round < q.rounds; ++round) {
         uint32_t li[RH];
 #pragma unroll
         for (int r = 0; r < RH; ++r) li[r] = key_idx(key[r]);
@@ -127,7 +126,7 @@ __global__ void __launch_bounds__(256) insert_refine_kernel(InsertParams q) {
         const int mcopy = kl < k ? kl : k;
         for (int l = 0; l < mcopy; ++l) q.ld_idx[gi * kl + l] = s_list[l];
         for (int l = mcopy; l < kl; ++l) {
-            const uint4 w = philox(q.t, i, kStreamInsert, static_cast<uint32_t>(256 + l), q.seed);
+            const uint4 w = philox(q.t, i, kStreamInsert, 0x40000000u + static_cast<uint32_t>(l), q.seed);
             uint32_t o = map_index(w.x, m);
             for (;;) {
                 bool taken = false;

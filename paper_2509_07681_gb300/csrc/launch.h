@@ -50,6 +50,7 @@ struct InsertParams {
     int64_t N, n_old;
     int32_t k_hd, k_ld, n4, xpitch;
     int32_t g;         // lanes per FP32 row (the iteration's grouping)
+    int32_t rounds;    // neighbour-of-neighbour rounds (slots 64 + 32 r + s)
     float log_perp;
     uint32_t t;
     uint64_t seed;

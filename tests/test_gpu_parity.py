@@ -219,18 +219,21 @@ def test_whole_run_blobs_recall_and_structure():
     assert math.isfinite(s["Zhat"]) and s["error_word"] == 0
 
 
-def test_insertion_matches_oracle():
+@pytest.mark.parametrize("rounds", [16, 0, 5])
+def test_insertion_matches_oracle(rounds):
     """funcsne_insert (mean placement) against the oracle from the same state:
     the new points' HD/LD lists, positions and bandwidths, the scalars, and
-    the next iteration over the grown state."""
+    the next iteration over the grown state; with the default 16, no, and 5
+    neighbour-of-neighbour rounds."""
     X = synth.blobs(n=2600, dim=30, n_clusters=6, seed=15)
     p = dict(d=2, k_hd=16, k_ld=8, n_neg=8, alpha=1.0, perplexity=8.0)
     m = _make(X[:2000], p, hd_mode=1)
+    m.set_option("insert_rounds", rounds)
     m.step(30)
     st = m.export_state()
     o = oracle_from_state(X[:2000], st, p, hd_mode=1)
     first = m.insert(X[2000:])
-    o.insert(X[2000:])
+    o.insert(X[2000:], rounds=rounds)
     assert first == 2000 and m.N == 2600
     st1 = m.export_state()
     new = range(2000, 2600)

@@ -355,7 +355,7 @@ def test_insertion_lists_placement_and_scalars():
         assert abs(st.P[i].sum() - 1) < 1e-9
     assert abs(st.Zhat - z0 * (700 * 699) / (600 * 599)) <= 1e-12 * st.Zhat
     assert st.E == max(e0, 100 / 700)
-    # four neighbour-of-neighbour rounds from a random start already find a
+    # the default 16 neighbour-of-neighbour rounds from a random start find a
     # large share of the exact neighbours among the existing points (random
     # lists would find about 16/600 of them); later iterations refine the rest
     ex, _ = O.bruteforce_knn(X[:600], 16)
@@ -367,6 +367,40 @@ def test_insertion_lists_placement_and_scalars():
     # the state keeps stepping
     out = st.step()
     assert np.isfinite(st.Y).all() and out["A"].shape == (700, 2)
+
+
+def test_insertion_rounds():
+    """Zero rounds keep the k_hd random starting points (ordered); each
+    round is a greedy top-k merge, so the k-th distance never grows with
+    more rounds on the same draws, and many rounds reach the exact
+    neighbours of well-separated data."""
+    X = synth.blobs(n=900, dim=10, n_clusters=4, seed=17)
+    base = O.OracleState(X[:800], 2, 12, 6, 6, 1.0, 6.0, seed=17)
+    for _ in range(20):
+        base.step()
+    new = np.arange(800, 900)
+    kth, rec = [], []
+    exact = np.array([np.lexsort((np.arange(800), ((X[:800].astype(np.float64) - X[i]) ** 2).sum(1)))[:12]
+                      for i in new])
+    for rounds in (0, 1, 4, 24):
+        st = base.copy()
+        st.insert(X[800:], rounds=rounds)
+        if rounds == 0:
+            for i in new:
+                w = [O.philox([st.t, i, 5, l], [17, 0])[0] for l in range(12)]
+                offs = []
+                for u in w:
+                    o = (int(u) * 800) >> 32
+                    while o in offs:
+                        o = (o + 1) % 800
+                    offs.append(o)
+                assert set(st.hd_idx[i].tolist()) == set(offs)
+        d2 = np.array([((st.X[st.hd_idx[i]] - st.X[i]) ** 2).sum(1).max() for i in new])
+        kth.append(d2)
+        rec.append(recall(st.hd_idx[new], exact))
+    for a, b in zip(kth, kth[1:]):
+        assert np.all(b <= a + 1e-12)
+    assert rec[0] < 0.1 and rec[-1] > 0.9 and rec[-1] >= rec[2] >= rec[1]
 
 
 def test_insertion_with_more_ld_than_hd_neighbours():
