@@ -249,6 +249,43 @@ __device__ __forceinline__ float group_sum(float v) {
 }
 
 // ------------------------------------------------------------------ LD refinement
+// Squared LD distances from y_i to row cv of Y for the candidate of every
+// lane (0 where cv == kNoRow), rows read by groups of G lanes: lane l holds
+// the CW = DP / G components CW (l mod G) ... of y_i in yi. All lanes call it.
+template <int DP, int G>
+__device__ __forceinline__ float group_ld_dist(const float (&yi)[DP / G], const float* __restrict__ Y,
+                                               uint32_t cv, int lane) {
+    constexpr int CW = DP / G, R = 32 / G;
+    const int g = lane / G, s = lane % G;
+    float mine = 0.f;
+#pragma unroll
+    for (int p = 0; p < G; ++p) {
+        const uint32_t cj = __shfl_sync(kFull, cv, p * R + g);
+        float v[CW];
+        if (cj != kNoRow) {
+            load_chunk<CW>(Y + static_cast<int64_t>(cj) * DP + CW * s, v);
+        } else {
+#pragma unroll
+            for (int c = 0; c < CW; ++c) v[c] = yi[c];
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+            const float d = __fsub_rn(yi[c], v[c]);
+            acc = __fmaf_rn(d, d, acc);
+        }
+        acc = group_sum<G>(acc);
+        const float val = __shfl_sync(kFull, acc, (lane % R) * G);
+        if (lane / R == p) mine = val;
+    }
+    return mine;
+}
+
+// Lanes per LD row in the LD refinement: rows of 32 bytes and more are read
+// two lanes per row (both 16-byte halves of a 32-byte sector in one request).
+template <int DP>
+__host__ __device__ constexpr int ld_lanes() { return DP >= 8 ? 2 : 1; }
+
 template <int DP, int RH>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
 ld_refine_kernel(const StepParams p) {
@@ -274,8 +311,9 @@ ld_refine_kernel(const StepParams p) {
             hidx[r] = e < k_hd ? static_cast<uint32_t>(__ldg(L.hd_idx_c + gi * k_hd + e)) : 0xffffffffu;
         }
         const uint32_t lidx = lane < k_ld ? static_cast<uint32_t>(__ldg(L.ld_idx_c + gi * k_ld + lane)) : 0xffffffffu;
-        float yi[DP];
-        load_row<DP>(Y + gi * DP, yi);
+        constexpr int GL = ld_lanes<DP>();
+        float yi[DP / GL];
+        load_chunk<DP / GL>(Y + gi * DP + (DP / GL) * (lane % GL), yi);
         const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
         hset_clear(tab, lane);
         __syncwarp();
@@ -293,18 +331,10 @@ ld_refine_kernel(const StepParams p) {
         __syncwarp();
         bool valid = (c != i) && (c < N) && !hset_has(tab, c);
         valid &= (__match_any_sync(kFull, c) & ((1u << lane) - 1u)) == 0u;
-        uint64_t lk[1] = {kSentinel};
-        uint64_t ck = kSentinel;
-        if (lane < k_ld) {
-            float yo[DP];
-            load_row<DP>(Y + static_cast<int64_t>(lidx) * DP, yo);
-            lk[0] = make_key(sqdist_ld<DP>(yi, yo), lidx);
-        }
-        if (valid) {
-            float yc[DP];
-            load_row<DP>(Y + static_cast<int64_t>(c) * DP, yc);
-            ck = make_key(sqdist_ld<DP>(yi, yc), c);
-        }
+        const float d_old = group_ld_dist<DP, GL>(yi, Y, lane < k_ld ? lidx : kNoRow, lane);
+        const float d_c = group_ld_dist<DP, GL>(yi, Y, valid ? c : kNoRow, lane);
+        uint64_t lk[1] = {lane < k_ld ? make_key(d_old, lidx) : kSentinel};
+        const uint64_t ck = valid ? make_key(d_c, c) : kSentinel;
         // the old list ordered under the distances at Y_t, then the candidates
         warp_sort<1>(lk, lane);
         const uint64_t thr = shfl64(lk[0], k_ld - 1);
