@@ -348,6 +348,42 @@ ld_refine_kernel(const StepParams p) {
     }
 }
 
+// Reduce-scatter of V-element vectors over the lanes that share lane mod G
+// (xor partners at distances 16, 8, ..., G): while a lane holds more than one
+// element it keeps half and sends half (recursive halving), later stages add
+// single elements. Afterwards v[0 .. C) holds elements [base, base + C) of
+// the sum, C = scatter_count<V, G>(); `owner` is false on the lanes that hold
+// a copy of another lane's elements.
+template <int V, int G>
+__host__ __device__ constexpr int scatter_count() {
+    int c = V;
+    for (int m = 16; m >= G; m >>= 1)
+        if (c > 1) c >>= 1;
+    return c;
+}
+
+template <int V, int C, int M, int G>
+__device__ __forceinline__ void reduce_scatter_stages(float (&v)[V], int lane, int& base, bool& owner) {
+    if constexpr (M >= G && M >= 1) {
+        if constexpr (C > 1) {
+            constexpr int H = C / 2;
+            const bool up = (lane & M) != 0;
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                const float send = up ? v[k] : v[k + H];
+                const float keep = up ? v[k + H] : v[k];
+                v[k] = keep + __shfl_xor_sync(kFull, send, M);
+            }
+            if (up) base += H;
+            reduce_scatter_stages<V, H, M / 2, G>(v, lane, base, owner);
+        } else {
+            v[0] += __shfl_xor_sync(kFull, v[0], M);
+            if (lane & M) owner = false;
+            reduce_scatter_stages<V, 1, M / 2, G>(v, lane, base, owner);
+        }
+    }
+}
+
 template <int DP>
 constexpr int forces_min_blocks() { return 4; }
 
@@ -477,23 +513,28 @@ forces_kernel(const StepParams p) {
             for (int c = 0; c < CW; ++c) rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
             if (lane % G == 0) z = __fmaf_rn(p.neg_scale, w, z);
         }
-        // sum over the row groups; lanes 0..G-1 then hold A_i and R_i
+        // sum over the row groups, scattered: each lane ends with C elements
+        // of (A_i, R_i) restricted to its components, which it adds to A_i
+        // (the reverse attraction of other points lands there too) or stores
+        // into R_i
+        constexpr int V = 2 * CW;
+        float v[V];
 #pragma unroll
-        for (int m = G; m < 32; m <<= 1)
+        for (int c = 0; c < CW; ++c) {
+            v[c] = att[c];
+            v[CW + c] = rep[c];
+        }
+        int base = 0;
+        bool owner = true;
+        reduce_scatter_stages<V, V, 16, G>(v, lane, base, owner);
+        if (owner) {
 #pragma unroll
-            for (int c = 0; c < CW; ++c) {
-                att[c] += __shfl_xor_sync(kFull, att[c], m);
-                rep[c] += __shfl_xor_sync(kFull, rep[c], m);
-            }
-        if (lane < G) {
-            atomic_add_chunk<CW>(p.A + gi * DP + co, att, 1.f);
-            if constexpr (CW % 4 == 0) {
-#pragma unroll
-                for (int q = 0; q < CW / 4; ++q)
-                    reinterpret_cast<float4*>(p.R + gi * DP + co)[q] =
-                        make_float4(rep[4 * q], rep[4 * q + 1], rep[4 * q + 2], rep[4 * q + 3]);
-            } else {
-                *reinterpret_cast<float2*>(p.R + gi * DP + co) = make_float2(rep[0], rep[1]);
+            for (int q = 0; q < scatter_count<V, G>(); ++q) {
+                const int e = base + q;
+                if (e < CW)
+                    atomicAdd(p.A + gi * DP + co + e, v[q]);
+                else
+                    p.R[gi * DP + co + e - CW] = v[q];
             }
         }
         z = warp_sum(z);
