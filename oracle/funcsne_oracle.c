@@ -78,7 +78,8 @@ enum {
     STREAM_INIT_HD = 6,
     STREAM_INIT_LD = 7,
     STREAM_INIT_Y = 8,
-    STREAM_ZINIT = 9
+    STREAM_ZINIT = 9,
+    STREAM_REMOVE = 11  /* replacements for neighbours that were removed */
 };
 
 /* Builder constants (the paper gives none of these). */
@@ -1099,4 +1100,91 @@ void oracle_forces_points(const oracle_state *st, uint32_t t, uint32_t neg_strea
     }
     free(S);
     free(slot);
+}
+
+
+/*
+ * Recalibrate every point from its current HD list: list distances
+ * recomputed from X, the list reordered by (d2, idx), beta and P from a cold
+ * start at the state's perplexity (Eq. 1). Follows a change of perplexity or
+ * of rows of X (drift); the lists themselves are kept.
+ */
+void oracle_recalibrate(oracle_state *st, double bisect_tol, int bisect_maxit)
+{
+    int kh = st->k_hd;
+    for (int64_t i = 0; i < st->N; ++i) {
+        sort_hd_list(st, i);
+        oracle_bisect(st->hd_d2 + i * kh, kh, st->perplexity, 0.0, bisect_tol, bisect_maxit,
+                      st->beta + i, st->P + i * kh);
+    }
+}
+
+/* Replace the entries -1 of list row `row` (k entries, point n of N): slot e
+ * draws j = map_other(w0, N, n) from counter (t, n, REMOVE, salt + e) and
+ * steps to j + 1 (mod N, skipping n) while j is already in the row. */
+static void fill_removed(oracle_state *st, int32_t *row, int k, int64_t n, int64_t N, uint32_t salt)
+{
+    for (int e = 0; e < k; ++e) {
+        if (row[e] >= 0) continue;
+        uint32_t w[4];
+        draw4(st->seed, st->t, (uint32_t)n, STREAM_REMOVE, salt + (uint32_t)e, w);
+        int64_t j = map_other(w[0], N, n);
+        for (;;) {
+            int taken = 0;
+            for (int a = 0; a < k; ++a)
+                if (row[a] == j) taken = 1;
+            if (!taken) break;
+            j = (j + 1) % N;
+            if (j == n) j = (j + 1) % N;
+        }
+        row[e] = (int32_t)j;
+    }
+}
+
+/*
+ * Remove the points flagged in `removed` (N entries). The state's X must
+ * already hold the kept rows, compacted in their original order; every
+ * other array is compacted here in place, and st->N becomes the kept count
+ * N'. Kept point o gets index n = its rank among the kept points. In every
+ * kept point's HD and LD list, entries that point to a kept point are
+ * renumbered, entries that pointed to a removed point are replaced by
+ * fill_removed (HD slots salt 0, LD slots salt 1024). Then HD distances,
+ * order, beta and P are recomputed for every point (oracle_recalibrate), A
+ * and V of kept points are kept, Zhat is scaled by the ratio of ordered pair
+ * counts and E = max(E, n_removed / N). Returns N'.
+ */
+int64_t oracle_remove(oracle_state *st, const uint8_t *removed, double bisect_tol, int bisect_maxit)
+{
+    int64_t N = st->N, Nk = 0;
+    int d = st->d, kh = st->k_hd, kl = st->k_ld;
+    int64_t *map = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    for (int64_t o = 0; o < N; ++o) map[o] = removed[o] ? -1 : Nk++;
+    for (int64_t o = 0; o < N; ++o) {
+        int64_t n = map[o];
+        if (n < 0) continue;
+        for (int c = 0; c < d; ++c) {
+            st->Y[n * d + c] = st->Y[o * d + c];
+            st->V[n * d + c] = st->V[o * d + c];
+        }
+        st->beta[n] = st->beta[o];
+        for (int e = 0; e < kh; ++e) {
+            int32_t j = st->hd_idx[o * kh + e];
+            st->hd_idx[n * kh + e] = (int32_t)map[j];
+        }
+        for (int e = 0; e < kl; ++e) {
+            int32_t j = st->ld_idx[o * kl + e];
+            st->ld_idx[n * kl + e] = (int32_t)map[j];
+        }
+    }
+    for (int64_t n = 0; n < Nk; ++n) {
+        fill_removed(st, st->hd_idx + n * kh, kh, n, Nk, 0u);
+        fill_removed(st, st->ld_idx + n * kl, kl, n, Nk, 1024u);
+    }
+    double nr = (double)(N - Nk);
+    st->Zhat *= ((double)Nk * (double)(Nk - 1)) / ((double)N * (double)(N - 1));
+    if (nr / (double)N > st->E) st->E = nr / (double)N;
+    st->N = Nk;
+    oracle_recalibrate(st, bisect_tol, bisect_maxit);
+    free(map);
+    return Nk;
 }

@@ -89,6 +89,10 @@ def _declare(L):
     L.oracle_query_knn.restype = None
     L.oracle_insert.argtypes = [sp, C.c_int64, C.c_int, C.c_double, C.c_int]
     L.oracle_insert.restype = None
+    L.oracle_recalibrate.argtypes = [sp, C.c_double, C.c_int]
+    L.oracle_recalibrate.restype = None
+    L.oracle_remove.argtypes = [sp, _bp, C.c_double, C.c_int]
+    L.oracle_remove.restype = C.c_int64
     L.oracle_forces_points.argtypes = [sp, C.c_uint32, C.c_uint32, C.c_double, _lp, C.c_int64, _dp, _dp]
     L.oracle_forces_points.restype = None
     L.oracle_bf16.argtypes = [C.c_double]
@@ -379,6 +383,32 @@ class OracleState:
         self._bind()
         lib().oracle_insert(C.byref(self._s), n_old, int(rounds), float(tol), int(maxit))
         return n_old
+
+    def set_perplexity(self, perplexity, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
+        """Change the perplexity and recalibrate every point from its list."""
+        self._s.perplexity = float(perplexity)
+        lib().oracle_recalibrate(C.byref(self._s), float(tol), int(maxit))
+
+    def update_rows(self, ids, X_rows, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
+        """Replace rows of X (drift), then recalibrate every point."""
+        self.X[np.asarray(ids, dtype=np.int64)] = _f64(X_rows)
+        lib().oracle_recalibrate(C.byref(self._s), float(tol), int(maxit))
+
+    def remove(self, ids, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
+        """Remove the points `ids`; the kept points are renumbered in order.
+        Returns the number of points left."""
+        removed = np.zeros(self.N, dtype=np.uint8)
+        removed[np.asarray(ids, dtype=np.int64)] = 1
+        keep = removed == 0
+        self.X = np.ascontiguousarray(self.X[keep])
+        self._bind()
+        n = lib().oracle_remove(C.byref(self._s), _p(removed, _bp), float(tol), int(maxit))
+        for name in ("Y", "V", "hd_idx", "hd_d2", "ld_idx", "beta", "P"):
+            setattr(self, name, np.ascontiguousarray(getattr(self, name)[:n]))
+        self.N = int(n)
+        self._s.N = int(n)
+        self._bind()
+        return int(n)
 
     def dense_p(self):
         Pd = np.zeros((self.N, self.N))

@@ -413,6 +413,89 @@ def test_insertion_with_more_ld_than_hd_neighbours():
         assert row[:8].tolist() == st.hd_idx[i].tolist()
 
 
+# ---------------------------------------------------------------- live changes
+def test_perplexity_change_recalibrates_every_point():
+    X = synth.blobs(n=400, dim=8, n_clusters=4, seed=40)
+    st = O.OracleState(X, 2, 16, 8, 8, 1.0, 6.0, seed=40)
+    for _ in range(10):
+        st.step()
+    sets = [set(r.tolist()) for r in st.hd_idx]
+    st.set_perplexity(11.0)
+    for i in range(400):
+        assert set(st.hd_idx[i].tolist()) == sets[i]
+        P = st.P[i]
+        assert abs(P.sum() - 1) < 1e-12
+        H = -np.sum(P[P > 0] * np.log(P[P > 0]))
+        assert abs(H - np.log(11.0)) < 1e-8
+        # P follows Eq. 1 with the point's beta over the shifted distances
+        d2 = st.hd_d2[i]
+        q = np.exp(-st.beta[i] * (d2 - d2[0]))
+        np.testing.assert_allclose(P, q / q.sum(), rtol=1e-12, atol=1e-15)
+
+
+def test_drifted_rows_refresh_list_distances():
+    X = synth.blobs(n=300, dim=6, n_clusters=3, seed=41)
+    st = O.OracleState(X, 2, 12, 6, 6, 1.0, 5.0, seed=41)
+    for _ in range(8):
+        st.step()
+    ids = np.array([3, 77, 150])
+    rows = X[ids] + 2.5
+    st.update_rows(ids, rows)
+    X2 = X.astype(np.float64).copy()
+    X2[ids] = rows
+    for i in range(300):
+        d2 = ((X2[st.hd_idx[i]] - X2[i]) ** 2).sum(1)
+        np.testing.assert_allclose(st.hd_d2[i], d2, rtol=1e-14)
+        assert np.all(np.diff(d2) >= 0)
+        assert abs(st.P[i].sum() - 1) < 1e-12
+
+
+def test_removal_renumbers_replaces_and_recalibrates():
+    X = synth.blobs(n=500, dim=8, n_clusters=4, seed=42)
+    st = O.OracleState(X, 2, 12, 8, 6, 1.0, 6.0, seed=42)
+    for _ in range(10):
+        st.step()
+    before = st.copy()
+    ids = np.array([0, 5, 17, 250, 499])
+    keep = np.setdiff1d(np.arange(500), ids)
+    new_of = -np.ones(500, dtype=np.int64)
+    new_of[keep] = np.arange(len(keep))
+    z0, e0 = st.Zhat, st.E
+    n = st.remove(ids)
+    assert n == 495 and st.N == 495 and st.X.shape == (495, 8)
+    np.testing.assert_array_equal(st.X, X[keep].astype(np.float64))
+    np.testing.assert_array_equal(st.Y, before.Y[keep])
+    np.testing.assert_array_equal(st.V, before.V[keep])
+    assert abs(st.Zhat - z0 * (495 * 494) / (500 * 499)) <= 1e-12 * z0
+    assert st.E == max(e0, 5 / 500)
+    for n_i, o_i in enumerate(keep):
+        for lst_new, lst_old, k, salt in ((st.hd_idx, before.hd_idx, 12, 0), (st.ld_idx, before.ld_idx, 8, 1024)):
+            row = lst_new[n_i]
+            assert len(set(row.tolist())) == k and row.min() >= 0 and row.max() < 495 and n_i not in row
+            kept_old = [new_of[j] for j in lst_old[o_i] if new_of[j] >= 0]
+            assert set(kept_old) <= set(row.tolist())
+        # the replacement rule, re-derived for the LD list (its order is kept)
+        old = before.ld_idx[o_i]
+        row = [int(new_of[j]) for j in old]
+        for e in range(8):
+            if row[e] >= 0:
+                continue
+            w = O.philox([st.t, n_i, 11, 1024 + e], [42, 0])[0]
+            j = (int(w) * 494) >> 32
+            j += j >= n_i
+            while j in row:
+                j = (j + 1) % 495
+                if j == n_i:
+                    j = (j + 1) % 495
+            row[e] = j
+        assert row == st.ld_idx[n_i].tolist()
+        d2 = ((st.X[st.hd_idx[n_i]] - st.X[n_i]) ** 2).sum(1)
+        np.testing.assert_allclose(st.hd_d2[n_i], d2, rtol=1e-14)
+        assert abs(st.P[n_i].sum() - 1) < 1e-12
+    st.step()
+    assert np.isfinite(st.Y).all()
+
+
 # ---------------------------------------------------------------- learned placement (MLP)
 def test_bf16_rounding_matches_torch():
     torch = pytest.importorskip("torch")
