@@ -138,6 +138,9 @@ int funcsne_create(const float *X, int64_t N, int32_t D, int32_t d, int32_t k_hd
  *                    (Section 3); 1: every iteration; 2: never
  *   "precision"      FUNCSNE_FP32 / FUNCSNE_BF16 / FUNCSNE_FP8 HD storage
  *   "alpha"          tail parameter (may change between steps)
+ *   "perplexity"     target perplexity in (1, k_hd + 1); a change recomputes
+ *                    every HD list's distances and order and recalibrates
+ *                    every beta and P from a cold start (Eq. 1)
  *   "concurrent"     1: the HD and LD refinements (which only read the state
  *                    of the iteration) run side by side (default 0)
  *   "forces_cw"      floats of an LD row each lane reads in the forces
@@ -196,6 +199,34 @@ int funcsne_sync(funcsne_t *h);
  */
 int funcsne_insert(funcsne_t *h, const float *X_new, int64_t n_new, int32_t placement,
                    int64_t *first_id);
+
+/*
+ * funcsne_update_points -- replace the HD rows of n existing points (drift;
+ * Section 3 lets the data change while the method runs). ids: n distinct
+ * point ids in [0, N) (host or device int64); X_rows: n x D FP32 (host or
+ * device), copied. Every point's HD list then has its distances recomputed,
+ * is reordered by (d2, idx), and its beta and P are recalibrated from a cold
+ * start (Eq. 1); the lists themselves, Y and V are kept, and later
+ * iterations refine the neighbourhoods. Errors: FUNCSNE_E_ARG (ids out of
+ * range or repeated), FUNCSNE_E_NAN (non-finite rows: nothing changes),
+ * FUNCSNE_E_OOM, FUNCSNE_E_CUDA.
+ */
+int funcsne_update_points(funcsne_t *h, const int64_t *ids, int64_t n, const float *X_rows);
+
+/*
+ * funcsne_remove -- remove n points (Section 3: points may leave while the
+ * method runs). ids: n distinct ids in [0, N) (host or device int64). The
+ * kept points keep their order and are renumbered 0 .. N - n - 1. In every
+ * HD and LD list, entries that pointed to a removed point are replaced, in
+ * slot order, by j = a uniform other point from Philox counter
+ * (t, i, 11, salt + slot) (salt 0 for HD, 1024 for LD), stepped to j + 1
+ * while already listed; then every HD list is re-scored, reordered and
+ * recalibrated as in funcsne_update_points. Zhat is scaled by the ratio of
+ * ordered pair counts and E becomes max(E, n / N). Capacity is kept.
+ * Errors: FUNCSNE_E_ARG (ids out of range or repeated, or fewer than
+ * max(k_hd, k_ld) + 1 points would remain), FUNCSNE_E_OOM, FUNCSNE_E_CUDA.
+ */
+int funcsne_remove(funcsne_t *h, const int64_t *ids, int64_t n);
 
 /*
  * Placement MLP (an addition to the method; the paper has no learned part):

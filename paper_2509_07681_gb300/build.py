@@ -11,8 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfuncsne.so")
-SOURCES = ["api.cu", "init_kernels.cu", "insert_kernels.cu", "knn_exact.cu", "knn_noalloc.cu", "mlp_kernels.cu",
-           "update_kernel.cu",
+SOURCES = ["api.cu", "init_kernels.cu", "insert_kernels.cu", "knn_exact.cu", "knn_noalloc.cu", "live_kernels.cu",
+           "mlp_kernels.cu", "update_kernel.cu",
            "step_f32.cu", "step_bf16.cu", "step_fp8.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

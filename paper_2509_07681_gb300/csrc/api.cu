@@ -8,6 +8,7 @@
 //   Y V A R  N x DP FP32 (element count rounded up to a multiple of 4)
 //   hd_idx[2] hd_d2[2]  N x k_hd ping-pong lists;  ld_idx[2]  N x k_ld
 //   P N x k_hd, beta N; DevScalars; per-block Z partials and counters.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -365,8 +366,9 @@ int quantize(funcsne* h) {
         h->nq = nw;
         h->qscale_off = h->qpitch - 4;
     }
-    FSNE_CUDA(h, dalloc(&h->Xq, static_cast<size_t>(h->N) * h->qpitch));
-    FSNE_CUDA(h, cudaMemsetAsync(h->Xq, 0, static_cast<size_t>(h->N) * h->qpitch, h->stream));
+    // sized for the capacity: insertions below it write rows N .. cap - 1
+    FSNE_CUDA(h, dalloc(&h->Xq, static_cast<size_t>(h->cap) * h->qpitch));
+    FSNE_CUDA(h, cudaMemsetAsync(h->Xq, 0, static_cast<size_t>(h->cap) * h->qpitch, h->stream));
     FSNE_CUDA(h, launch_quantize(h->X32, h->N, h->D, h->xpitch, h->precision, h->qpitch, h->qscale_off, h->Xq,
                                  h->stream));
     return FUNCSNE_OK;
@@ -699,6 +701,8 @@ int funcsne_create(const float* X, int64_t N, int32_t D, int32_t d, int32_t k_hd
     return FUNCSNE_OK;
 }
 
+int recalibrate(funcsne* h);
+
 int funcsne_set_option(funcsne_t* h, const char* key, double v) {
     if (!h || !key) return fail(h, FUNCSNE_E_ARG, "NULL handle or key");
     const std::string k(key);
@@ -732,6 +736,12 @@ int funcsne_set_option(funcsne_t* h, const char* key, double v) {
         if (v != 4 && v != 8 && v != 16) return fail(h, FUNCSNE_E_ARG, "forces_cw must be 4, 8 or 16");
         h->forces_cw = static_cast<int32_t>(v);
         configure_step(h);
+    } else if (k == "perplexity") {
+        if (!(v > 1) || !(v < h->k_hd + 1))
+            return fail(h, FUNCSNE_E_ARG, "perplexity must be in (1, k_hd + 1)");
+        h->perplexity = static_cast<float>(v);
+        drop_graphs(h);
+        return recalibrate(h);
     } else if (k == "insert_rounds") {
         if (v < 0 || v > 64 || v != static_cast<int>(v))
             return fail(h, FUNCSNE_E_ARG, "insert_rounds must be an integer in [0, 64]");
@@ -791,6 +801,7 @@ int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
     else if (k == "forces_cw") *v = h->forces_cw;
     else if (k == "hd_lanes") *v = hd_lanes(h);
     else if (k == "insert_rounds") *v = h->insert_rounds;
+    else if (k == "perplexity") *v = h->perplexity;
     else if (k == "surrogate") *v = h->surrogate ? 1 : 0;
     else if (k == "mlp_every") *v = h->mlp_every;
     else if (k == "mlp_lr") *v = h->mlp_lr;
@@ -1005,6 +1016,147 @@ int funcsne_insert(funcsne_t* h, const float* X_new, int64_t n_new, int32_t plac
     configure_step(h);
     *first_id = n_old;
     return FUNCSNE_OK;
+}
+
+// Every point's HD list distances recomputed from X32, its list reordered
+// by (d2, idx), beta and P calibrated from a cold start (Eq. 1).
+int recalibrate(funcsne* h) {
+    DevScalars s;
+    int rc = read_scalars(h, &s);
+    if (rc) return rc;
+    FinalizeParams f{};
+    f.N = h->N;
+    f.k_hd = h->k_hd;
+    f.n4 = h->n4;
+    f.g = hd_lanes_f32(h);
+    f.xpitch = h->xpitch;
+    f.log_perp = std::log(h->perplexity);
+    f.X32 = h->X32;
+    f.idx = h->hd_idx[s.hd_cur];
+    f.d2 = h->hd_d2[s.hd_cur];
+    f.P = h->P;
+    f.beta = h->beta;
+    f.Pin = nullptr;
+    FSNE_CUDA(h, launch_hd_finalize(f, 8 * h->num_sms, h->stream));
+    FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return FUNCSNE_OK;
+}
+
+// Host copy of n point ids (host or device memory), checked to be distinct
+// and in [0, N).
+int host_ids(funcsne* h, const int64_t* ids, int64_t n, std::vector<int64_t>& out) {
+    out.resize(static_cast<size_t>(n));
+    FSNE_CUDA(h, cudaMemcpy(out.data(), ids, static_cast<size_t>(n) * sizeof(int64_t), cudaMemcpyDefault));
+    std::vector<int64_t> s(out);
+    std::sort(s.begin(), s.end());
+    for (size_t a = 0; a < s.size(); ++a) {
+        if (s[a] < 0 || s[a] >= h->N) return fail(h, FUNCSNE_E_ARG, "point id %lld out of range", (long long)s[a]);
+        if (a && s[a] == s[a - 1]) return fail(h, FUNCSNE_E_ARG, "point id %lld repeated", (long long)s[a]);
+    }
+    return FUNCSNE_OK;
+}
+
+int funcsne_update_points(funcsne_t* h, const int64_t* ids, int64_t n, const float* X_rows) {
+    if (!h || !ids || !X_rows) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    if (n < 1) return fail(h, FUNCSNE_E_ARG, "n must be >= 1");
+    std::vector<int64_t> hid;
+    int rc = host_ids(h, ids, n, hid);
+    if (rc) return rc;
+    int64_t* did = nullptr;
+    float* drows = nullptr;
+    FSNE_CUDA(h, dalloc(&did, static_cast<size_t>(n)));
+    cudaError_t e = dalloc(&drows, static_cast<size_t>(n) * h->D);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(did, hid.data(), static_cast<size_t>(n) * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(drows, X_rows, static_cast<size_t>(n) * h->D * sizeof(float), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = launch_check_finite(drows, static_cast<int64_t>(n) * h->D, &h->sc->err, h->stream);
+    DevScalars chk{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&chk, h->sc, sizeof(chk), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && !(chk.err & kErrNonFinite))
+        e = launch_scatter_rows(h->X32, h->xpitch, did, drows, n, h->D, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(did);
+    cudaFree(drows);
+    FSNE_CUDA(h, e);
+    if (chk.err & kErrNonFinite) {
+        clear_error_word(h);
+        return fail(h, FUNCSNE_E_NAN, "X_rows holds non-finite values");
+    }
+    if (h->precision != FUNCSNE_FP32 && (rc = quantize(h))) return rc;
+    drop_graphs(h);
+    return recalibrate(h);
+}
+
+int funcsne_remove(funcsne_t* h, const int64_t* ids, int64_t n) {
+    if (!h || !ids) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    if (n < 1) return fail(h, FUNCSNE_E_ARG, "n must be >= 1");
+    std::vector<int64_t> hid;
+    int rc = host_ids(h, ids, n, hid);
+    if (rc) return rc;
+    const int64_t N = h->N, Nk = N - n;
+    if (Nk <= h->k_hd || Nk <= h->k_ld)
+        return fail(h, FUNCSNE_E_ARG, "removal would leave %lld points, at most k_hd or k_ld", (long long)Nk);
+    DevScalars s;
+    if ((rc = read_scalars(h, &s))) return rc;
+    std::vector<int32_t> new_of(static_cast<size_t>(N), 0), old_of;
+    for (int64_t id : hid) new_of[static_cast<size_t>(id)] = -1;
+    old_of.reserve(static_cast<size_t>(Nk));
+    for (int64_t o = 0; o < N; ++o)
+        if (new_of[static_cast<size_t>(o)] == 0) {
+            new_of[static_cast<size_t>(o)] = static_cast<int32_t>(old_of.size());
+            old_of.push_back(static_cast<int32_t>(o));
+        } else {
+            new_of[static_cast<size_t>(o)] = -1;
+        }
+    int32_t *d_new = nullptr, *d_old = nullptr;
+    uint32_t* tmp = nullptr;
+    const int64_t widest = std::max<int64_t>({h->xpitch, static_cast<int64_t>(h->DP), h->k_hd, h->k_ld});
+    FSNE_CUDA(h, dalloc(&d_new, static_cast<size_t>(N)));
+    cudaError_t e = dalloc(&d_old, static_cast<size_t>(Nk));
+    if (e == cudaSuccess) e = dalloc(&tmp, static_cast<size_t>(Nk * widest));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_new, new_of.data(), static_cast<size_t>(N) * 4, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_old, old_of.data(), static_cast<size_t>(Nk) * 4, cudaMemcpyHostToDevice, h->stream);
+    // compact the kept rows of each array, in order, through tmp
+    auto compact = [&](void* arr, int64_t pitch) {
+        if (e != cudaSuccess) return;
+        e = launch_gather_rows(tmp, static_cast<const uint32_t*>(arr), pitch, d_old, Nk, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(arr, tmp, static_cast<size_t>(Nk * pitch) * 4, cudaMemcpyDeviceToDevice, h->stream);
+    };
+    compact(h->X32, h->xpitch);
+    compact(h->Y, h->DP);
+    compact(h->V, h->DP);
+    compact(h->beta, 1);
+    compact(h->hd_idx[s.hd_cur], h->k_hd);
+    compact(h->ld_idx[s.ld_cur], h->k_ld);
+    if (e == cudaSuccess)
+        e = launch_remap_lists(h->hd_idx[s.hd_cur], h->k_hd, d_new, Nk, s.t, h->seed, 0u, h->stream);
+    if (e == cudaSuccess)
+        e = launch_remap_lists(h->ld_idx[s.ld_cur], h->k_ld, d_new, Nk, s.t, h->seed, 1024u, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d_new);
+    cudaFree(d_old);
+    cudaFree(tmp);
+    FSNE_CUDA(h, e);
+    h->N = Nk;
+    h->yelem = (Nk * h->DP + 3) / 4 * 4;
+    FSNE_CUDA(h, cudaMemsetAsync(h->Y + Nk * h->DP, 0, static_cast<size_t>(N - Nk) * h->DP * 4, h->stream));
+    FSNE_CUDA(h, cudaMemsetAsync(h->A, 0, static_cast<size_t>(h->cap) * h->DP * 4, h->stream));
+    if (h->precision != FUNCSNE_FP32 && (rc = quantize(h))) return rc;
+    // removed points count as points whose neighbourhood changed; Zhat
+    // follows the ordered pair count
+    s.Zhat *= (static_cast<double>(Nk) * static_cast<double>(Nk - 1)) /
+              (static_cast<double>(N) * static_cast<double>(N - 1));
+    const double frac = static_cast<double>(n) / static_cast<double>(N);
+    if (frac > s.E) s.E = frac;
+    FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->Zhat, &s.Zhat, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->E, &s.E, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    configure_step(h);
+    return recalibrate(h);
 }
 
 int funcsne_get_embedding(const funcsne_t* hc, float* Y_out, int64_t cap_rows) {

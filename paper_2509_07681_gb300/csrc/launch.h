@@ -90,6 +90,13 @@ cudaError_t launch_quantize(const float* X32, int64_t N, int D, int xpitch, int 
                             int scale_off, uint8_t* Q, cudaStream_t s);
 cudaError_t launch_check_lists(const int32_t* idx, int64_t N, int k, uint32_t* err, cudaStream_t s);
 cudaError_t launch_check_finite(const float* X, int64_t n, uint32_t* err, cudaStream_t s);
+// live changes of the point set (live_kernels.cu)
+cudaError_t launch_gather_rows(uint32_t* dst, const uint32_t* src, int64_t pitch, const int32_t* old,
+                               int64_t n_rows, cudaStream_t s);
+cudaError_t launch_scatter_rows(float* X32, int xpitch, const int64_t* ids, const float* rows, int64_t n, int D,
+                                cudaStream_t s);
+cudaError_t launch_remap_lists(int32_t* list, int k, const int32_t* new_of, int64_t N, uint32_t t, uint64_t seed,
+                               uint32_t salt, cudaStream_t s);
 cudaError_t launch_ld_distances(const float* Y, const int32_t* idx, int64_t N, int k, int DP, float* d2,
                                 cudaStream_t s);
 

@@ -19,6 +19,7 @@ constexpr uint32_t kStreamInitHd = 6;
 constexpr uint32_t kStreamInitLd = 7;
 constexpr uint32_t kStreamInitY = 8;
 constexpr uint32_t kStreamZinit = 9;
+constexpr uint32_t kStreamRemove = 11;  // replacements for removed neighbours
 
 // Candidate layout (32 per point and refinement; the paper names the
 // sources but not their counts).

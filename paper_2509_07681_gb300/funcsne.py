@@ -64,6 +64,8 @@ ABI_FUNCTIONS = {
     "funcsne_step": (C.c_int, [_h, C.c_int32]),
     "funcsne_sync": (C.c_int, [_h]),
     "funcsne_insert": (C.c_int, [_h, _vp, C.c_int64, C.c_int32, C.POINTER(C.c_int64)]),
+    "funcsne_update_points": (C.c_int, [_h, _vp, C.c_int64, _vp]),
+    "funcsne_remove": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_get_embedding": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_get_knn": (C.c_int, [_h, C.c_int32, _vp, _vp]),
     "funcsne_get_stats": (C.c_int, [_h, C.POINTER(Stats)]),
@@ -163,6 +165,17 @@ def funcsne_insert(h, X_new, placement=PLACE_MEAN):
     first = C.c_int64()
     _check(load().funcsne_insert(h, p, X_new.shape[0], placement, C.byref(first)), h)
     return first.value
+
+
+def funcsne_update_points(h, ids, X_rows):
+    pi, keep_i = _ptr(ids)
+    px, keep_x = _ptr(X_rows)
+    _check(load().funcsne_update_points(h, pi, ids.shape[0], px), h)
+
+
+def funcsne_remove(h, ids):
+    pi, keep_i = _ptr(ids)
+    _check(load().funcsne_remove(h, pi, ids.shape[0]), h)
 
 
 def funcsne_get_embedding(h, out):
@@ -377,6 +390,18 @@ class FuncSNE:
         first = funcsne_insert(self.h, X_new, placement)
         self.N += X_new.shape[0]
         return first
+
+    def update_points(self, ids, X_rows):
+        """Replace the HD rows of existing points (drift); every point is
+        then recalibrated from its list."""
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        funcsne_update_points(self.h, ids, _as_f32(X_rows))
+
+    def remove(self, ids):
+        """Remove points; the kept points are renumbered in order."""
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        funcsne_remove(self.h, ids)
+        self.N -= ids.shape[0]
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,0 +1,156 @@
+"""GPU parity of the live changes of the point set against the oracle, from
+the same exported state: a new perplexity, drifted rows of X, removed
+points (renumbering and replacement draws are integer work: bit-exact), and
+an iteration after each. Also insertions below a grown capacity after a
+change of storage precision."""
+import numpy as np
+import pytest
+
+from paper_2509_07681_gb300 import funcsne as F
+from paper_2509_07681_gb300 import synth
+
+from gpu_util import compare_sets, fp32_band, lib, oracle_from_state, rel_err_rows
+
+pytestmark = pytest.mark.gpu
+
+P = dict(d=2, k_hd=16, k_ld=8, n_neg=8, alpha=1.0, perplexity=8.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lib()
+
+
+def _run(X, steps=15, **opts):
+    m = F.FuncSNE(X, P["d"], P["k_hd"], P["k_ld"], P["n_neg"], P["alpha"], P["perplexity"], seed=0, hd_mode=1,
+                  **opts)
+    m.step(steps)
+    m.sync()
+    return m
+
+
+def _by_index(idx, vals):
+    o = np.argsort(idx, axis=1, kind="stable")
+    return np.take_along_axis(idx, o, 1), np.take_along_axis(vals, o, 1)
+
+
+def _check_calibration(st, o, rows):
+    """Same HD sets (the lists are kept), rows ordered by distance, beta and
+    P of the oracle (entries aligned by neighbour index)."""
+    for i in range(len(st["hd_idx"])):
+        assert set(st["hd_idx"][i].tolist()) == set(o.hd_idx[i].tolist())
+        d2 = ((rows[st["hd_idx"][i]] - rows[i]) ** 2).sum(1)
+        assert np.all(np.diff(d2) >= -fp32_band(rows.shape[1]) * d2[-1])
+    np.testing.assert_allclose(st["beta"], o.beta, rtol=5e-3)
+    gi, gp = _by_index(st["hd_idx"], st["P"])
+    oi, op = _by_index(o.hd_idx.astype(np.int32), o.P)
+    np.testing.assert_array_equal(gi, oi)
+    np.testing.assert_allclose(gp, op, atol=2e-4)
+
+
+def _one_more_iteration(m, X, st, hd_mode=1):
+    o = oracle_from_state(X, st, P, hd_mode=hd_mode)
+    att, rep = m.debug_step()
+    out = o.step()
+    st1 = m.export_state()
+    bad, amb = compare_sets(st1["hd_idx"], o.hd_idx, range(len(X)), o.X, fp32_band(X.shape[1]))
+    assert bad == 0 and amb <= 3
+    if amb == 0:
+        assert np.quantile(rel_err_rows(att.astype(np.float64), out["A"]), 0.99) < 1e-4
+
+
+def test_perplexity_change_matches_oracle():
+    X = synth.blobs(n=1500, dim=20, n_clusters=5, seed=50)
+    m = _run(X)
+    st = m.export_state()
+    o = oracle_from_state(X, st, P, hd_mode=1)
+    m.set_option("perplexity", 12.0)
+    assert m.get_option("perplexity") == 12.0
+    o.set_perplexity(12.0)
+    st1 = m.export_state()
+    _check_calibration(st1, o, X.astype(np.float64))
+    assert st1["Zhat"] == st["Zhat"] and st1["E"] == st["E"] and st1["t"] == st["t"]
+    with pytest.raises(F.FuncSNEError):
+        m.set_option("perplexity", 17.5)
+    m.close()
+
+
+def test_drifted_rows_match_oracle():
+    X = synth.blobs(n=1500, dim=20, n_clusters=5, seed=51)
+    m = _run(X, precision=F.BF16)
+    st = m.export_state()
+    o = oracle_from_state(X, st, P, hd_mode=1)
+    ids = np.array([4, 99, 700, 1499])
+    rows = X[ids][::-1] + 0.5
+    m.update_points(ids, rows)
+    o.update_rows(ids, rows)
+    X2 = X.copy()
+    X2[ids] = rows
+    st1 = m.export_state()
+    _check_calibration(st1, o, X2.astype(np.float64))
+    # the BF16 copy follows the new rows: one iteration equals FP32's
+    ref = m.export_state()
+    m.step(1)
+    b = m.export_state()
+    m.set_option("precision", F.FP32)
+    m.import_state(ref)
+    m.step(1)
+    a = m.export_state()
+    np.testing.assert_array_equal(a["hd_idx"], b["hd_idx"])
+    with pytest.raises(F.FuncSNEError):
+        m.update_points(np.array([3, 3]), X[:2])
+    with pytest.raises(F.FuncSNEError):
+        bad = X[:1].copy()
+        bad[0, 0] = np.nan
+        m.update_points(np.array([5]), bad)
+    m.close()
+
+
+@pytest.mark.parametrize("precision", [F.FP32, F.FP8])
+def test_removal_matches_oracle(precision):
+    X = synth.blobs(n=1600, dim=20, n_clusters=5, seed=52)
+    m = _run(X, precision=precision)
+    st = m.export_state()
+    o = oracle_from_state(X, st, P, hd_mode=1)
+    rng = np.random.default_rng(3)
+    ids = np.sort(rng.choice(1600, 100, replace=False))
+    ids = np.unique(np.concatenate([ids, [0, 1599]]))
+    keep = np.setdiff1d(np.arange(1600), ids)
+    m.remove(ids[::-1].copy())
+    n = o.remove(ids)
+    assert m.N == n == len(keep) and m.stats()["N"] == n
+    st1 = m.export_state()
+    # renumbering and replacement draws: bit-exact
+    np.testing.assert_array_equal(st1["ld_idx"], o.ld_idx)
+    np.testing.assert_array_equal(np.sort(st1["hd_idx"], 1), np.sort(o.hd_idx, 1))
+    np.testing.assert_array_equal(st1["Y"], st["Y"][keep])
+    np.testing.assert_array_equal(st1["V"], st["V"][keep])
+    assert abs(st1["Zhat"] - o.Zhat) <= 1e-12 * o.Zhat and st1["E"] == o.E
+    Xk = X[keep]
+    _check_calibration(st1, o, Xk.astype(np.float64))
+    _one_more_iteration(m, Xk, st1)
+    with pytest.raises(F.FuncSNEError):
+        m.remove(np.arange(m.N - 10))
+    m.close()
+
+
+def test_insertion_below_grown_capacity_after_precision_change():
+    """Capacity grows on the first insertion; the BF16 copy created after it
+    must cover the capacity, so the second insertion (no growth) fits."""
+    X = synth.blobs(n=2600, dim=24, n_clusters=6, seed=53)
+    m = _run(X[:2000])
+    m.insert(X[2000:2100])
+    m.set_option("precision", F.BF16)
+    m.insert(X[2100:2600])
+    m.step(5)
+    m.sync()
+    st = m.export_state()
+    assert m.N == 2600 and np.isfinite(st["Y"]).all()
+    m.step(1)
+    b = m.export_state()
+    m.set_option("precision", F.FP32)
+    m.import_state(st)
+    m.step(1)
+    a = m.export_state()
+    np.testing.assert_array_equal(a["hd_idx"], b["hd_idx"])
+    m.close()
