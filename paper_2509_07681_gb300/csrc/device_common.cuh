@@ -353,47 +353,6 @@ __device__ __forceinline__ ApproxDist finish_band(float acc, float s1, float s2,
     return r;
 }
 
-// BF16 rows: 8 values per 16-byte chunk, nq data chunks, then a 16-byte
-// chunk whose first four bytes hold an upper bound N_c of the row's norm.
-// The candidate's rounding error e satisfies |e_f| <= u |x~_f|, so
-// ||e|| <= u N_c = E and |d~2 - d2| <= 2 ||x_i - x~_c|| E + E^2 (Cauchy-
-// Schwarz), plus the FP32 rounding of both distance evaluations.
-__device__ __forceinline__ ApproxDist dist_bf16(const float* __restrict__ xs,
-                                                const uint16_t* __restrict__ xc, int nq, float u,
-                                                float gamma) {
-    const uint4* b = reinterpret_cast<const uint4*>(xc);
-    float acc = 0.f;
-#pragma unroll 2
-    for (int q = 0; q < nq; ++q) {
-        const uint4 raw = __ldg(b + q);
-        const float4 x0 = reinterpret_cast<const float4*>(xs)[2 * q];
-        const float4 x1 = reinterpret_cast<const float4*>(xs)[2 * q + 1];
-        float d = __fsub_rn(x0.x, __uint_as_float(raw.x << 16));
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(x0.y, __uint_as_float(raw.x & 0xffff0000u));
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(x0.z, __uint_as_float(raw.y << 16));
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(x0.w, __uint_as_float(raw.y & 0xffff0000u));
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(x1.x, __uint_as_float(raw.z << 16));
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(x1.y, __uint_as_float(raw.z & 0xffff0000u));
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(x1.z, __uint_as_float(raw.w << 16));
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(x1.w, __uint_as_float(raw.w & 0xffff0000u));
-        acc = __fmaf_rn(d, d, acc);
-    }
-    const float norm = __ldg(reinterpret_cast<const float*>(b + nq));
-    const float E = u * norm;
-    const float b0 = 2.f * sqrtf(acc * (1.f + gamma)) * E + E * E;
-    ApproxDist r;
-    r.d2 = acc;
-    r.band = b0 * (1.f + 4.f * gamma) + gamma * (2.f * acc + 2.f * b0) + 1e-30f;
-    return r;
-}
-
 // FP8-E4M3 rows with a per-row FP32 scale stored after the codes:
 // 16 codes per 16-byte chunk, x~ = code * scale.
 __device__ __forceinline__ void fp8x4_to_float(uint32_t w, float s, float (&o)[4]) {
@@ -407,33 +366,6 @@ __device__ __forceinline__ void fp8x4_to_float(uint32_t w, float s, float (&o)[4
     o[3] = b.y * s;
 }
 
-__device__ __forceinline__ ApproxDist dist_fp8(const float* __restrict__ xs,
-                                               const uint8_t* __restrict__ xc, int nw,
-                                               int scale_off, float u, float a_rel, float gamma) {
-    // nw = ceil(D / 4) code words; the row's last 4 bytes hold the scale.
-    const float s = __ldg(reinterpret_cast<const float*>(xc + scale_off));
-    const float a = a_rel * s;
-    const uint4* b = reinterpret_cast<const uint4*>(xc);
-    float acc = 0.f, s1 = 0.f, s2 = 0.f;
-    const int nq = (nw + 3) >> 2;
-    for (int q = 0; q < nq; ++q) {
-        const uint4 raw = __ldg(b + q);
-        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            if (4 * q + m < nw) {
-                float v[4];
-                fp8x4_to_float(w4[m], s, v);
-                const float4 xi = reinterpret_cast<const float4*>(xs)[4 * q + m];
-                approx_acc(xi.x, v[0], u, a, acc, s1, s2);
-                approx_acc(xi.y, v[1], u, a, acc, s1, s2);
-                approx_acc(xi.z, v[2], u, a, acc, s1, s2);
-                approx_acc(xi.w, v[3], u, a, acc, s1, s2);
-            }
-        }
-    }
-    return finish_band(acc, s1, s2, gamma);
-}
 
 // ------------------------------------------------------- row-group distances
 // A warp scores the candidates of its 32 lanes (lane l owns candidate l) by
@@ -492,6 +424,25 @@ __device__ __forceinline__ float group_dist_f32(const float* __restrict__ xs, co
     return mine;
 }
 
+// Position of the set bit of rank k (0-based, from bit 0) of m; m must have
+// more than k set bits. Binary search on prefix population counts.
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const uint32_t low = m & ((1u << w) - 1u);  // bits [pos, pos + w) of the window
+        const int c = __popc(low);
+        if (c <= k) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = low;
+        }
+    }
+    return pos;
+}
+
 // The same FP32 distances (same grouping, hence the same bits) for only the
 // lanes with need == true, packed R to a pass. All lanes must call it.
 __device__ __forceinline__ float group_rerank_f32(const float* __restrict__ xs, const float* __restrict__ X32,
@@ -503,9 +454,7 @@ __device__ __forceinline__ float group_rerank_f32(const float* __restrict__ xs, 
     float mine = 0.f;
     for (int base = 0; base < nn; base += R) {
         const int k = base + g;  // this group scores the k-th flagged lane's row
-        uint32_t mk = m;
-        for (int j = 0; j < k && mk; ++j) mk &= mk - 1u;
-        const int src = (k < nn) ? (__ffs(static_cast<int>(mk)) - 1) : 0;
+        const int src = (k < nn) ? nth_set_bit(m, k) : 0;
         const uint32_t cj = __shfl_sync(kFull, c, src);
         float acc = 0.f;
         if (k < nn) acc = part_f32(xs, X32 + static_cast<int64_t>(cj) * xpitch, n4, s, G);
@@ -518,8 +467,12 @@ __device__ __forceinline__ float group_rerank_f32(const float* __restrict__ xs, 
     return mine;
 }
 
-// BF16 rows by groups: the distance to the dequantised row and the
-// Cauchy-Schwarz band of dist_bf16, for the candidate of every lane.
+// BF16 rows by groups: the distance to the dequantised row and its band,
+// for the candidate of every lane. BF16 rows hold nq chunks of 8 values,
+// then a 16-byte chunk whose first four bytes hold an upper bound N_c of the
+// rounded row's norm. With |x_f - x~_f| <= u |x~_f|, ||e|| <= u N_c = E and
+// |d~2 - d2| <= 2 ||x_i - x~_c|| E + E^2 (Cauchy-Schwarz), plus the FP32
+// rounding of both distance evaluations.
 template <int G>
 __device__ __forceinline__ ApproxDist group_dist_bf16(const float* __restrict__ xs,
                                                       const uint8_t* __restrict__ Xq, int qpitch, int nq,
@@ -576,7 +529,8 @@ __device__ __forceinline__ ApproxDist group_dist_bf16(const float* __restrict__ 
 }
 
 // FP8-E4M3 rows by groups: distance to the dequantised row and the
-// element-wise band of dist_fp8, for the candidate of every lane.
+// element-wise band (see approx_acc and finish_band), for the candidate of
+// every lane.
 template <int G>
 __device__ __forceinline__ ApproxDist group_dist_fp8(const float* __restrict__ xs,
                                                      const uint8_t* __restrict__ Xq, int qpitch, int nw,
