@@ -551,6 +551,70 @@ def run_reference(args, rank, world):
     return line
 
 
+def run_feedback(args, rank, world):
+    """The feedback loop between the two neighbour searches (Section 3,
+    Fig. 4 and Fig. 7), measured on synthetic data:
+      * HD-KNN recall@k_hd (sampled queries against brute force) along the
+        iterations on the 70,000-point pixels workload, with Y optimised or
+        held at its random-projection start (learning rate 1e-12), for d = 2
+        and d = 8;
+      * HD-KNN recall after 3,000 and 9,000 iterations on 5 overlapping
+        blobs (N = 20,000, centres N(0, I)) and on 1,000 disjoint blobs of
+        30 points (centres N(0, 100 I)), D = 30, d = 2.
+    HD refinement runs every iteration."""
+    import torch
+    from paper_2509_07681_gb300 import funcsne as F
+    from paper_2509_07681_gb300 import synth
+    from paper_2509_07681_gb300.quality import recall
+
+    local, dist = _setup_gpu(world)
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(0)
+    out = {"fig4": {}, "fig7": {}}
+    X, p = synth.make("pixels-70k", n=args.n)
+    N = X.shape[0]
+    q = np.sort(rng.choice(N, min(2000, N), replace=False)).astype(np.int32)
+    checkpoints = [0, 10, 25, 50, 100, 200, 400, 700, 1000]
+    exact = None
+    for d in (2, 8):
+        for mode in ("optimised", "fixed"):
+            m = F.FuncSNE(X, d, p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0, hd_mode=1)
+            m.set_stream(stream)
+            if mode == "fixed":
+                m.set_option("lr", 1e-12)
+            if exact is None:
+                exact, _ = m.exact_knn(q, p["k_hd"])
+            curve, done = [], 0
+            for c in checkpoints:
+                m.step(c - done)
+                done = c
+                curve.append(round(recall(m.knn(F.SPACE_HD, with_d2=False)[q], exact), 4))
+            out["fig4"][f"d={d} {mode}"] = dict(zip(map(str, checkpoints), curve))
+            m.close()
+    sets = {"5 overlapping blobs": synth.blobs(n=20000, dim=30, n_clusters=5, centre_std=1.0, seed=7),
+            "1000 disjoint blobs x 30": synth.blobs(n=30000, dim=30, n_clusters=1000, centre_std=10.0, seed=8)}
+    for name, Xb in sets.items():
+        m = F.FuncSNE(Xb, 2, 32, 16, 16, 1.0, 30.0, seed=0, hd_mode=1)
+        m.set_stream(stream)
+        qb = np.sort(rng.choice(len(Xb), 2000, replace=False)).astype(np.int32)
+        ex, _ = m.exact_knn(qb, 32)
+        res = {}
+        done = 0
+        for c in (0, 3000, 9000):
+            m.step(c - done)
+            done = c
+            res[str(c)] = round(recall(m.knn(F.SPACE_HD, with_d2=False)[qb], ex), 4)
+        out["fig7"][name] = res
+        m.close()
+    if rank == 0:
+        print(json.dumps({"metric": "HD-KNN recall@k_hd along the iterations (feedback loop)", "data": "synthetic",
+                          "config": {"fig4": f"pixels-70k N={N}, k_hd={p['k_hd']}, {len(q)} sampled queries",
+                                     "fig7": "D=30, d=2, k_hd=32, k_ld=16, n_neg=16, perplexity 30"},
+                          "results": out}), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def run_profile_case(args):
     """A short, fixed sequence of launches for ncu: create the workload at N
     (default: the workload's own N), then for each precision `warmup` +
@@ -587,8 +651,9 @@ def parse_args(argv=None):
     ap.add_argument("--alpha", type=float, default=None, help="override the workload's alpha")
     ap.add_argument("--n", type=int, default=None, help="override N (default: the workload's own)")
     ap.add_argument("--cpu-sample", type=int, default=20000, help="points in the reference arm's oracle sample")
-    ap.add_argument("--mode", choices=["bench", "dynamic", "ncu"], default="bench",
-                    help="dynamic: insertion protocol; ncu: the short fixed launch sequence used for profiling")
+    ap.add_argument("--mode", choices=["bench", "dynamic", "feedback", "ncu"], default="bench",
+                    help="dynamic: insertion protocol; feedback: HD-KNN recall with optimised or fixed Y; "
+                         "ncu: the short fixed launch sequence used for profiling")
     ap.add_argument("--precisions", default="fp32,bf16,fp8", help="precisions of --mode ncu")
     ap.add_argument("--burn-in", type=int, default=0, help="untimed iterations first (0: the mode's default)")
     ap.add_argument("--insert-n", type=int, default=10000, help="--mode dynamic: points per insertion")
@@ -616,6 +681,8 @@ def main():
         run_reference(args, rank, world)
     elif args.mode == "dynamic":
         run_dynamic(args, rank, world)
+    elif args.mode == "feedback":
+        run_feedback(args, rank, world)
     else:
         run_ours(args, rank, world)
 

@@ -150,7 +150,8 @@ int funcsne_create(const float *X, int64_t N, int32_t D, int32_t d, int32_t k_hd
  *   "hd_lanes"       lanes that read one gathered HD row in the refinement:
  *                    1, 2, 4 or 8, or 0 (default) to choose from the row
  *                    bytes. A tuning knob; it fixes the FP32 summation order,
- *                    so results depend on it (bit for bit)
+ *                    so results depend on it (bit for bit). Read-only
+ *                    "hd_lanes_used" gives the lanes in use
  *   "surrogate"      1: train the placement MLP inside funcsne_step, one
  *                    step before every "mlp_every"-th iteration (default 0)
  *   "mlp_every"      iterations between training steps (default 10)
@@ -246,6 +247,11 @@ int funcsne_mlp_debug_step(funcsne_t *h, funcsne_mlp_debug_t *out);
 
 /* Copy the first min(N, cap_rows) rows of the N x d embedding into Y_out. */
 int funcsne_get_embedding(const funcsne_t *h, float *Y_out, int64_t cap_rows);
+
+/* Copy the first min(N, cap_rows) rows of the N x D HD data (FP32, as held
+ * after insertions, drift and removals) into X_out (host or device). With
+ * funcsne_export_state this is a complete checkpoint of the iteration. */
+int funcsne_get_data(const funcsne_t *h, float *X_out, int64_t cap_rows);
 
 /* Copy the current neighbour lists of `space` (FUNCSNE_SPACE_HD: N x k_hd,
  * FUNCSNE_SPACE_LD: N x k_ld) into idx and, when d2 is non-NULL, their

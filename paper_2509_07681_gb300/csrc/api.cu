@@ -799,7 +799,8 @@ int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
     else if (k == "precision") *v = h->precision;
     else if (k == "concurrent") *v = h->concurrent ? 1 : 0;
     else if (k == "forces_cw") *v = h->forces_cw;
-    else if (k == "hd_lanes") *v = hd_lanes(h);
+    else if (k == "hd_lanes") *v = h->hd_lanes_opt;
+    else if (k == "hd_lanes_used") *v = hd_lanes(h);
     else if (k == "insert_rounds") *v = h->insert_rounds;
     else if (k == "perplexity") *v = h->perplexity;
     else if (k == "surrogate") *v = h->surrogate ? 1 : 0;
@@ -1164,6 +1165,16 @@ int funcsne_get_embedding(const funcsne_t* hc, float* Y_out, int64_t cap_rows) {
     if (!h || !Y_out) return fail(h, FUNCSNE_E_ARG, "NULL argument");
     const int64_t rows = cap_rows < h->N ? cap_rows : h->N;
     int rc = copy_rows<float>(h, Y_out, h->d, h->Y, h->DP, rows, h->d);
+    if (rc) return rc;
+    FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return FUNCSNE_OK;
+}
+
+int funcsne_get_data(const funcsne_t* hc, float* X_out, int64_t cap_rows) {
+    funcsne* h = const_cast<funcsne*>(hc);
+    if (!h || !X_out) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    const int64_t rows = cap_rows < h->N ? cap_rows : h->N;
+    int rc = copy_rows<float>(h, X_out, h->D, h->X32, h->xpitch, rows, h->D);
     if (rc) return rc;
     FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
     return FUNCSNE_OK;

@@ -67,6 +67,7 @@ ABI_FUNCTIONS = {
     "funcsne_update_points": (C.c_int, [_h, _vp, C.c_int64, _vp]),
     "funcsne_remove": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_get_embedding": (C.c_int, [_h, _vp, C.c_int64]),
+    "funcsne_get_data": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_get_knn": (C.c_int, [_h, C.c_int32, _vp, _vp]),
     "funcsne_get_stats": (C.c_int, [_h, C.POINTER(Stats)]),
     "funcsne_export_state": (C.c_int, [_h, C.POINTER(State)]),
@@ -176,6 +177,12 @@ def funcsne_update_points(h, ids, X_rows):
 def funcsne_remove(h, ids):
     pi, keep_i = _ptr(ids)
     _check(load().funcsne_remove(h, pi, ids.shape[0]), h)
+
+
+def funcsne_get_data(h, out):
+    p, keep = _ptr(out)
+    _check(load().funcsne_get_data(h, p, out.shape[0]), h)
+    return out
 
 
 def funcsne_get_embedding(h, out):
@@ -297,6 +304,7 @@ class FuncSNE:
         X = _as_f32(X)
         self.N, self.D = X.shape
         self.d, self.k_hd, self.k_ld, self.n_neg = d, k_hd, k_ld, n_neg
+        self._alpha0, self._perplexity0, self._seed = alpha, perplexity, seed
         self.h = funcsne_create(X, d, k_hd, k_ld, n_neg, alpha, perplexity, seed)
         for k, v in options.items():
             self.set_option(k, v)
@@ -390,6 +398,47 @@ class FuncSNE:
         first = funcsne_insert(self.h, X_new, placement)
         self.N += X_new.shape[0]
         return first
+
+    def data(self, out=None):
+        """The N x D HD rows the handle holds."""
+        if out is None:
+            out = np.empty((self.N, self.D), dtype=np.float32)
+        return funcsne_get_data(self.h, out)
+
+    CHECKPOINT_OPTIONS = ("lr", "momentum", "att_ratio", "rep_ratio", "exaggeration", "exag_iters", "hd_mode",
+                          "precision", "alpha", "perplexity", "concurrent", "surrogate", "mlp_every", "mlp_lr",
+                          "mlp_batch", "mlp_hidden", "forces_cw", "hd_lanes", "insert_rounds")
+
+    def save(self, path):
+        """Checkpoint: HD rows, the exported iteration state, the creation
+        parameters, the seed and the options, in one .npz file. The placement
+        MLP's parameters are not part of it (it retrains online)."""
+        st = self.export_state()
+        opts = {k: self.get_option(k) for k in self.CHECKPOINT_OPTIONS}
+        np.savez(path, X=self.data(), **{k: v for k, v in st.items() if isinstance(v, np.ndarray)},
+                 Zhat=st["Zhat"], E=st["E"], t=st["t"],
+                 params=np.array([self.d, self.k_hd, self.k_ld, self.n_neg], dtype=np.int64),
+                 alpha0=self._alpha0, perplexity0=self._perplexity0, seed=np.uint64(self._seed),
+                 opt_keys=np.array(list(opts)), opt_vals=np.array(list(opts.values()), dtype=np.float64))
+
+    @classmethod
+    def load_checkpoint(cls, path):
+        """Recreate a handle from save(): same rows, state, seed and options;
+        the next iterations draw the same random numbers."""
+        z = np.load(path)
+        d, k_hd, k_ld, n_neg = (int(v) for v in z["params"])
+        m = cls(z["X"], d, k_hd, k_ld, n_neg, float(z["alpha0"]), float(z["perplexity0"]), seed=int(z["seed"]))
+        opts = dict(zip(z["opt_keys"].tolist(), z["opt_vals"].tolist()))
+        for k in ("precision", "hd_lanes", "forces_cw", "concurrent", "mlp_batch", "mlp_hidden"):
+            m.set_option(k, opts.pop(k))
+        perp = opts.pop("perplexity")
+        for k, v in opts.items():
+            m.set_option(k, v)
+        if perp != m.get_option("perplexity"):
+            m.set_option("perplexity", perp)
+        m.import_state({k: z[k] for k in ("Y", "V", "hd_idx", "ld_idx", "beta", "P")} |
+                       {"Zhat": float(z["Zhat"]), "E": float(z["E"]), "t": int(z["t"])})
+        return m
 
     def update_points(self, ids, X_rows):
         """Replace the HD rows of existing points (drift); every point is

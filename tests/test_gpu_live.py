@@ -154,3 +154,32 @@ def test_insertion_below_grown_capacity_after_precision_change():
     a = m.export_state()
     np.testing.assert_array_equal(a["hd_idx"], b["hd_idx"])
     m.close()
+
+
+def test_checkpoint_resume(tmp_path):
+    """save() / load_checkpoint(): the resumed handle's next iteration gives
+    the same lists as the original's (the lists do not depend on the order of
+    the force atomics) and nearly the same positions."""
+    X = synth.blobs(n=1800, dim=20, n_clusters=5, seed=54)
+    m = _run(X, precision=F.BF16)
+    m.set_option("momentum", 0.7)
+    m.remove(np.array([3, 4, 5]))
+    m.step(3)
+    m.sync()
+    path = str(tmp_path / "ckpt.npz")
+    m.save(path)
+    m2 = F.FuncSNE.load_checkpoint(path)
+    assert m2.N == m.N and m2.get_option("momentum") == 0.7 and m2.get_option("precision") == F.BF16
+    np.testing.assert_array_equal(m2.data(), m.data())
+    a, b = m.export_state(), m2.export_state()
+    for k in ("hd_idx", "ld_idx", "Y", "V"):
+        np.testing.assert_array_equal(a[k], b[k])
+    assert a["t"] == b["t"] and a["Zhat"] == b["Zhat"] and a["E"] == b["E"]
+    m.step(1)
+    m2.step(1)
+    a, b = m.export_state(), m2.export_state()
+    np.testing.assert_array_equal(a["hd_idx"], b["hd_idx"])
+    np.testing.assert_array_equal(a["ld_idx"], b["ld_idx"])
+    np.testing.assert_allclose(a["Y"], b["Y"], rtol=1e-4, atol=1e-5 * np.abs(a["Y"]).max())
+    m.close()
+    m2.close()
