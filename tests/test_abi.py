@@ -71,4 +71,9 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.funcsne_step(None, 1) == -1
     assert lib.funcsne_sync(None) == -1
     assert lib.funcsne_set_option(None, b"lr", 1.0) == -1
+    ids = np.zeros(2, dtype=np.int64)
+    rows = np.zeros((2, 5), dtype=np.float32)
+    assert lib.funcsne_remove(None, ids.ctypes.data, 2) == -1
+    assert lib.funcsne_update_points(None, ids.ctypes.data, 2, rows.ctypes.data) == -1
+    assert lib.funcsne_get_data(None, rows.ctypes.data, 2) == -1
     lib.funcsne_destroy(None)

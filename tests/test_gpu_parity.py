@@ -42,6 +42,16 @@ CASES = {
     # dynamic-dataset shape: D=128, d=8
     "swissroll-shape": (lambda: synth.swissroll(n=2500, dim=128, seed=6),
                         dict(d=8, k_hd=32, k_ld=16, n_neg=16, alpha=100.0, perplexity=30.0)),
+    # smallest N for k_hd = 32 (every other point is listed), D = 1, d = 1,
+    # a single negative sample
+    "n33-D1-d1": (lambda: synth.blobs(n=33, dim=1, n_clusters=2, seed=7),
+                  dict(d=1, k_hd=32, k_ld=16, n_neg=1, alpha=1.0, perplexity=20.0)),
+    # more LD than HD neighbours, tiny n_neg
+    "kld-gt-khd": (lambda: synth.blobs(n=400, dim=5, n_clusters=3, seed=8),
+                   dict(d=2, k_hd=8, k_ld=24, n_neg=3, alpha=1.0, perplexity=5.0)),
+    # perplexity above k_hd: no bandwidth reaches it, P is uniform
+    "uniform-P": (lambda: synth.blobs(n=500, dim=9, n_clusters=3, seed=9),
+                  dict(d=2, k_hd=10, k_ld=8, n_neg=8, alpha=1.0, perplexity=10.5)),
 }
 
 
