@@ -230,6 +230,14 @@ def run_ours(args, rank, world):
     results = {}
     clocks = ClockSampler(local)
     precisions = [("fp32", F.FP32), ("bf16", F.BF16), ("fp8", F.FP8)]
+    # one iteration from the same state per precision: the exact re-rank
+    # makes the reduced-precision HD lists equal the FP32 lists bit for bit
+    one_iter = {}
+    for name, prec in precisions:
+        m.import_state(base)
+        m.set_option("precision", prec)
+        m.step(1)
+        one_iter[name] = m.knn(F.SPACE_HD, with_d2=False)
     for name, prec in precisions:
         m.import_state(base)
         m.set_option("precision", prec)
@@ -270,7 +278,10 @@ def run_ours(args, rank, world):
     from paper_2509_07681_gb300.quality import recall
     for name in results:
         results[name]["recall"] = recall(results[name]["hd_idx"][q], exact)
-        results[name]["sets_equal_fp32"] = bool(np.array_equal(results[name]["hd_idx"], results["fp32"]["hd_idx"]))
+        results[name]["lists_equal_fp32_one_iteration"] = bool(np.array_equal(one_iter[name], one_iter["fp32"]))
+        # after the K timed iterations the runs differ by the order of FP32 atomics
+        results[name]["lists_equal_fp32_after_steps"] = bool(
+            np.array_equal(results[name]["hd_idx"], results["fp32"]["hd_idx"]))
 
     # end to end through the C ABI with host buffers: create from pinned host
     # X (H2D), then every step read the embedding back to pinned host memory
@@ -330,7 +341,9 @@ def run_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "precisions": {n: {"iters_per_s": round(K / (r["total_ms"] / 1e3), 2),
                            "kernel_ms": {k: round(v, 4) for k, v in r["kernel_ms"].items()},
-                           "recall_at_k_hd": round(r["recall"], 5), "sets_equal_fp32": r["sets_equal_fp32"],
+                           "recall_at_k_hd": round(r["recall"], 5),
+                           "lists_equal_fp32_one_iteration": r["lists_equal_fp32_one_iteration"],
+                           "lists_equal_fp32_after_steps": r["lists_equal_fp32_after_steps"],
                            "rerank_rows_per_point": round(r["rerank_rows"], 3),
                            "rerank_fraction": None if r["rerank_frac"] is None else round(r["rerank_frac"], 4),
                            "achieved_alg_gbs": {k: round(v, 1) for k, v in r["achieved_gbs"].items()}}
