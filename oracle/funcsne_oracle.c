@@ -233,6 +233,42 @@ int oracle_topk_merge(int64_t i, int k, const int32_t *old_idx, const double *ol
 }
 
 /*
+ * LD merge (Section 3, LD refinement; this library's reading of how the LD
+ * set is kept): the LD list is a set held in k slots. Candidates are dropped
+ * when equal to i, in the old list, or repeated in an earlier slot; the rest
+ * are taken in slot order, and one whose (d2, idx) precedes the largest
+ * (d2, idx) currently listed replaces that entry in its slot. The final set
+ * is the k smallest of the old set and the candidates; entries that stay
+ * keep their slots. idx and d2 (the old entries' distances at Y_t) are
+ * updated in place. Returns the number of replacements.
+ */
+int oracle_ld_merge(int64_t i, int k, int32_t *idx, double *d2, int n_cand, const int64_t *cand_idx,
+                    const double *cand_d2)
+{
+    int32_t *old = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+    memcpy(old, idx, sizeof(int32_t) * (size_t)k);
+    int n_rep = 0;
+    for (int s = 0; s < n_cand; ++s) {
+        int64_t c = cand_idx[s];
+        if (c == i || contains(old, k, c)) continue;
+        int seen = 0;
+        for (int r = 0; r < s; ++r)
+            if (cand_idx[r] == c) seen = 1;
+        if (seen) continue;
+        int w = 0;  /* slot of the largest (d2, idx) */
+        for (int a = 1; a < k; ++a)
+            if (d2[a] > d2[w] || (d2[a] == d2[w] && idx[a] > idx[w])) w = a;
+        if (cand_d2[s] < d2[w] || (cand_d2[s] == d2[w] && c < idx[w])) {
+            idx[w] = (int32_t)c;
+            d2[w] = cand_d2[s];
+            ++n_rep;
+        }
+    }
+    free(old);
+    return n_rep;
+}
+
+/*
  * HD candidates of point i at iteration t (Section 3: neighbours of
  * neighbours, with the LD sets proposing candidates for the HD set).
  * Slot s uses words w0, w1 of the Philox block at counter (t, i, REFINE, s):
@@ -634,10 +670,11 @@ void oracle_step(oracle_state *st, double bisect_tol, int bisect_maxit, double *
         oracle_ld_candidates(st, i, cand);
         for (int s = 0; s < CAND_LD; ++s)
             cd2[s] = (cand[s] == i) ? 0.0 : sqdist(st->Y + i * d, st->Y + cand[s] * d, d);
-        for (int a = 0; a < kl; ++a)
-            old_d2[a] = sqdist(st->Y + i * d, st->Y + (int64_t)st->ld_idx[i * kl + a] * d, d);
-        oracle_topk_merge(i, kl, st->ld_idx + i * kl, old_d2, CAND_LD, cand, cd2,
-                          nl_idx + i * kl, ld_new_d2);
+        for (int a = 0; a < kl; ++a) {
+            nl_idx[i * kl + a] = st->ld_idx[i * kl + a];
+            ld_new_d2[a] = sqdist(st->Y + i * d, st->Y + (int64_t)st->ld_idx[i * kl + a] * d, d);
+        }
+        oracle_ld_merge(i, kl, nl_idx + i * kl, ld_new_d2, CAND_LD, cand, cd2);
     }
     free(old_d2);
     free(ld_new_d2);

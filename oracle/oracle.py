@@ -11,7 +11,7 @@ import numpy as np
 
 from .build import build_oracle
 
-__all__ = ["lib", "philox", "OracleState", "bf16", "mlp_size", "mlp_init", "mlp_grad", "mlp_forward", "adam", "bisect", "entropy", "topk_merge",
+__all__ = ["lib", "philox", "OracleState", "bf16", "mlp_size", "mlp_init", "mlp_grad", "mlp_forward", "adam", "bisect", "entropy", "topk_merge", "ld_merge",
            "exact_z", "kl_divergence", "exact_grad", "bruteforce_knn", "query_knn",
            "ORACLE_BISECT_TOL", "ORACLE_BISECT_MAXIT", "STREAMS", "CAND_HD", "CAND_LD"]
 
@@ -61,6 +61,8 @@ def _declare(L):
     L.oracle_bisect.restype = C.c_int
     L.oracle_topk_merge.argtypes = [C.c_int64, C.c_int, _ip, _dp, C.c_int, _lp, _dp, _ip, _dp]
     L.oracle_topk_merge.restype = C.c_int
+    L.oracle_ld_merge.argtypes = [C.c_int64, C.c_int, _ip, _dp, C.c_int, _lp, _dp]
+    L.oracle_ld_merge.restype = C.c_int
     L.oracle_hd_candidates.argtypes = [sp, C.c_int64, _lp]
     L.oracle_hd_candidates.restype = None
     L.oracle_ld_candidates.argtypes = [sp, C.c_int64, _lp]
@@ -154,6 +156,17 @@ def topk_merge(i, old_idx, old_d2, cand_idx, cand_d2):
     ch = lib().oracle_topk_merge(int(i), k, _p(old_idx, _ip), _p(old_d2, _dp), len(cand_idx),
                                  _p(cand_idx, _lp), _p(cand_d2, _dp), _p(ni, _ip), _p(nd, _dp))
     return ni, nd, bool(ch)
+
+
+def ld_merge(i, old_idx, old_d2, cand_idx, cand_d2):
+    """The LD list's slot-keeping merge. Returns (new_idx, new_d2, replacements)."""
+    ni = np.array(old_idx, dtype=np.int32)
+    nd = np.array(old_d2, dtype=np.float64)
+    cand_idx = np.ascontiguousarray(cand_idx, dtype=np.int64)
+    cand_d2 = _f64(cand_d2)
+    n = lib().oracle_ld_merge(int(i), len(ni), _p(ni, _ip), _p(nd, _dp), len(cand_idx), _p(cand_idx, _lp),
+                              _p(cand_d2, _dp))
+    return ni, nd, int(n)
 
 
 def exact_z(Y, alpha):

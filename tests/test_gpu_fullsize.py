@@ -49,7 +49,7 @@ def test_full_size_sampled_parity(precision):
         cd2 = ((Y0[cand] - Y0[i]) ** 2).sum(1)
         old = st0["ld_idx"][i]
         od2 = ((Y0[old] - Y0[i]) ** 2).sum(1)
-        ld_new[a], _, _ = O.topk_merge(i, old, od2, cand, cd2)
+        ld_new[a], _, _ = O.ld_merge(i, old, od2, cand, cd2)
     gpu_hd = st1["hd_idx"][pts]
     gpu_ld = st1["ld_idx"][pts]
     bad = amb = 0
