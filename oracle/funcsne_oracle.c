@@ -233,39 +233,44 @@ int oracle_topk_merge(int64_t i, int k, const int32_t *old_idx, const double *ol
 }
 
 /*
- * LD merge (Section 3, LD refinement; this library's reading of how the LD
- * set is kept): the LD list is a set held in k slots. Candidates are dropped
- * when equal to i, in the old list, or repeated in an earlier slot; the rest
- * are taken in slot order, and one whose (d2, idx) precedes the largest
- * (d2, idx) currently listed replaces that entry in its slot. The final set
- * is the k smallest of the old set and the candidates; entries that stay
- * keep their slots. idx and d2 (the old entries' distances at Y_t) are
- * updated in place. Returns the number of replacements.
+ * LD merge (Section 3, LD refinement). The LD list is re-ordered every
+ * iteration: the old entries (with their distances at Y_t) and the
+ * candidates that are not i, not listed and not repeated in an earlier slot
+ * are ordered by (d2, idx), and the first k are the new list, even when no
+ * candidate entered (the old order was by the distances at Y_{t-1}). idx and
+ * d2 are replaced in place. Returns 1 when the set changed.
  */
 int oracle_ld_merge(int64_t i, int k, int32_t *idx, double *d2, int n_cand, const int64_t *cand_idx,
                     const double *cand_d2)
 {
-    int32_t *old = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
-    memcpy(old, idx, sizeof(int32_t) * (size_t)k);
-    int n_rep = 0;
+    entry *u = (entry *)malloc(sizeof(entry) * (size_t)(k + n_cand));
+    int n = 0;
+    for (int a = 0; a < k; ++a) {
+        u[n].d2 = d2[a];
+        u[n].idx = idx[a];
+        ++n;
+    }
     for (int s = 0; s < n_cand; ++s) {
         int64_t c = cand_idx[s];
-        if (c == i || contains(old, k, c)) continue;
+        if (c == i || contains(idx, k, c)) continue;
         int seen = 0;
         for (int r = 0; r < s; ++r)
             if (cand_idx[r] == c) seen = 1;
         if (seen) continue;
-        int w = 0;  /* slot of the largest (d2, idx) */
-        for (int a = 1; a < k; ++a)
-            if (d2[a] > d2[w] || (d2[a] == d2[w] && idx[a] > idx[w])) w = a;
-        if (cand_d2[s] < d2[w] || (cand_d2[s] == d2[w] && c < idx[w])) {
-            idx[w] = (int32_t)c;
-            d2[w] = cand_d2[s];
-            ++n_rep;
-        }
+        u[n].d2 = cand_d2[s];
+        u[n].idx = c;
+        ++n;
     }
-    free(old);
-    return n_rep;
+    qsort(u, (size_t)n, sizeof(entry), entry_cmp);
+    int changed = 0;
+    for (int a = 0; a < k; ++a)
+        if (!contains(idx, k, u[a].idx)) changed = 1;
+    for (int a = 0; a < k; ++a) {
+        idx[a] = (int32_t)u[a].idx;
+        d2[a] = u[a].d2;
+    }
+    free(u);
+    return changed;
 }
 
 /*

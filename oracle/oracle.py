@@ -159,14 +159,16 @@ def topk_merge(i, old_idx, old_d2, cand_idx, cand_d2):
 
 
 def ld_merge(i, old_idx, old_d2, cand_idx, cand_d2):
-    """The LD list's slot-keeping merge. Returns (new_idx, new_d2, replacements)."""
+    """The LD list's merge: old entries and new candidates ordered by
+    (d2, idx), first k kept, also when nothing entered. Returns
+    (new_idx, new_d2, changed)."""
     ni = np.array(old_idx, dtype=np.int32)
     nd = np.array(old_d2, dtype=np.float64)
     cand_idx = np.ascontiguousarray(cand_idx, dtype=np.int64)
     cand_d2 = _f64(cand_d2)
-    n = lib().oracle_ld_merge(int(i), len(ni), _p(ni, _ip), _p(nd, _dp), len(cand_idx), _p(cand_idx, _lp),
-                              _p(cand_d2, _dp))
-    return ni, nd, int(n)
+    ch = lib().oracle_ld_merge(int(i), len(ni), _p(ni, _ip), _p(nd, _dp), len(cand_idx), _p(cand_idx, _lp),
+                               _p(cand_d2, _dp))
+    return ni, nd, bool(ch)
 
 
 def exact_z(Y, alpha):

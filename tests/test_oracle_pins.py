@@ -135,17 +135,15 @@ def _state(N=300, D=10, d=2, kh=16, kl=8, nneg=8, alpha=1.0, perp=8.0, seed=5, *
     return O.OracleState(X, d, kh, kl, nneg, alpha, perp, seed=seed, **kw)
 
 
-def test_ld_merge_keeps_slots_and_takes_the_k_smallest():
-    # hand example: 7 replaces the largest entry (9, slot 1); the repeat of 9
-    # is an old entry and is dropped; 4 (2.5) is above the new largest (2.0)
-    ni, nd, n = O.ld_merge(0, [5, 9, 2], [1.0, 3.0, 2.0], [7, 9, 4], [0.5, 9.9, 2.5])
-    assert ni.tolist() == [5, 7, 2] and nd.tolist() == [1.0, 0.5, 2.0] and n == 1
-    # nothing qualifies: the list and its order are unchanged
-    ni, nd, n = O.ld_merge(0, [3, 1, 2], [0.3, 0.1, 0.2], [4, 5], [0.9, 0.8])
-    assert ni.tolist() == [3, 1, 2] and n == 0
-    # random cases against the plain definition: the set is the k smallest of
-    # (old, candidates) after dropping self, listed points and repeats; entries
-    # that stay keep their slots
+def test_ld_merge_reorders_every_time():
+    # hand example: 7 enters, 9 (a listed point) and 4 (too far) do not; the
+    # list comes out ordered by (d2, idx)
+    ni, nd, ch = O.ld_merge(0, [5, 9, 2], [1.0, 3.0, 2.0], [7, 9, 4], [0.5, 9.9, 2.5])
+    assert ni.tolist() == [7, 5, 2] and nd.tolist() == [0.5, 1.0, 2.0] and ch
+    # nothing enters: the same set, re-ordered under the new distances
+    ni, nd, ch = O.ld_merge(0, [3, 1, 2], [0.3, 0.1, 0.2], [4, 5], [0.9, 0.8])
+    assert ni.tolist() == [1, 2, 3] and not ch
+    # random cases against the plain definition
     rng = np.random.default_rng(12)
     for _ in range(300):
         k = int(rng.integers(1, 12))
@@ -155,14 +153,11 @@ def test_ld_merge_keeps_slots_and_takes_the_k_smallest():
         d = {int(j): float(rng.integers(0, 6)) + 0.01 * j for j in np.concatenate([pool, [0]])}
         od = np.array([d[int(j)] for j in old])
         cd = np.array([d[int(j)] for j in cand])
-        ni, nd, n = O.ld_merge(0, old, od, cand, cd)
+        ni, nd, ch = O.ld_merge(0, old, od, cand, cd)
         keep = [j for s, j in enumerate(cand.tolist()) if j != 0 and j not in old.tolist() and j not in cand[:s].tolist()]
         union = sorted(set(old.tolist()) | set(keep), key=lambda j: (d[j], j))[:k]
-        assert set(ni.tolist()) == set(union)
-        for a in range(k):
-            if old[a] in set(ni.tolist()):
-                assert ni[a] == old[a]
-        assert np.allclose(nd, [d[int(j)] for j in ni])
+        assert ni.tolist() == union
+        assert ch == (set(union) != set(old.tolist()))
 
 
 def test_initial_lists_distinct_and_valid():
