@@ -97,9 +97,20 @@ def test_one_iteration_matches_oracle(case):
     bad, amb = compare_sets(st1["hd_idx"], o.hd_idx, range(N), X64, band)
     assert bad == 0, f"{bad} HD sets differ beyond FP32 near-ties"
     assert amb <= max(2, N // 500)
-    badl, ambl = compare_sets(st1["ld_idx"], o.ld_idx, range(N), st["Y"].astype(np.float64), band)
+    Y0 = st["Y"].astype(np.float64)
+    badl, ambl = compare_sets(st1["ld_idx"], o.ld_idx, range(N), Y0, band)
     assert badl == 0, f"{badl} LD sets differ beyond FP32 near-ties"
     assert ambl <= max(2, N // 500)
+    # LD lists come out ordered by (d2, idx) at Y_t on both sides: where the
+    # sets agree, the order agrees too unless two neighbours are FP32 near-ties
+    for i in range(N):
+        a, b = st1["ld_idx"][i], o.ld_idx[i]
+        if set(a.tolist()) != set(b.tolist()) or np.array_equal(a, b):
+            continue
+        d2 = ((Y0[b] - Y0[i]) ** 2).sum(1)
+        ties = np.diff(d2) <= band * np.maximum(d2[1:], 1e-300)
+        wrong = np.nonzero(a != b)[0]
+        assert all(ties[max(w - 1, 0):w + 1].any() for w in wrong), (i, a, b)
     # flags and the smoothed fraction
     assert s1["last_coin"] == 1 and out["coin"]
     if amb == 0:
