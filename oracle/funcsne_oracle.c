@@ -146,6 +146,8 @@ typedef struct {
     int32_t exag_iters;   /* exaggeration applies while t < exag_iters     */
     int32_t hd_mode;      /* 0 adaptive coin, 1 always refine, 2 never     */
     int32_t neg_mode;     /* 0 Philox negatives, 1 exhaustive (pin mode)   */
+    int32_t jump_iters;   /* jump start: projections instead of gradients  */
+    int32_t jump_parts;   /*   while t < jump_iters, in jump_parts parts    */
     /* state */
     const double *X;      /* N x D                                          */
     double *Y, *V;        /* N x d                                          */
@@ -551,27 +553,20 @@ double oracle_forces(const oracle_state *st, uint32_t t, uint32_t neg_stream, do
 }
 
 /*
- * Initial state: random distinct HD and LD lists (HD lists sorted by
- * (d2, idx)), Y0 = (X - mean) R with R_fc ~ N(0,1) from counter
- * (0, f, INIT_Y, c), each LD dimension rescaled to std 1e-4 (a random linear
- * projection, Section 3's jump-start idea), V = 0, every beta calibrated
- * from a cold start, E = 1, t = 0, and Zhat = the Z estimate of this state
- * with negatives from the ZINIT stream.
+ * Y = (X - mean) R, a random linear projection of the data: R_fc ~ N(0, 1)
+ * by Box-Muller from the Philox block at counter (ctr, f, INIT_Y, c), each
+ * LD dimension then rescaled to standard deviation INIT_Y_STD. ctr = 0 is
+ * the initial layout; the jump start uses ctr = 1, 2, ... (Section 3).
  */
-void oracle_init(oracle_state *st, double bisect_tol, int bisect_maxit)
+static void project_y(oracle_state *st, uint32_t ctr)
 {
     int64_t N = st->N;
-    int D = st->D, d = st->d, kh = st->k_hd, kl = st->k_ld;
-    for (int64_t i = 0; i < N; ++i) {
-        oracle_initial_list(st->seed, N, i, kh, STREAM_INIT_HD, st->hd_idx + i * kh);
-        sort_hd_list(st, i);
-        oracle_initial_list(st->seed, N, i, kl, STREAM_INIT_LD, st->ld_idx + i * kl);
-    }
+    int D = st->D, d = st->d;
     double *Rm = (double *)malloc(sizeof(double) * (size_t)(D * d));
     for (int f = 0; f < D; ++f)
         for (int c = 0; c < d; ++c) {
             uint32_t w[4];
-            draw4(st->seed, 0u, (uint32_t)f, STREAM_INIT_Y, (uint32_t)c, w);
+            draw4(st->seed, ctr, (uint32_t)f, STREAM_INIT_Y, (uint32_t)c, w);
             Rm[f * d + c] = gauss_from(w[0], w[1]);
         }
     double *mu = (double *)calloc((size_t)(D > 0 ? D : 1), sizeof(double));
@@ -593,6 +588,28 @@ void oracle_init(oracle_state *st, double bisect_tol, int bisect_maxit)
         double scale = sd > 0.0 ? INIT_Y_STD / sd : 1.0;
         for (int64_t i = 0; i < N; ++i) st->Y[i * d + c] *= scale;
     }
+    free(Rm);
+    free(mu);
+}
+
+/*
+ * Initial state: random distinct HD and LD lists (HD lists sorted by
+ * (d2, idx)), Y0 = (X - mean) R with R_fc ~ N(0,1) from counter
+ * (0, f, INIT_Y, c), each LD dimension rescaled to std 1e-4 (a random linear
+ * projection, Section 3's jump-start idea), V = 0, every beta calibrated
+ * from a cold start, E = 1, t = 0, and Zhat = the Z estimate of this state
+ * with negatives from the ZINIT stream.
+ */
+void oracle_init(oracle_state *st, double bisect_tol, int bisect_maxit)
+{
+    int64_t N = st->N;
+    int D = st->D, d = st->d, kh = st->k_hd, kl = st->k_ld;
+    for (int64_t i = 0; i < N; ++i) {
+        oracle_initial_list(st->seed, N, i, kh, STREAM_INIT_HD, st->hd_idx + i * kh);
+        sort_hd_list(st, i);
+        oracle_initial_list(st->seed, N, i, kl, STREAM_INIT_LD, st->ld_idx + i * kl);
+    }
+    project_y(st, 0u);
     memset(st->V, 0, sizeof(double) * (size_t)(N * d));
     for (int64_t i = 0; i < N; ++i)
         oracle_bisect(st->hd_d2 + i * kh, kh, st->perplexity, 0.0, bisect_tol, bisect_maxit,
@@ -605,8 +622,6 @@ void oracle_init(oracle_state *st, double bisect_tol, int bisect_maxit)
     st->Zhat = oracle_forces(st, 0u, STREAM_ZINIT, 1.0, A, R, NULL);
     free(A);
     free(R);
-    free(Rm);
-    free(mu);
 }
 
 /* Coin for HD refinement at iteration t: refine iff the uniform draw from
@@ -649,6 +664,16 @@ void oracle_step(oracle_state *st, double bisect_tol, int bisect_maxit, double *
     memcpy(nh_d2, st->hd_d2, sizeof(double) * (size_t)(N * kh));
     memset(flags, 0, (size_t)N);
 
+    /* jump start (Section 3): while t < jump_iters, Y is a random linear
+     * projection of the data, renewed at the start of each of jump_parts
+     * equal parts (t = floor(p * jump_iters / jump_parts)), and no gradient
+     * is applied */
+    int jump = st->t < (uint32_t)st->jump_iters;
+    if (jump) {
+        int parts = st->jump_parts > 0 ? st->jump_parts : 1;
+        for (int p = 0; p < parts; ++p)
+            if ((int64_t)st->t == ((int64_t)p * st->jump_iters) / parts) project_y(st, (uint32_t)(p + 1));
+    }
     int fire = oracle_coin(st);
     int64_t n_new = 0;
     int64_t cand[CAND_HD > CAND_LD ? CAND_HD : CAND_LD];
@@ -695,7 +720,7 @@ void oracle_step(oracle_state *st, double bisect_tol, int bisect_maxit, double *
     double exag = (st->t < (uint32_t)st->exag_iters) ? st->exaggeration : 1.0;
     for (int64_t e = 0; e < N * d; ++e) {
         double g = st->att_ratio * exag * A_out[e] - st->rep_ratio * R_out[e];
-        st->V[e] = st->momentum * st->V[e] - st->lr * g;
+        st->V[e] = jump ? 0.0 : st->momentum * st->V[e] - st->lr * g;
         st->Y[e] = st->Y[e] + st->V[e];
     }
     st->Zhat = (1.0 - GAMMA_Z) * st->Zhat + GAMMA_Z * zt;
@@ -1229,4 +1254,25 @@ int64_t oracle_remove(oracle_state *st, const uint8_t *removed, double bisect_to
     oracle_recalibrate(st, bisect_tol, bisect_maxit);
     free(map);
     return Nk;
+}
+
+
+/*
+ * Shrink (or grow) the embedding: Y and V scaled by `factor` (the paper's
+ * "implosion", which makes gradients significant again after the layout has
+ * spread), then Zhat re-estimated at the new Y with negatives from counter
+ * (t, i, ZINIT, s), as for the first estimate.
+ */
+void oracle_scale(oracle_state *st, double factor)
+{
+    int64_t n = st->N * st->d;
+    for (int64_t e = 0; e < n; ++e) {
+        st->Y[e] *= factor;
+        st->V[e] *= factor;
+    }
+    double *A = (double *)malloc(sizeof(double) * (size_t)n);
+    double *R = (double *)malloc(sizeof(double) * (size_t)n);
+    st->Zhat = oracle_forces(st, st->t, STREAM_ZINIT, 1.0, A, R, NULL);
+    free(A);
+    free(R);
 }

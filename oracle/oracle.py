@@ -46,7 +46,7 @@ class _State(C.Structure):
                 ("perplexity", C.c_double), ("seed", C.c_uint64), ("lr", C.c_double),
                 ("momentum", C.c_double), ("att_ratio", C.c_double), ("rep_ratio", C.c_double),
                 ("exaggeration", C.c_double), ("exag_iters", C.c_int32), ("hd_mode", C.c_int32),
-                ("neg_mode", C.c_int32), ("X", _dp), ("Y", _dp), ("V", _dp), ("hd_idx", _ip),
+                ("neg_mode", C.c_int32), ("jump_iters", C.c_int32), ("jump_parts", C.c_int32), ("X", _dp), ("Y", _dp), ("V", _dp), ("hd_idx", _ip),
                 ("hd_d2", _dp), ("ld_idx", _ip), ("beta", _dp), ("P", _dp), ("Zhat", C.c_double),
                 ("E", C.c_double), ("t", C.c_uint32)]
 
@@ -91,6 +91,8 @@ def _declare(L):
     L.oracle_query_knn.restype = None
     L.oracle_insert.argtypes = [sp, C.c_int64, C.c_int, C.c_double, C.c_int]
     L.oracle_insert.restype = None
+    L.oracle_scale.argtypes = [sp, C.c_double]
+    L.oracle_scale.restype = None
     L.oracle_recalibrate.argtypes = [sp, C.c_double, C.c_int]
     L.oracle_recalibrate.restype = None
     L.oracle_remove.argtypes = [sp, _bp, C.c_double, C.c_int]
@@ -262,7 +264,7 @@ class OracleState:
 
     def __init__(self, X, d, k_hd, k_ld, n_neg, alpha, perplexity, seed=0, lr=None,
                  momentum=0.8, att_ratio=1.0, rep_ratio=1.0, exaggeration=1.0, exag_iters=0,
-                 hd_mode=0, neg_mode=0, init=True):
+                 hd_mode=0, neg_mode=0, jump_iters=0, jump_parts=2, init=True):
         self.X = _f64(X)
         N, D = self.X.shape
         self.N, self.D = N, D
@@ -280,6 +282,7 @@ class OracleState:
         s.alpha, s.perplexity, s.seed = alpha, perplexity, seed
         s.lr, s.momentum, s.att_ratio, s.rep_ratio = lr, momentum, att_ratio, rep_ratio
         s.exaggeration, s.exag_iters, s.hd_mode, s.neg_mode = exaggeration, exag_iters, hd_mode, neg_mode
+        s.jump_iters, s.jump_parts = jump_iters, jump_parts
         self._s = s
         self._bind()
         if init:
@@ -299,7 +302,7 @@ class OracleState:
     # scalar state and options
     def __getattr__(self, name):
         if name in ("Zhat", "E", "t", "lr", "momentum", "att_ratio", "rep_ratio", "exaggeration",
-                    "exag_iters", "hd_mode", "neg_mode", "alpha", "perplexity", "seed", "n_neg",
+                    "exag_iters", "hd_mode", "neg_mode", "jump_iters", "jump_parts", "alpha", "perplexity", "seed", "n_neg",
                     "k_hd", "k_ld", "d"):
             return getattr(self.__dict__["_s"], name)
         raise AttributeError(name)
@@ -398,6 +401,10 @@ class OracleState:
         self._bind()
         lib().oracle_insert(C.byref(self._s), n_old, int(rounds), float(tol), int(maxit))
         return n_old
+
+    def scale(self, factor):
+        """Scale Y and V by factor and re-estimate Zhat (the implosion)."""
+        lib().oracle_scale(C.byref(self._s), float(factor))
 
     def set_perplexity(self, perplexity, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
         """Change the perplexity and recalibrate every point from its list."""

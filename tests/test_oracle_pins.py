@@ -521,6 +521,44 @@ def test_removal_renumbers_replaces_and_recalibrates():
     assert np.isfinite(st.Y).all()
 
 
+def test_jump_start_projects_instead_of_stepping():
+    """While t < jump_iters: Y is a centred random linear projection of X with
+    per-dimension std 1e-4, renewed at t = 0 and t = jump_iters / 2 (two
+    parts), V stays 0; afterwards the gradient moves Y."""
+    X = synth.blobs(n=300, dim=12, n_clusters=3, seed=60)
+    st = O.OracleState(X, 3, 12, 8, 8, 1.0, 6.0, seed=60, jump_iters=6, jump_parts=2)
+    Xc = st.X - st.X.mean(0)
+    ys = []
+    for t in range(8):
+        st.step()
+        ys.append(st.Y.copy())
+        if t < 6:
+            assert np.all(st.V == 0)
+            np.testing.assert_allclose(st.Y.std(0), 1e-4, rtol=1e-9)
+            np.testing.assert_allclose(st.Y.mean(0), 0.0, atol=1e-18)
+            # Y is linear in the centred data
+            M, res, *_ = np.linalg.lstsq(Xc, st.Y, rcond=None)
+            assert np.abs(Xc @ M - st.Y).max() < 1e-12 * np.abs(st.Y).max()
+    for t in (1, 2, 4, 5):
+        np.testing.assert_array_equal(ys[t], ys[t - 1])
+    assert not np.allclose(ys[3], ys[2])          # the second projection at t = 3
+    assert not np.allclose(ys[7], ys[6]) and np.any(st.V != 0)
+
+
+def test_implosion_scales_and_reestimates_z():
+    """Scaling Y and V by f; with exhaustive negatives the new Zhat is the
+    exact sum of w over all ordered pairs at the scaled embedding."""
+    X = synth.blobs(n=200, dim=6, n_clusters=3, seed=61)
+    st = O.OracleState(X, 2, 10, 6, 4, 0.8, 5.0, seed=61, neg_mode=1)
+    for _ in range(5):
+        st.step()
+    Y0, V0 = st.Y.copy(), st.V.copy()
+    st.scale(0.1)
+    np.testing.assert_array_equal(st.Y, Y0 * 0.1)
+    np.testing.assert_array_equal(st.V, V0 * 0.1)
+    assert abs(st.Zhat - O.exact_z(st.Y, 0.8)) <= 1e-10 * st.Zhat
+
+
 # ---------------------------------------------------------------- learned placement (MLP)
 def test_bf16_rounding_matches_torch():
     torch = pytest.importorskip("torch")
