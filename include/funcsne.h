@@ -145,6 +145,13 @@ int funcsne_create(const float *X, int64_t N, int32_t D, int32_t d, int32_t k_hd
  *                    of the iteration) run side by side (default 0)
  *   "forces_cw"      floats of an LD row each lane reads in the forces
  *                    kernel: 4, 8 (default) or 16 (a tuning knob)
+ *   "jump_iters"     jump start (Section 3): during the first jump_iters
+ *                    iterations no gradient is applied; instead, at the start
+ *                    of each of "jump_parts" (default 2) equal parts, Y is
+ *                    replaced by a random linear projection of the data
+ *                    (Philox counter (part + 1, f, 8, c), std 1e-4 per
+ *                    dimension) while both neighbour sets keep refining
+ *                    (default 0: off)
  *   "insert_rounds"  neighbour-of-neighbour rounds that build an inserted
  *                    point's HD list (0..64, default 16)
  *   "hd_lanes"       lanes that read one gathered HD row in the refinement:
@@ -247,6 +254,15 @@ int funcsne_mlp_debug_step(funcsne_t *h, funcsne_mlp_debug_t *out);
 
 /* Copy the first min(N, cap_rows) rows of the N x d embedding into Y_out. */
 int funcsne_get_embedding(const funcsne_t *h, float *Y_out, int64_t cap_rows);
+
+/*
+ * funcsne_scale_embedding -- multiply Y and V by factor (> 0), then
+ * re-estimate Zhat at the scaled embedding (negatives from Philox counter
+ * (t, i, 9, s)). Section 3's "implosion": a layout that keeps spreading makes
+ * the gradients small, and shrinking it makes them significant again.
+ * Errors: FUNCSNE_E_ARG, FUNCSNE_E_OOM, FUNCSNE_E_CUDA.
+ */
+int funcsne_scale_embedding(funcsne_t *h, float factor);
 
 /* Copy the first min(N, cap_rows) rows of the N x D HD data (FP32, as held
  * after insertions, drift and removals) into X_out (host or device). With

@@ -55,6 +55,8 @@ struct funcsne {
     int32_t forces_cw = 8;    // floats of an LD row per lane in the forces kernel
     int32_t hd_lanes_opt = 0; // lanes per gathered HD row (0: chosen from the row bytes)
     int32_t insert_rounds = 16; // neighbour-of-neighbour rounds of an insertion
+    int32_t jump_iters = 0, jump_parts = 2;  // jump start by linear projections
+    bool frozen = false;      // an iteration of the jump start: no gradient step
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     int hd_blocks = 0, ld_blocks = 0, fo_blocks = 0, update_blocks = 0;
@@ -190,8 +192,8 @@ UpdateParams update_params(const funcsne* h, float* dbg_att, float* dbg_rep) {
     u.n_cnt = h->hd_blocks;
     u.hd_mode = h->hd_mode;
     u.N = h->N;
-    u.lr = static_cast<float>(h->lr);
-    u.momentum = static_cast<float>(h->momentum);
+    u.lr = h->frozen ? 0.f : static_cast<float>(h->lr);
+    u.momentum = h->frozen ? 0.f : static_cast<float>(h->momentum);
     u.att = static_cast<float>(h->att);
     u.rep = static_cast<float>(h->rep);
     u.exaggeration = static_cast<float>(h->exaggeration);
@@ -683,7 +685,7 @@ int funcsne_create(const float* X, int64_t N, int32_t D, int32_t d, int32_t k_hd
         const int64_t len = static_cast<int64_t>(D) * d + D + 2 * h->DP + 1024 * cols;
         double* scratch = nullptr;
         CREATE_CUDA(dalloc(&scratch, static_cast<size_t>(len)));
-        cudaError_t e = launch_init_y(h->X32, N, D, h->xpitch, d, h->DP, seed, h->Y, scratch, len, s);
+        cudaError_t e = launch_init_y(h->X32, N, D, h->xpitch, d, h->DP, seed, 0u, h->Y, scratch, len, s);
         if (e == cudaSuccess) {
             ZinitParams z = zinit_params(h, h->hd_idx[0], h->ld_idx[0], scratch);
             int blocks = 4 * h->num_sms;
@@ -742,6 +744,10 @@ int funcsne_set_option(funcsne_t* h, const char* key, double v) {
         h->perplexity = static_cast<float>(v);
         drop_graphs(h);
         return recalibrate(h);
+    } else if (k == "jump_iters" || k == "jump_parts") {
+        if (v < (k == "jump_parts" ? 1 : 0) || v > 1e7 || v != static_cast<int>(v))
+            return fail(h, FUNCSNE_E_ARG, "%s must be an integer (jump_iters >= 0, jump_parts >= 1)", key);
+        (k == "jump_iters" ? h->jump_iters : h->jump_parts) = static_cast<int32_t>(v);
     } else if (k == "insert_rounds") {
         if (v < 0 || v > 64 || v != static_cast<int>(v))
             return fail(h, FUNCSNE_E_ARG, "insert_rounds must be an integer in [0, 64]");
@@ -802,6 +808,8 @@ int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
     else if (k == "hd_lanes") *v = h->hd_lanes_opt;
     else if (k == "hd_lanes_used") *v = hd_lanes(h);
     else if (k == "insert_rounds") *v = h->insert_rounds;
+    else if (k == "jump_iters") *v = h->jump_iters;
+    else if (k == "jump_parts") *v = h->jump_parts;
     else if (k == "perplexity") *v = h->perplexity;
     else if (k == "surrogate") *v = h->surrogate ? 1 : 0;
     else if (k == "mlp_every") *v = h->mlp_every;
@@ -828,9 +836,48 @@ int funcsne_set_stream(funcsne_t* h, void* stream) {
     return FUNCSNE_OK;
 }
 
+// Y = a random linear projection of the data, Philox counter (ctr, f,
+// INIT_Y, c), each LD dimension at the initial scale.
+int project_embedding(funcsne* h, uint32_t ctr) {
+    const int64_t cols = h->D > h->DP ? h->D : h->DP;
+    const int64_t len = static_cast<int64_t>(h->D) * h->d + h->D + 2 * h->DP + 1024 * cols;
+    double* scratch = nullptr;
+    FSNE_CUDA(h, dalloc(&scratch, static_cast<size_t>(len)));
+    cudaError_t e = launch_init_y(h->X32, h->N, h->D, h->xpitch, h->d, h->DP, h->seed, ctr, h->Y, scratch, len,
+                                  h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(scratch);
+    FSNE_CUDA(h, e);
+    return FUNCSNE_OK;
+}
+
+// One iteration of the jump start (Section 3): at the start of each of
+// jump_parts equal parts of the first jump_iters iterations the embedding is
+// replaced by a fresh random linear projection of the data; the iteration
+// refines both neighbour sets and estimates Z, but applies no gradient.
+int jump_iteration(funcsne* h) {
+    const int64_t t = h->t_host, J = h->jump_iters, P = h->jump_parts;
+    for (int64_t p = 0; p < P; ++p)
+        if (t == p * J / P) {
+            int rc = project_embedding(h, static_cast<uint32_t>(p + 1));
+            if (rc) return rc;
+        }
+    h->frozen = true;
+    int rc = enqueue_iteration(h, h->stream, nullptr, nullptr);
+    h->frozen = false;
+    if (rc) return rc;
+    ++h->t_host;
+    return FUNCSNE_OK;
+}
+
 int funcsne_step(funcsne_t* h, int32_t n_iters) {
     if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
     if (n_iters < 0) return fail(h, FUNCSNE_E_ARG, "n_iters must be >= 0");
+    while (n_iters > 0 && h->t_host < static_cast<uint32_t>(h->jump_iters)) {
+        int rc = jump_iteration(h);
+        if (rc) return rc;
+        --n_iters;
+    }
     if (n_iters == 0) return FUNCSNE_OK;
     if (!h->graph1) {
         int rc = build_graph(h, 1, &h->graph1);
@@ -1177,6 +1224,27 @@ int funcsne_get_data(const funcsne_t* hc, float* X_out, int64_t cap_rows) {
     int rc = copy_rows<float>(h, X_out, h->D, h->X32, h->xpitch, rows, h->D);
     if (rc) return rc;
     FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return FUNCSNE_OK;
+}
+
+int funcsne_scale_embedding(funcsne_t* h, float factor) {
+    if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
+    if (!(factor > 0.f) || !std::isfinite(factor)) return fail(h, FUNCSNE_E_ARG, "factor must be > 0 and finite");
+    DevScalars s;
+    int rc = read_scalars(h, &s);
+    if (rc) return rc;
+    FSNE_CUDA(h, launch_scale_rows(h->Y, h->V, h->N * h->DP, factor, h->stream));
+    // Zhat re-estimated at the scaled embedding, negatives from (t, i, ZINIT, s)
+    double* part = nullptr;
+    int blocks = 4 * h->num_sms;
+    if (blocks > 1024) blocks = 1024;
+    FSNE_CUDA(h, dalloc(&part, static_cast<size_t>(blocks)));
+    ZinitParams z = zinit_params(h, h->hd_idx[s.hd_cur], h->ld_idx[s.ld_cur], part);
+    z.t = s.t;
+    cudaError_t e = launch_zinit(z, h->DP, blocks, h->sc, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(part);
+    FSNE_CUDA(h, e);
     return FUNCSNE_OK;
 }
 

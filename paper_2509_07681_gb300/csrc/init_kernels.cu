@@ -98,12 +98,12 @@ __global__ void __launch_bounds__(256) hd_finalize_kernel(FinalizeParams f) {
     }
 }
 
-// Gaussian matrix R (D x d, FP64) from counter (0, f, INIT_Y, c), Box-Muller.
-__global__ void gauss_matrix_kernel(int D, int d, uint64_t seed, double* R) {
+// Gaussian matrix R (D x d, FP64) from counter (ctr, f, INIT_Y, c), Box-Muller.
+__global__ void gauss_matrix_kernel(int D, int d, uint32_t ctr, uint64_t seed, double* R) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= D * d) return;
     const int fi = e / d, c = e % d;
-    const uint4 w = philox(0u, static_cast<uint32_t>(fi), kStreamInitY, static_cast<uint32_t>(c), seed);
+    const uint4 w = philox(ctr, static_cast<uint32_t>(fi), kStreamInitY, static_cast<uint32_t>(c), seed);
     const double u1 = (static_cast<double>(w.x) + 0.5) * (1.0 / 4294967296.0);
     const double u2 = (static_cast<double>(w.y) + 0.5) * (1.0 / 4294967296.0);
     R[e] = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
@@ -310,7 +310,7 @@ cudaError_t launch_hd_finalize(const FinalizeParams& f, int blocks, cudaStream_t
 }
 
 cudaError_t launch_init_y(const float* X32, int64_t N, int D, int xpitch, int d, int DP, uint64_t seed,
-                          float* Y, double* scratch, int64_t scratch_len, cudaStream_t s) {
+                          uint32_t ctr, float* Y, double* scratch, int64_t scratch_len, cudaStream_t s) {
     // scratch layout: R (D*d) | mu (D) | moments (2*DP) | partials
     double* R = scratch;
     double* mu = R + static_cast<int64_t>(D) * d;
@@ -324,7 +324,7 @@ cudaError_t launch_init_y(const float* X32, int64_t N, int D, int xpitch, int d,
     if (nb < 1) return cudaErrorInvalidValue;
     const int64_t rpb = (N + nb - 1) / nb;
     nb = static_cast<int>((N + rpb - 1) / rpb);
-    gauss_matrix_kernel<<<grid_for(static_cast<int64_t>(D) * d, 128), 128, 0, s>>>(D, d, seed, R);
+    gauss_matrix_kernel<<<grid_for(static_cast<int64_t>(D) * d, 128), 128, 0, s>>>(D, d, ctr, seed, R);
     col_sums_kernel<<<nb, 256, 0, s>>>(X32, N, D, xpitch, rpb, nullptr, 0, part);
     reduce_parts_kernel<<<grid_for(D, 128), 128, 0, s>>>(part, nb, D, 1.0 / static_cast<double>(N), mu);
     project_kernel<<<grid_for(N, 128), 128, 0, s>>>(X32, N, D, xpitch, mu, R, d, DP, Y);

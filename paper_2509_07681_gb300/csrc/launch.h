@@ -84,7 +84,7 @@ cudaError_t update_launch(const UpdateParams& u, int blocks, cudaStream_t s);
 cudaError_t launch_init_lists(int64_t N, int k, uint32_t stream, uint64_t seed, int32_t* out, cudaStream_t s);
 cudaError_t launch_hd_finalize(const FinalizeParams& f, int blocks, cudaStream_t s);
 cudaError_t launch_init_y(const float* X32, int64_t N, int D, int xpitch, int d, int DP, uint64_t seed,
-                          float* Y, double* scratch, int64_t scratch_len, cudaStream_t s);
+                          uint32_t ctr, float* Y, double* scratch, int64_t scratch_len, cudaStream_t s);
 cudaError_t launch_zinit(const ZinitParams& z, int DP, int blocks, DevScalars* sc, cudaStream_t s);
 cudaError_t launch_quantize(const float* X32, int64_t N, int D, int xpitch, int precision, int qpitch,
                             int scale_off, uint8_t* Q, cudaStream_t s);
@@ -95,6 +95,7 @@ cudaError_t launch_gather_rows(uint32_t* dst, const uint32_t* src, int64_t pitch
                                int64_t n_rows, cudaStream_t s);
 cudaError_t launch_scatter_rows(float* X32, int xpitch, const int64_t* ids, const float* rows, int64_t n, int D,
                                 cudaStream_t s);
+cudaError_t launch_scale_rows(float* Y, float* V, int64_t n_elem, float factor, cudaStream_t s);
 cudaError_t launch_remap_lists(int32_t* list, int k, const int32_t* new_of, int64_t N, uint32_t t, uint64_t seed,
                                uint32_t salt, cudaStream_t s);
 cudaError_t launch_ld_distances(const float* Y, const int32_t* idx, int64_t N, int k, int DP, float* d2,

@@ -75,6 +75,15 @@ __global__ void remap_lists_kernel(int32_t* __restrict__ list, int k, const int3
     }
 }
 
+// Y and V scaled by one factor (the embedding's padding columns stay 0).
+__global__ void scale_rows_kernel(float* __restrict__ Y, float* __restrict__ V, int64_t n, float f) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        Y[e] *= f;
+        V[e] *= f;
+    }
+}
+
 static int grid_for(int64_t work, int threads) {
     int64_t b = (work + threads - 1) / threads;
     if (b > 8192) b = 8192;
@@ -103,4 +112,12 @@ cudaError_t launch_remap_lists(int32_t* list, int k, const int32_t* new_of, int6
     return cudaGetLastError();
 }
 
+}  // namespace fsne
+
+namespace fsne {
+cudaError_t launch_scale_rows(float* Y, float* V, int64_t n_elem, float factor, cudaStream_t s) {
+    if (n_elem <= 0) return cudaSuccess;
+    scale_rows_kernel<<<grid_for(n_elem, 256), 256, 0, s>>>(Y, V, n_elem, factor);
+    return cudaGetLastError();
+}
 }  // namespace fsne

@@ -68,6 +68,7 @@ ABI_FUNCTIONS = {
     "funcsne_remove": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_get_embedding": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_get_data": (C.c_int, [_h, _vp, C.c_int64]),
+    "funcsne_scale_embedding": (C.c_int, [_h, C.c_float]),
     "funcsne_get_knn": (C.c_int, [_h, C.c_int32, _vp, _vp]),
     "funcsne_get_stats": (C.c_int, [_h, C.POINTER(Stats)]),
     "funcsne_export_state": (C.c_int, [_h, C.POINTER(State)]),
@@ -177,6 +178,10 @@ def funcsne_update_points(h, ids, X_rows):
 def funcsne_remove(h, ids):
     pi, keep_i = _ptr(ids)
     _check(load().funcsne_remove(h, pi, ids.shape[0]), h)
+
+
+def funcsne_scale_embedding(h, factor):
+    _check(load().funcsne_scale_embedding(h, float(factor)), h)
 
 
 def funcsne_get_data(h, out):
@@ -399,6 +404,10 @@ class FuncSNE:
         self.N += X_new.shape[0]
         return first
 
+    def scale_embedding(self, factor):
+        """Scale Y and V by factor and re-estimate Zhat (the implosion)."""
+        funcsne_scale_embedding(self.h, factor)
+
     def data(self, out=None):
         """The N x D HD rows the handle holds."""
         if out is None:
@@ -407,7 +416,8 @@ class FuncSNE:
 
     CHECKPOINT_OPTIONS = ("lr", "momentum", "att_ratio", "rep_ratio", "exaggeration", "exag_iters", "hd_mode",
                           "precision", "alpha", "perplexity", "concurrent", "surrogate", "mlp_every", "mlp_lr",
-                          "mlp_batch", "mlp_hidden", "forces_cw", "hd_lanes", "insert_rounds")
+                          "mlp_batch", "mlp_hidden", "forces_cw", "hd_lanes", "insert_rounds",
+                          "jump_iters", "jump_parts")
 
     def save(self, path):
         """Checkpoint: HD rows, the exported iteration state, the creation

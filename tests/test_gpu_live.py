@@ -183,3 +183,45 @@ def test_checkpoint_resume(tmp_path):
     np.testing.assert_allclose(a["Y"], b["Y"], rtol=1e-4, atol=1e-5 * np.abs(a["Y"]).max())
     m.close()
     m2.close()
+
+
+def test_jump_start_matches_oracle():
+    """Jump start: at t = 0 and t = 3 (jump_iters 6, two parts) the embedding
+    is the oracle's random linear projection; in between no gradient moves
+    it; afterwards the gradient steps resume."""
+    X = synth.blobs(n=1500, dim=20, n_clusters=5, seed=55)
+    m = F.FuncSNE(X, P["d"], P["k_hd"], P["k_ld"], P["n_neg"], P["alpha"], P["perplexity"], seed=0, hd_mode=1,
+                  jump_iters=6, jump_parts=2)
+    st = m.export_state()
+    o = oracle_from_state(X, st, P, hd_mode=1, jump_iters=6, jump_parts=2)
+    ys = []
+    for t in range(7):
+        m.step(1)
+        o.step()
+        g = m.export_state()
+        if t in (0, 3):
+            assert np.max(rel_err_rows(g["Y"].astype(np.float64), o.Y)) < 1e-5
+        if t < 6:
+            assert np.all(g["V"] == 0)
+        ys.append(g["Y"])
+    np.testing.assert_array_equal(ys[1], ys[0])
+    np.testing.assert_array_equal(ys[5], ys[3])
+    assert not np.array_equal(ys[3], ys[2]) and not np.array_equal(ys[6], ys[5])
+    m.close()
+
+
+def test_implosion_matches_oracle():
+    X = synth.blobs(n=1500, dim=20, n_clusters=5, seed=56)
+    m = _run(X, steps=20)
+    st = m.export_state()
+    o = oracle_from_state(X, st, P, hd_mode=1)
+    m.scale_embedding(0.1)
+    o.scale(0.1)
+    g = m.export_state()
+    assert np.max(rel_err_rows(g["Y"].astype(np.float64), o.Y)) < 1e-6
+    assert abs(g["Zhat"] - o.Zhat) <= 1e-5 * o.Zhat and g["Zhat"] > st["Zhat"]
+    with pytest.raises(F.FuncSNEError):
+        m.scale_embedding(0.0)
+    m.step(2)
+    assert np.isfinite(m.embedding()).all()
+    m.close()
