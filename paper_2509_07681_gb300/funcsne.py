@@ -404,6 +404,19 @@ class FuncSNE:
         self.N += X_new.shape[0]
         return first
 
+    def anneal(self, alphas, iters_per_level):
+        """Snapshots under growing tail weight (Section 4.2): for each alpha
+        in `alphas` (usually decreasing, so the LD kernel tails get heavier
+        and clusters fragment), set it, run `iters_per_level` iterations and
+        keep a copy of the embedding. Returns the list of N x d snapshots;
+        clustering them into a hierarchy is left to the caller."""
+        snaps = []
+        for a in alphas:
+            self.set_option("alpha", float(a))
+            self.step(int(iters_per_level))
+            snaps.append(self.embedding())
+        return snaps
+
     def scale_embedding(self, factor):
         """Scale Y and V by factor and re-estimate Zhat (the implosion)."""
         funcsne_scale_embedding(self.h, factor)

@@ -225,3 +225,15 @@ def test_implosion_matches_oracle():
     m.step(2)
     assert np.isfinite(m.embedding()).all()
     m.close()
+
+
+def test_alpha_annealing_snapshots():
+    """anneal(): one snapshot per tail weight; lowering alpha during the run
+    changes the forces (the snapshots differ) and keeps the run finite."""
+    X = synth.blobs(n=1200, dim=12, n_clusters=4, seed=57)
+    m = _run(X, steps=30)
+    snaps = m.anneal([1.0, 0.5, 0.25], 10)
+    assert len(snaps) == 3 and all(s.shape == (1200, 2) for s in snaps)
+    assert m.get_option("alpha") == 0.25
+    assert all(np.isfinite(s).all() for s in snaps) and not np.array_equal(snaps[1], snaps[2])
+    m.close()
