@@ -10,7 +10,7 @@ normalisation, momentum update. Metric: iterations/s, BF16 HD storage vs
 FP32 at equal KNN recall (the FP32 re-rank makes the neighbour sets equal).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload NAME] [--alpha A] [--mode bench|dynamic|ncu]
+                    [--workload NAME] [--alpha A] [--mode bench|dynamic|feedback|ncu]
 
 --workload picks another synthetic workload (blobs-2k, pixels-70k,
 swissroll-200k, lowrank-2m) for the same measurement. --mode dynamic runs the

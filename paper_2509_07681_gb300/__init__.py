@@ -1,4 +1,4 @@
-"""GB300-native FUnc-SNE: the fused per-iteration step as hand-written CUDA
+"""GB300-native FUnc-SNE: the per-iteration step as hand-written CUDA
 behind a C ABI (``include/funcsne.h``), with a thin Python binding.
 
 Import ``paper_2509_07681_gb300.funcsne`` for the binding; this package

@@ -1,4 +1,4 @@
-"""GPU parity of the fused FUnc-SNE iteration against the FP64 oracle,
+"""GPU parity of the FUnc-SNE iteration (phase kernels) against the FP64 oracle,
 through the C ABI. One iteration from the same state and Philox streams:
 neighbour index sets bit-exact (FP32/FP64 near-ties at the list boundary
 are reported, never silently accepted beyond a handful), forces within
