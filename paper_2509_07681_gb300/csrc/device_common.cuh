@@ -511,13 +511,37 @@ __device__ __forceinline__ float group_rerank_f32(const float* __restrict__ xs, 
     return mine;
 }
 
+// Adds the squared differences between own-row floats 8q .. 8q + 7 and the
+// eight BF16 values of chunk q to acc, in order.
+__device__ __forceinline__ float bf16_chunk_acc(const float* __restrict__ xs, const uint4 raw, int q, float acc) {
+    const float4 x0 = reinterpret_cast<const float4*>(xs)[2 * q];
+    const float4 x1 = reinterpret_cast<const float4*>(xs)[2 * q + 1];
+    float d = __fsub_rn(x0.x, __uint_as_float(raw.x << 16));
+    acc = __fmaf_rn(d, d, acc);
+    d = __fsub_rn(x0.y, __uint_as_float(raw.x & 0xffff0000u));
+    acc = __fmaf_rn(d, d, acc);
+    d = __fsub_rn(x0.z, __uint_as_float(raw.y << 16));
+    acc = __fmaf_rn(d, d, acc);
+    d = __fsub_rn(x0.w, __uint_as_float(raw.y & 0xffff0000u));
+    acc = __fmaf_rn(d, d, acc);
+    d = __fsub_rn(x1.x, __uint_as_float(raw.z << 16));
+    acc = __fmaf_rn(d, d, acc);
+    d = __fsub_rn(x1.y, __uint_as_float(raw.z & 0xffff0000u));
+    acc = __fmaf_rn(d, d, acc);
+    d = __fsub_rn(x1.z, __uint_as_float(raw.w << 16));
+    acc = __fmaf_rn(d, d, acc);
+    d = __fsub_rn(x1.w, __uint_as_float(raw.w & 0xffff0000u));
+    acc = __fmaf_rn(d, d, acc);
+    return acc;
+}
+
 // BF16 rows by groups: the distance to the dequantised row and its band,
 // for the candidate of every lane. BF16 rows hold nq chunks of 8 values,
 // then a 16-byte chunk whose first four bytes hold an upper bound N_c of the
 // rounded row's norm. With |x_f - x~_f| <= u |x~_f|, ||e|| <= u N_c = E and
 // |d~2 - d2| <= 2 ||x_i - x~_c|| E + E^2 (Cauchy-Schwarz), plus the FP32
 // rounding of both distance evaluations.
-template <int G>
+template <int G, bool BATCH>
 __device__ __forceinline__ ApproxDist group_dist_bf16(const float* __restrict__ xs,
                                                       const uint8_t* __restrict__ Xq, int qpitch, int nq,
                                                       uint32_t cv, int lane, float u, float gamma) {
@@ -531,27 +555,25 @@ __device__ __forceinline__ ApproxDist group_dist_bf16(const float* __restrict__ 
         float acc = 0.f, nrm = 0.f;
         if (cj != kNoRow) {
             const uint4* b = reinterpret_cast<const uint4*>(Xq + static_cast<int64_t>(cj) * qpitch);
+            if constexpr (BATCH) {
+                // all of a batch's chunk loads in flight before any is used
+                constexpr int kB = 8;
+                for (int q0 = s; q0 < nq; q0 += kB * G) {
+                    uint4 raw[kB];
+#pragma unroll
+                    for (int k = 0; k < kB; ++k) {
+                        const int q = q0 + k * G;
+                        raw[k] = q < nq ? __ldg(b + q) : make_uint4(0u, 0u, 0u, 0u);
+                    }
+#pragma unroll
+                    for (int k = 0; k < kB; ++k) {
+                        const int q = q0 + k * G;
+                        if (q < nq) acc = bf16_chunk_acc(xs, raw[k], q, acc);
+                    }
+                }
+            } else {
 #pragma unroll 2
-            for (int q = s; q < nq; q += G) {
-                const uint4 raw = __ldg(b + q);
-                const float4 x0 = reinterpret_cast<const float4*>(xs)[2 * q];
-                const float4 x1 = reinterpret_cast<const float4*>(xs)[2 * q + 1];
-                float d = __fsub_rn(x0.x, __uint_as_float(raw.x << 16));
-                acc = __fmaf_rn(d, d, acc);
-                d = __fsub_rn(x0.y, __uint_as_float(raw.x & 0xffff0000u));
-                acc = __fmaf_rn(d, d, acc);
-                d = __fsub_rn(x0.z, __uint_as_float(raw.y << 16));
-                acc = __fmaf_rn(d, d, acc);
-                d = __fsub_rn(x0.w, __uint_as_float(raw.y & 0xffff0000u));
-                acc = __fmaf_rn(d, d, acc);
-                d = __fsub_rn(x1.x, __uint_as_float(raw.z << 16));
-                acc = __fmaf_rn(d, d, acc);
-                d = __fsub_rn(x1.y, __uint_as_float(raw.z & 0xffff0000u));
-                acc = __fmaf_rn(d, d, acc);
-                d = __fsub_rn(x1.z, __uint_as_float(raw.w << 16));
-                acc = __fmaf_rn(d, d, acc);
-                d = __fsub_rn(x1.w, __uint_as_float(raw.w & 0xffff0000u));
-                acc = __fmaf_rn(d, d, acc);
+                for (int q = s; q < nq; q += G) acc = bf16_chunk_acc(xs, __ldg(b + q), q, acc);
             }
             if (s == sn) nrm = __ldg(reinterpret_cast<const float*>(b + nq));
         }

@@ -127,7 +127,8 @@ hd_refine_kernel(const StepParams p) {
             const float thr = warp_get<RH>(hd2, static_cast<uint32_t>(k_hd - 1));
             ApproxDist a;
             if constexpr (XM == 1)
-                a = group_dist_bf16<G>(xs, p.Xq, p.qpitch, p.nq, cv, lane, p.q_u, p.q_gamma);
+                // batched loads pay off with the 64 registers of the k_hd > 32 variant
+                a = group_dist_bf16<G, RH == 2>(xs, p.Xq, p.qpitch, p.nq, cv, lane, p.q_u, p.q_gamma);
             else  // nq = code words for FP8
                 a = group_dist_fp8<G>(xs, p.Xq, p.qpitch, p.nq, p.qscale_off, cv, lane, p.q_u, p.q_a,
                                       p.q_gamma);

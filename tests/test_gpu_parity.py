@@ -138,14 +138,15 @@ def test_one_iteration_matches_oracle(case):
     m.close()
 
 
-@pytest.mark.parametrize("dim", [50, 200])
+@pytest.mark.parametrize("dim,k_hd", [(50, 32), (200, 32), (200, 64)])
 @pytest.mark.parametrize("precision", [F.BF16, F.FP8])
-def test_reduced_precision_sets_equal_fp32(precision, dim):
+def test_reduced_precision_sets_equal_fp32(precision, dim, k_hd):
     """BF16 / FP8 rows with the exact FP32 re-rank give the FP32 path's sets
     and distances bit for bit (D = 200: the reduced-precision rows and the
-    FP32 rows are read by different numbers of lanes per row)."""
+    FP32 rows are read by different numbers of lanes per row; k_hd = 64: the
+    two-register list, whose BF16 pass batches its loads)."""
     X = synth.spectrum(n=4000, dim=dim, n_clusters=12, seed=7)
-    p = CASES["spectrum-shape"][1]
+    p = dict(CASES["spectrum-shape"][1], k_hd=k_hd)
     m = _make(X, p, hd_mode=1)
     m.step(3)
     st = m.export_state()
