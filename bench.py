@@ -632,6 +632,66 @@ def run_feedback(args, rank, world):
         dist.destroy_process_group()
 
 
+def run_timing(args, rank, world):
+    """Time of `--iters` iterations (default 3,000) across dataset sizes of
+    fixed dimensionality 32 (Section 6, Fig. 8): HD refinement at every
+    iteration (the figure's dashed lines) against the adaptive coin with
+    probability floor + (1 - floor) E (its plain lines, Section 3), and, at
+    the largest size, variants of the floor and of the smoothing rate
+    gamma_e. Data: the spectrum generator at D = 32 (50 Zipf-sized clusters,
+    variance of feature j ~ 1/j). Reports the time, the share of iterations
+    that refined the HD sets and the final HD-KNN recall@k_hd on 1,000
+    sampled queries against exact neighbours."""
+    import torch
+    from paper_2509_07681_gb300 import funcsne as F
+    from paper_2509_07681_gb300 import synth
+    from paper_2509_07681_gb300.quality import recall
+
+    local, dist = _setup_gpu(world)
+    stream = torch.cuda.Stream()
+    p = dict(d=2, k_hd=32, k_ld=16, n_neg=16, alpha=1.0, perplexity=30.0)
+    sizes = [int(v) for v in args.sizes.split(",")]
+    iters = args.iters
+
+    def run(X, hd_mode, floor=0.05, gamma_e=0.1):
+        m = F.FuncSNE(X, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0,
+                      hd_mode=hd_mode, coin_floor=floor, gamma_e=gamma_e)
+        m.set_stream(stream)
+        m.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m.step(iters)
+        e1.record(stream)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        st = m.stats()
+        q = np.sort(np.random.default_rng(1).choice(len(X), min(1000, len(X)), replace=False)).astype(np.int32)
+        ex, _ = m.exact_knn(q, p["k_hd"])
+        rec = recall(m.knn(F.SPACE_HD, with_d2=False)[q], ex)
+        m.close()
+        return {"seconds": round(sec, 3), "refined_share": round(st["n_refined"] / iters, 4),
+                "recall_hd": round(rec, 4), "E_final": round(st["E"], 5)}
+
+    rows = {}
+    variants = {}
+    for N in sizes:
+        X = synth.spectrum(n=N, dim=32, n_clusters=50, seed=0)
+        rows[str(N)] = {"every iteration": run(X, 1), "adaptive": run(X, 0)}
+        if N == sizes[-1]:
+            for floor, ge in ((0.0, 0.1), (0.2, 0.1), (0.05, 0.5), (0.05, 0.02)):
+                variants[f"floor={floor}, gamma_e={ge}"] = run(X, 0, floor, ge)
+    if rank == 0:
+        print(json.dumps({"metric": f"seconds for {iters} iterations (HD refinement every iteration vs adaptive)",
+                          "data": "synthetic",
+                          "config": {"generator": "spectrum, D=32, 50 clusters", **p,
+                                     "iterations": iters, "recall": "1000 sampled queries, exact KNN on the GPU"},
+                          "results": rows, "coin_variants_at_N": {str(sizes[-1]): variants}}), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def run_profile_case(args):
     """A short, fixed sequence of launches for ncu: create the workload at N
     (default: the workload's own N), then for each precision `warmup` +
@@ -668,9 +728,12 @@ def parse_args(argv=None):
     ap.add_argument("--alpha", type=float, default=None, help="override the workload's alpha")
     ap.add_argument("--n", type=int, default=None, help="override N (default: the workload's own)")
     ap.add_argument("--cpu-sample", type=int, default=20000, help="points in the reference arm's oracle sample")
-    ap.add_argument("--mode", choices=["bench", "dynamic", "feedback", "ncu"], default="bench",
+    ap.add_argument("--mode", choices=["bench", "dynamic", "feedback", "timing", "ncu"], default="bench",
                     help="dynamic: insertion protocol; feedback: HD-KNN recall with optimised or fixed Y; "
-                         "ncu: the short fixed launch sequence used for profiling")
+                         "timing: time of --iters iterations across sizes, adaptive vs every-iteration HD "
+                         "refinement; ncu: the short fixed launch sequence used for profiling")
+    ap.add_argument("--sizes", default="100000,200000,500000,1000000,2000000", help="--mode timing: dataset sizes")
+    ap.add_argument("--iters", type=int, default=3000, help="--mode timing: iterations per run")
     ap.add_argument("--precisions", default="fp32,bf16,fp8", help="precisions of --mode ncu")
     ap.add_argument("--burn-in", type=int, default=0, help="untimed iterations first (0: the mode's default)")
     ap.add_argument("--insert-n", type=int, default=10000, help="--mode dynamic: points per insertion")
@@ -698,6 +761,8 @@ def main():
         run_reference(args, rank, world)
     elif args.mode == "dynamic":
         run_dynamic(args, rank, world)
+    elif args.mode == "timing":
+        run_timing(args, rank, world)
     elif args.mode == "feedback":
         run_feedback(args, rank, world)
     else:

@@ -81,6 +81,7 @@ typedef struct {
     int64_t cand_reranked; /* of which re-ranked from FP32 rows (cumulative)         */
     int64_t mlp_steps;     /* training steps of the placement MLP                    */
     double mlp_loss;       /* its loss on the last training batch                    */
+    int64_t n_refined;     /* steps that refined the HD sets (cumulative)           */
 } funcsne_stats_t;
 
 /* One training step of the placement MLP with its intermediate values, for
@@ -136,6 +137,14 @@ int funcsne_create(const float *X, int64_t N, int32_t D, int32_t d, int32_t k_hd
  *   "exag_iters"     iterations with exaggeration (default 0)
  *   "hd_mode"        0: refine the HD sets with probability 0.05 + 0.95 E
  *                    (Section 3); 1: every iteration; 2: never
+ *   "coin_floor"     p0 of the refinement probability p0 + (1 - p0) E in
+ *                    [0, 1] (default 0.05, the paper's value)
+ *   "gamma_e"        smoothing rate in (0, 1] of E, the running fraction of
+ *                    points that found new HD neighbours:
+ *                    E <- (1 - gamma_e) E + gamma_e N_new / N after each
+ *                    refinement (default 0.1; the paper gives none)
+ *   "gamma_z"        smoothing rate in (0, 1] of the normalisation estimate:
+ *                    Zhat <- (1 - gamma_z) Zhat + gamma_z Z_t (default 0.1)
  *   "precision"      FUNCSNE_FP32 / FUNCSNE_BF16 / FUNCSNE_FP8 HD storage
  *   "alpha"          tail parameter (may change between steps)
  *   "perplexity"     target perplexity in (1, k_hd + 1); a change recomputes

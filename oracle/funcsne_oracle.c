@@ -17,7 +17,8 @@
  *   Section 3  joint HD/LD neighbour refinement from neighbours of neighbours
  *              and cross-space proposals; new-neighbour flags; warm-restart
  *              bandwidth recalibration; HD refinement with probability
- *              0.05 + 0.95 E[N_new/N]; LD refinement every iteration;
+ *              0.05 + 0.95 E[N_new/N] (floor 0.05 is an option); LD
+ *              refinement every iteration;
  *              separate attraction / repulsion scaling.
  * Readings where the paper is silent (candidate counts, random-number
  * mapping, tie-break, Jacobi update order, bisection details, Z estimator,
@@ -92,8 +93,6 @@ enum {
 #define LD_SLOTS_NN 16         /* LD slots 0..15: LD neighbour of neighbour */
 #define LD_SLOTS_HDNB 24       /* LD slots 16..23: HD neighbour             */
                                /* LD slots 24..31: uniform random           */
-#define GAMMA_E 0.1            /* smoothing of E[N_new/N]                   */
-#define GAMMA_Z 0.1            /* smoothing of the normalisation estimate   */
 #define INIT_Y_STD 1e-4        /* per-dimension std of the initial layout   */
 #define INSERT_SLOTS_NN 24     /* insertion slots 0..23: neighbour of neighbour */
                                /* insertion slots 24..31: random existing point */
@@ -148,6 +147,9 @@ typedef struct {
     int32_t neg_mode;     /* 0 Philox negatives, 1 exhaustive (pin mode)   */
     int32_t jump_iters;   /* jump start: projections instead of gradients  */
     int32_t jump_parts;   /*   while t < jump_iters, in jump_parts parts    */
+    double coin_floor;    /* refinement probability floor + (1-floor) E    */
+    double gamma_e;       /* smoothing rate of E[N_new/N]                  */
+    double gamma_z;       /* smoothing rate of the normalisation estimate  */
     /* state */
     const double *X;      /* N x D                                          */
     double *Y, *V;        /* N x d                                          */
@@ -625,14 +627,15 @@ void oracle_init(oracle_state *st, double bisect_tol, int bisect_maxit)
 }
 
 /* Coin for HD refinement at iteration t: refine iff the uniform draw from
- * counter (t, 0, COIN, 0) is below 0.05 + 0.95 E (Section 3). */
+ * counter (t, 0, COIN, 0) is below floor + (1 - floor) E; the paper sets
+ * the floor to 0.05 (Section 3). */
 int oracle_coin(const oracle_state *st)
 {
     if (st->hd_mode == 1) return 1;
     if (st->hd_mode == 2) return 0;
     uint32_t w[4];
     draw4(st->seed, st->t, 0u, STREAM_COIN, 0u, w);
-    double p = 0.05 + 0.95 * st->E;
+    double p = st->coin_floor + (1.0 - st->coin_floor) * st->E;
     double u = (double)w[0] * (1.0 / 4294967296.0);
     return u < p;
 }
@@ -646,8 +649,9 @@ int oracle_coin(const oracle_state *st)
  *   2. LD refinement of every point from the lists of t and Y_t;
  *   3. forces with the new lists, P and Y_t, Zhat_t;
  *   4. g = att * exag * A - rep * R; V = momentum V - lr g; Y += V;
- *      Zhat <- (1 - 0.1) Zhat + 0.1 Z_t; E <- (1 - 0.1) E + 0.1 N_new/N
- *      when the coin fired; t <- t + 1.
+ *      Zhat <- (1 - gamma_z) Zhat + gamma_z Z_t; E <- (1 - gamma_e) E +
+ *      gamma_e N_new/N when the coin fired (both rates 0.1 by default);
+ *      t <- t + 1.
  * A_out / R_out (N x d) receive the forces of step 3; flags (N bytes) the
  * new-neighbour flags; info[0] = coin, info[1] = N_new. z_out (N) receives
  * the per-point Z terms when non-NULL.
@@ -723,8 +727,8 @@ void oracle_step(oracle_state *st, double bisect_tol, int bisect_maxit, double *
         st->V[e] = jump ? 0.0 : st->momentum * st->V[e] - st->lr * g;
         st->Y[e] = st->Y[e] + st->V[e];
     }
-    st->Zhat = (1.0 - GAMMA_Z) * st->Zhat + GAMMA_Z * zt;
-    if (fire) st->E = (1.0 - GAMMA_E) * st->E + GAMMA_E * ((double)n_new / (double)N);
+    st->Zhat = (1.0 - st->gamma_z) * st->Zhat + st->gamma_z * zt;
+    if (fire) st->E = (1.0 - st->gamma_e) * st->E + st->gamma_e * ((double)n_new / (double)N);
     st->t += 1;
     info[0] = fire;
     info[1] = n_new;

@@ -46,7 +46,8 @@ class _State(C.Structure):
                 ("perplexity", C.c_double), ("seed", C.c_uint64), ("lr", C.c_double),
                 ("momentum", C.c_double), ("att_ratio", C.c_double), ("rep_ratio", C.c_double),
                 ("exaggeration", C.c_double), ("exag_iters", C.c_int32), ("hd_mode", C.c_int32),
-                ("neg_mode", C.c_int32), ("jump_iters", C.c_int32), ("jump_parts", C.c_int32), ("X", _dp), ("Y", _dp), ("V", _dp), ("hd_idx", _ip),
+                ("neg_mode", C.c_int32), ("jump_iters", C.c_int32), ("jump_parts", C.c_int32),
+                ("coin_floor", C.c_double), ("gamma_e", C.c_double), ("gamma_z", C.c_double), ("X", _dp), ("Y", _dp), ("V", _dp), ("hd_idx", _ip),
                 ("hd_d2", _dp), ("ld_idx", _ip), ("beta", _dp), ("P", _dp), ("Zhat", C.c_double),
                 ("E", C.c_double), ("t", C.c_uint32)]
 
@@ -264,7 +265,8 @@ class OracleState:
 
     def __init__(self, X, d, k_hd, k_ld, n_neg, alpha, perplexity, seed=0, lr=None,
                  momentum=0.8, att_ratio=1.0, rep_ratio=1.0, exaggeration=1.0, exag_iters=0,
-                 hd_mode=0, neg_mode=0, jump_iters=0, jump_parts=2, init=True):
+                 hd_mode=0, neg_mode=0, jump_iters=0, jump_parts=2, coin_floor=0.05, gamma_e=0.1,
+                 gamma_z=0.1, init=True):
         self.X = _f64(X)
         N, D = self.X.shape
         self.N, self.D = N, D
@@ -283,6 +285,7 @@ class OracleState:
         s.lr, s.momentum, s.att_ratio, s.rep_ratio = lr, momentum, att_ratio, rep_ratio
         s.exaggeration, s.exag_iters, s.hd_mode, s.neg_mode = exaggeration, exag_iters, hd_mode, neg_mode
         s.jump_iters, s.jump_parts = jump_iters, jump_parts
+        s.coin_floor, s.gamma_e, s.gamma_z = coin_floor, gamma_e, gamma_z
         self._s = s
         self._bind()
         if init:
@@ -302,8 +305,8 @@ class OracleState:
     # scalar state and options
     def __getattr__(self, name):
         if name in ("Zhat", "E", "t", "lr", "momentum", "att_ratio", "rep_ratio", "exaggeration",
-                    "exag_iters", "hd_mode", "neg_mode", "jump_iters", "jump_parts", "alpha", "perplexity", "seed", "n_neg",
-                    "k_hd", "k_ld", "d"):
+                    "exag_iters", "hd_mode", "neg_mode", "jump_iters", "jump_parts", "coin_floor", "gamma_e",
+                    "gamma_z", "alpha", "perplexity", "seed", "n_neg", "k_hd", "k_ld", "d"):
             return getattr(self.__dict__["_s"], name)
         raise AttributeError(name)
 

@@ -32,6 +32,7 @@ struct funcsne {
     // options
     double lr = 200.0, momentum = 0.8, att = 1.0, rep = 1.0, exaggeration = 1.0;
     int32_t exag_iters = 0, hd_mode = kHdAdaptive, precision = FUNCSNE_FP32;
+    double coin_floor = kCoinFloor, gamma_e = kGammaE, gamma_z = kGammaZ;
     // layout
     int32_t xpitch = 0, n4 = 0, xs_floats = 0, qpitch = 0, nq = 0, qscale_off = 0;
     int64_t yelem = 0;
@@ -147,6 +148,8 @@ StepParams step_params(const funcsne* h) {
     p.qpitch = h->qpitch;
     p.qscale_off = h->qscale_off;
     p.hd_mode = h->hd_mode;
+    p.coin_p0 = h->coin_floor;
+    p.coin_p1 = 1.0 - h->coin_floor;
     p.xs_floats = h->xs_floats;
     p.smem_per_warp = h->xs_floats * 4 + kHashSlots * 4;
     p.gf = hd_lanes_f32(h);
@@ -191,6 +194,10 @@ UpdateParams update_params(const funcsne* h, float* dbg_att, float* dbg_rep) {
     u.n_zpart = h->fo_blocks;
     u.n_cnt = h->hd_blocks;
     u.hd_mode = h->hd_mode;
+    u.coin_p0 = h->coin_floor;
+    u.coin_p1 = 1.0 - h->coin_floor;
+    u.gamma_e = h->gamma_e;
+    u.gamma_z = h->gamma_z;
     u.N = h->N;
     u.lr = h->frozen ? 0.f : static_cast<float>(h->lr);
     u.momentum = h->frozen ? 0.f : static_cast<float>(h->momentum);
@@ -731,6 +738,10 @@ int funcsne_set_option(funcsne_t* h, const char* key, double v) {
         const int m = static_cast<int>(v);
         if (m != v || m < 0 || m > 2) return fail(h, FUNCSNE_E_ARG, "hd_mode must be 0, 1 or 2");
         h->hd_mode = m;
+    } else if (k == "coin_floor" || k == "gamma_e" || k == "gamma_z") {
+        if (!(v >= 0 && v <= 1) || (k != "coin_floor" && v == 0))
+            return fail(h, FUNCSNE_E_ARG, "%s must be in %s", key, k == "coin_floor" ? "[0, 1]" : "(0, 1]");
+        (k == "coin_floor" ? h->coin_floor : k == "gamma_e" ? h->gamma_e : h->gamma_z) = v;
     } else if (k == "alpha") {
         if (!(v > 0)) return fail(h, FUNCSNE_E_ARG, "alpha must be > 0");
         h->alpha = static_cast<float>(v);
@@ -801,6 +812,9 @@ int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
     else if (k == "exaggeration") *v = h->exaggeration;
     else if (k == "exag_iters") *v = h->exag_iters;
     else if (k == "hd_mode") *v = h->hd_mode;
+    else if (k == "coin_floor") *v = h->coin_floor;
+    else if (k == "gamma_e") *v = h->gamma_e;
+    else if (k == "gamma_z") *v = h->gamma_z;
     else if (k == "alpha") *v = h->alpha;
     else if (k == "precision") *v = h->precision;
     else if (k == "concurrent") *v = h->concurrent ? 1 : 0;
@@ -1295,6 +1309,7 @@ int funcsne_get_stats(const funcsne_t* hc, funcsne_stats_t* st) {
     st->cand_scored = static_cast<int64_t>(s.cand_scored);
     st->cand_reranked = static_cast<int64_t>(s.cand_reranked);
     st->mlp_steps = h->mlp_steps;
+    st->n_refined = static_cast<int64_t>(s.n_refined);
     st->mlp_loss = 0.0;
     if (h->mlp.ready) {
         FSNE_CUDA(h, cudaMemcpyAsync(&st->mlp_loss, h->mlp.loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));

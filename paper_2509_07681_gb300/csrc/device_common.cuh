@@ -774,13 +774,14 @@ __device__ __forceinline__ uint32_t negative_word(uint32_t w1, uint32_t w3, uint
     return h;
 }
 
-// Coin of iteration t: HD refinement iff u < 0.05 + 0.95 E (FP64, explicit
-// rounding so host and device agree bit for bit).
-__device__ __forceinline__ bool hd_coin(uint32_t t, double E, uint64_t seed, int mode) {
+// Coin of iteration t: HD refinement iff u < p0 + p1 E, by default
+// p0 = 0.05 and p1 = 1 - p0 = 0.95 (Section 3). FP64 with explicit rounding
+// so host and device agree bit for bit.
+__device__ __forceinline__ bool hd_coin(uint32_t t, double E, uint64_t seed, int mode, double p0, double p1) {
     if (mode == kHdAlways) return true;
     if (mode == kHdNever) return false;
     const uint4 w = philox(t, 0u, kStreamCoin, 0u, seed);
-    const double p = __dadd_rn(0.05, __dmul_rn(0.95, E));
+    const double p = __dadd_rn(p0, __dmul_rn(p1, E));
     const double u = __dmul_rn(static_cast<double>(w.x), 2.3283064365386962890625e-10);
     return u < p;
 }

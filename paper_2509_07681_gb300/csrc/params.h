@@ -31,8 +31,11 @@ constexpr int kCand = 32;
 constexpr int kHdNnEnd = 16, kHdLdNbEnd = 20, kHdLdNnEnd = 24;
 constexpr int kLdNnEnd = 16, kLdHdNbEnd = 24;
 
-constexpr double kGammaE = 0.1;  // smoothing of E[N_new / N]
-constexpr double kGammaZ = 0.1;  // smoothing of the normalisation estimate
+// Defaults of the options coin_floor, gamma_e and gamma_z (the paper sets
+// the floor to 0.05 and leaves both smoothing rates open).
+constexpr double kCoinFloor = 0.05;  // refinement probability when E = 0
+constexpr double kGammaE = 0.1;     // smoothing of E[N_new / N]
+constexpr double kGammaZ = 0.1;     // smoothing of the normalisation estimate
 constexpr double kInitYStd = 1e-4;
 
 constexpr float kBisectTol = 1e-5f;  // |H - ln perp| in FP32
@@ -57,6 +60,7 @@ struct DevScalars {
     unsigned long long cand_reranked;
     uint32_t err;        // error bits
     uint32_t ticket;     // last-block detection of the update kernel
+    unsigned long long n_refined;  // iterations whose coin fired (cumulative)
 };
 
 constexpr uint32_t kErrNonFinite = 1u;
@@ -81,6 +85,7 @@ struct StepParams {
     int32_t qpitch;      // bytes per quantised row
     int32_t qscale_off;  // byte offset of the FP8 row scale / the BF16 row-norm bound
     int32_t hd_mode;
+    double coin_p0, coin_p1;  // refinement probability coin_p0 + coin_p1 E
     int32_t smem_per_warp;  // bytes
     int32_t xs_floats;      // own-row floats staged per warp
     int32_t gf, ga;         // lanes per row: FP32 rows, reduced-precision rows (1, 2, 4 or 8)
@@ -110,6 +115,8 @@ struct UpdateParams {
     int32_t n_zpart;      // blocks of the forces kernel (Z partials)
     int32_t n_cnt;        // blocks of the HD refinement kernel (counters)
     int32_t hd_mode;
+    double coin_p0, coin_p1;  // refinement probability coin_p0 + coin_p1 E
+    double gamma_e, gamma_z;  // smoothing of E and of the normalisation estimate
     int64_t N;
     float lr, momentum, att, rep, exaggeration;
     int32_t exag_iters;

@@ -72,7 +72,7 @@ hd_refine_kernel(const StepParams p) {
 
     const DevScalars* sc = p.sc;
     const uint32_t t = sc->t;
-    if (!hd_coin(t, sc->E, p.seed, p.hd_mode)) return;  // uniform over the grid
+    if (!hd_coin(t, sc->E, p.seed, p.hd_mode, p.coin_p0, p.coin_p1)) return;  // uniform over the grid
     const ListView L = list_view(p, sc->hd_cur, sc->ld_cur);
     const uint32_t N = static_cast<uint32_t>(p.N);
     const int k_hd = p.k_hd, k_ld = p.k_ld;
@@ -401,7 +401,7 @@ forces_kernel(const StepParams p) {
 
     const DevScalars* sc = p.sc;
     const uint32_t t = sc->t;
-    const bool fire = hd_coin(t, sc->E, p.seed, p.hd_mode);
+    const bool fire = hd_coin(t, sc->E, p.seed, p.hd_mode, p.coin_p0, p.coin_p1);
     // lists of iteration t+1: the HD buffer flips only when the coin fired
     const int32_t* __restrict__ hd_new = (sc->hd_cur ^ (fire ? 1 : 0)) ? p.hd_idx1 : p.hd_idx0;
     const int32_t* __restrict__ ld_new = sc->ld_cur ? p.ld_idx0 : p.ld_idx1;

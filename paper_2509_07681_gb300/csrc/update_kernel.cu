@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) update_kernel(const UpdateParams u) {
         double z = 0.0;
         unsigned long long nn = 0, ns = 0, nr = 0;
         const DevScalars* s0 = u.sc;
-        const bool fired = hd_coin(t, s0->E, u.seed, u.hd_mode);
+        const bool fired = hd_coin(t, s0->E, u.seed, u.hd_mode, u.coin_p0, u.coin_p1);
         for (int b = threadIdx.x; b < u.n_zpart; b += 32) z += u.zpart[b];
         if (fired)
             for (int b = threadIdx.x; b < u.n_cnt; b += 32) {
@@ -68,13 +68,14 @@ __global__ void __launch_bounds__(256) update_kernel(const UpdateParams u) {
         }
         if (threadIdx.x == 0) {
             DevScalars* s = u.sc;
-            const bool fire = hd_coin(t, s->E, u.seed, u.hd_mode);
+            const bool fire = hd_coin(t, s->E, u.seed, u.hd_mode, u.coin_p0, u.coin_p1);
             s->last_Z = z;
-            s->Zhat = __dadd_rn(__dmul_rn(1.0 - kGammaZ, s->Zhat), __dmul_rn(kGammaZ, z));
+            s->Zhat = __dadd_rn(__dmul_rn(__dsub_rn(1.0, u.gamma_z), s->Zhat), __dmul_rn(u.gamma_z, z));
             if (fire) {
                 const double frac = __ddiv_rn(static_cast<double>(nn), static_cast<double>(u.N));
-                s->E = __dadd_rn(__dmul_rn(1.0 - kGammaE, s->E), __dmul_rn(kGammaE, frac));
+                s->E = __dadd_rn(__dmul_rn(__dsub_rn(1.0, u.gamma_e), s->E), __dmul_rn(u.gamma_e, frac));
                 s->hd_cur ^= 1;
+                s->n_refined += 1;
             }
             s->ld_cur ^= 1;
             s->last_coin = fire ? 1 : 0;

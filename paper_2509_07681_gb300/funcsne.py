@@ -43,7 +43,8 @@ class Stats(C.Structure):
     _fields_ = [("N", C.c_int64), ("t", C.c_uint32), ("E", C.c_double), ("Zhat", C.c_double),
                 ("last_Z", C.c_double), ("last_n_new", C.c_int64), ("last_coin", C.c_int32),
                 ("precision", C.c_int32), ("error_word", C.c_uint32), ("cand_scored", C.c_int64),
-                ("cand_reranked", C.c_int64), ("mlp_steps", C.c_int64), ("mlp_loss", C.c_double)]
+                ("cand_reranked", C.c_int64), ("mlp_steps", C.c_int64), ("mlp_loss", C.c_double),
+                ("n_refined", C.c_int64)]
 
 
 class MlpDebug(C.Structure):
@@ -430,7 +431,7 @@ class FuncSNE:
     CHECKPOINT_OPTIONS = ("lr", "momentum", "att_ratio", "rep_ratio", "exaggeration", "exag_iters", "hd_mode",
                           "precision", "alpha", "perplexity", "concurrent", "surrogate", "mlp_every", "mlp_lr",
                           "mlp_batch", "mlp_hidden", "forces_cw", "hd_lanes", "insert_rounds",
-                          "jump_iters", "jump_parts")
+                          "jump_iters", "jump_parts", "coin_floor", "gamma_e", "gamma_z")
 
     def save(self, path):
         """Checkpoint: HD rows, the exported iteration state, the creation

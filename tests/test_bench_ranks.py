@@ -84,6 +84,8 @@ def test_bench_args_and_bytes():
     import bench
     a = bench.parse_args(["--workload", "lowrank-2m", "--alpha", "0.5"])
     assert a.workload == "lowrank-2m" and a.alpha == 0.5 and a.mode == "bench"
+    a = bench.parse_args(["--mode", "timing", "--sizes", "1000,2000", "--iters", "30"])
+    assert a.mode == "timing" and a.sizes == "1000,2000" and a.iters == 30
     per = bench.algorithmic_bytes_per_point(50, 16, 32, 32, 32, 200)
     # 33 FP32 rows of D = 50 dominate HD refinement
     assert per["hd_refine"] == 33 * 200 + 8 * 32 + 4 * 32 + 80 + 8 * 32

@@ -211,6 +211,36 @@ def test_adaptive_coin_and_smoothing_match_oracle():
     m.close()
 
 
+def test_coin_floor_and_smoothing_options_match_oracle():
+    """Adaptive refinement with a non-default floor and smoothing rates: the
+    coin, E (integer counts, FP64 with explicit rounding) and Zhat follow the
+    oracle from the same state."""
+    X = synth.blobs(n=1500, dim=30, seed=12)
+    p = dict(d=2, k_hd=16, k_ld=8, n_neg=8, alpha=1.0, perplexity=8.0)
+    opts = dict(coin_floor=0.3, gamma_e=0.25, gamma_z=0.5)
+    m = _make(X, p, **opts)
+    for k, v in opts.items():
+        assert m.get_option(k) == v
+    m.step(30)
+    coins = []
+    for _ in range(6):
+        st = m.export_state()
+        o = oracle_from_state(X, st, p, **opts)
+        m.step(1)
+        s = m.stats()
+        out = o.step()
+        assert s["last_coin"] == int(out["coin"])
+        coins.append(out["coin"])
+        st1 = m.export_state()
+        if s["last_n_new"] == out["n_new"]:
+            assert st1["E"] == o.E
+        assert abs(st1["Zhat"] - o.Zhat) <= 1e-4 * o.Zhat
+    for k, v in (("coin_floor", 1.5), ("gamma_e", 0.0), ("gamma_z", -0.1)):
+        with pytest.raises(F.FuncSNEError):
+            m.set_option(k, v)
+    m.close()
+
+
 def test_exact_knn_matches_bruteforce():
     X = synth.spectrum(n=5000, dim=50, n_clusters=8, seed=11)
     with _make(X, CASES["spectrum-shape"][1]) as m:

@@ -342,6 +342,41 @@ def test_coin_probability_follows_smoothed_fraction():
     assert all(st.coin() for _ in range(3))
 
 
+def test_coin_floor_sets_the_refinement_probability():
+    """Floor f: the coin fires with probability f + (1 - f) E; f = 1 always
+    fires and f = 0 with E = 0 never does."""
+    st = _state(N=50, coin_floor=0.3)
+    st.set(E=0.5)
+    fired = 0
+    for t in range(4000):
+        st.set(t=t)
+        fired += st.coin()
+    # p = 0.65, standard error 0.0075
+    assert abs(fired / 4000 - 0.65) < 0.03
+    st.set(coin_floor=0.0, E=0.0)
+    assert not any(st.set(t=t) or st.coin() for t in range(2000))
+    st.set(coin_floor=1.0)
+    assert all(st.set(t=t) or st.coin() for t in range(2000))
+
+
+@pytest.mark.parametrize("gamma_e,gamma_z", [(1.0, 0.5), (0.5, 1.0)])
+def test_smoothing_rates_reach_the_last_values(gamma_e, gamma_z):
+    """A rate of 1 keeps only the last value: E becomes the step's fraction
+    of points with new HD neighbours, and with exhaustive negatives Zhat
+    becomes the exact sum of w over all ordered pairs at the step's starting
+    embedding. The other rate (0.5) averages old and new halves."""
+    X = synth.blobs(n=200, dim=6, n_clusters=3, seed=62)
+    st = O.OracleState(X, 2, 10, 6, 4, 0.8, 5.0, seed=62, neg_mode=1, hd_mode=1, gamma_e=gamma_e,
+                       gamma_z=gamma_z)
+    for _ in range(4):
+        Y0, E0, Z0 = st.Y.copy(), st.E, st.Zhat
+        out = st.step()
+        frac, z = out["n_new"] / 200, O.exact_z(Y0, 0.8)
+        assert out["coin"]
+        assert st.E == pytest.approx(frac if gamma_e == 1 else 0.5 * (E0 + frac), rel=1e-15, abs=0)
+        assert st.Zhat == pytest.approx(z if gamma_z == 1 else 0.5 * (Z0 + z), rel=1e-10)
+
+
 def test_whole_run_finds_neighbours_and_structure():
     """Approximate method: statistics only. A short run on Gaussian blobs must
     reach high HD-KNN recall and an embedding that keeps the clusters
