@@ -265,6 +265,25 @@ int funcsne_mlp_debug_step(funcsne_t *h, funcsne_mlp_debug_t *out);
 int funcsne_get_embedding(const funcsne_t *h, float *Y_out, int64_t cap_rows);
 
 /*
+ * funcsne_get_embedding_async -- read the embedding out without waiting, for
+ * a viewer that shows each iteration while the next ones run (Section 3:
+ * the method suits interactive visualisation). The embedding as left by the
+ * steps queued so far is snapshotted on the device (stream-ordered on the
+ * handle's stream), then copied to the first min(N, cap_rows) x d entries
+ * of Y_out on an internal stream, so steps queued afterwards run during the
+ * copy. Y_out (host or device) must stay valid and unread until
+ * funcsne_wait_embedding or funcsne_sync returns; with pageable host memory
+ * the call itself waits for the copy (pinned memory overlaps). One snapshot
+ * buffer: a second call waits on the device for the first copy to finish
+ * before it overwrites the snapshot. Errors: FUNCSNE_E_ARG, FUNCSNE_E_OOM,
+ * FUNCSNE_E_CUDA.
+ */
+int funcsne_get_embedding_async(funcsne_t *h, float *Y_out, int64_t cap_rows);
+
+/* Wait until the copy of the last funcsne_get_embedding_async has landed. */
+int funcsne_wait_embedding(funcsne_t *h);
+
+/*
  * funcsne_scale_embedding -- multiply Y and V by factor (> 0), then
  * re-estimate Zhat at the scaled embedding (negatives from Philox counter
  * (t, i, 9, s)). Section 3's "implosion": a layout that keeps spreading makes

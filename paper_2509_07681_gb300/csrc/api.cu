@@ -51,6 +51,12 @@ struct funcsne {
     // execution
     cudaStream_t own_stream = nullptr;
     cudaStream_t side_stream = nullptr;  // second branch of the captured iteration
+    // asynchronous read-out of the embedding: a device snapshot of Y, copied
+    // out on copy_stream while the next iterations run
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t snap_ev = nullptr, copy_ev = nullptr;
+    float* Ysnap = nullptr;
+    int64_t snap_rows = 0;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     bool concurrent = false;  // run the two refinements side by side in the graph
     int32_t forces_cw = 8;    // floats of an LD row per lane in the forces kernel
@@ -314,13 +320,52 @@ int read_scalars(funcsne* h, DevScalars* out) {
     return FUNCSNE_OK;
 }
 
+bool is_device_memory(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy `rows` rows of `cols` 4-byte elements between arrays of pitches
+// dst_pitch and src_pitch (elements), either side in host or device memory.
+// The copy engines move a pitched copy to or from host memory row by row:
+// rows of a few hundred bytes go at about 7 GB/s, one contiguous block at
+// about 200 GB/s (pinned memory, GB300). So a pitched copy with a host side
+// goes through a contiguous device staging buffer (stream-ordered
+// allocation) and the repacking kernel.
+cudaError_t copy_rows_raw(void* dst, size_t dst_pitch, const void* src, size_t src_pitch, int64_t rows, size_t cols,
+                          cudaStream_t s) {
+    if (rows <= 0 || cols == 0) return cudaSuccess;
+    const size_t bytes = static_cast<size_t>(rows) * cols * 4;
+    if (dst_pitch == cols && src_pitch == cols) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+    const bool dd = is_device_memory(dst), sd = is_device_memory(src);
+    if (dd && sd) return launch_repack_rows(dst, dst_pitch, src, src_pitch, rows, cols, s);
+    if (!dd && !sd)
+        return cudaMemcpy2DAsync(dst, dst_pitch * 4, src, src_pitch * 4, cols * 4, static_cast<size_t>(rows),
+                                 cudaMemcpyDefault, s);
+    void* stage = nullptr;
+    cudaError_t e = cudaMallocAsync(&stage, bytes, s);
+    if (e != cudaSuccess) return e;
+    if (sd) {
+        e = launch_repack_rows(stage, cols, src, src_pitch, rows, cols, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyDefault, s);
+    } else {
+        e = cudaMemcpyAsync(stage, src, bytes, cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = launch_repack_rows(dst, dst_pitch, stage, cols, rows, cols, s);
+    }
+    const cudaError_t e2 = cudaFreeAsync(stage, s);
+    return e != cudaSuccess ? e : e2;
+}
+
 // Copy an N x cols row-major array between a caller buffer (pitch cols) and
 // a device array of pitch `dpitch` elements.
 template <typename T>
 int copy_rows(funcsne* h, T* dst, size_t dst_pitch, const T* src, size_t src_pitch, int64_t rows, size_t cols) {
-    if (rows <= 0) return FUNCSNE_OK;
-    FSNE_CUDA(h, cudaMemcpy2DAsync(dst, dst_pitch * sizeof(T), src, src_pitch * sizeof(T), cols * sizeof(T),
-                                   static_cast<size_t>(rows), cudaMemcpyDefault, h->stream));
+    static_assert(sizeof(T) == 4, "rows of 4-byte elements");
+    FSNE_CUDA(h, copy_rows_raw(dst, dst_pitch, src, src_pitch, rows, cols, h->stream));
     return FUNCSNE_OK;
 }
 
@@ -351,6 +396,11 @@ void free_all(funcsne* h) {
                     static_cast<void*>(q.G2), static_cast<void*>(q.G1), static_cast<void*>(q.part),
                     static_cast<void*>(q.loss), static_cast<void*>(q.step)})
         cudaFree(p);
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+    cudaFree(h->Ysnap);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->snap_ev) cudaEventDestroy(h->snap_ev);
+    if (h->copy_ev) cudaEventDestroy(h->copy_ev);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     if (h->side_stream) cudaStreamDestroy(h->side_stream);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
@@ -646,8 +696,7 @@ int funcsne_create(const float* X, int64_t N, int32_t D, int32_t d, int32_t k_hd
     CREATE_CUDA(dalloc(&h->cnt, 3 * static_cast<size_t>(h->max_blocks) + 3));
     cudaStream_t s = h->stream;
     CREATE_CUDA(cudaMemsetAsync(h->X32, 0, static_cast<size_t>(N) * h->xpitch * sizeof(float), s));
-    CREATE_CUDA(cudaMemcpy2DAsync(h->X32, h->xpitch * sizeof(float), X, D * sizeof(float), D * sizeof(float),
-                                  static_cast<size_t>(N), cudaMemcpyDefault, s));
+    CREATE_CUDA(copy_rows_raw(h->X32, h->xpitch, X, D, N, D, s));
     CREATE_CUDA(cudaMemsetAsync(h->Y, 0, h->yelem * sizeof(float), s));
     CREATE_CUDA(cudaMemsetAsync(h->V, 0, h->yelem * sizeof(float), s));
     CREATE_CUDA(cudaMemsetAsync(h->A, 0, h->yelem * sizeof(float), s));
@@ -942,10 +991,10 @@ int funcsne_mlp_predict(const funcsne_t* hc, const float* X, int64_t n, float* Y
     if (e == cudaSuccess) e = dalloc(&yd, static_cast<size_t>(n) * h->DP);
     if (e == cudaSuccess) e = cudaMemsetAsync(xd, 0, static_cast<size_t>(n) * h->xpitch * 4, h->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(xd, h->xpitch * 4, X, h->D * 4, h->D * 4, static_cast<size_t>(n), cudaMemcpyDefault, h->stream);
+        e = copy_rows_raw(xd, h->xpitch, X, h->D, n, h->D, h->stream);
     if (e == cudaSuccess) e = launch_mlp_place(mlp_params(h), xd, h->xpitch, 0, n, yd, h->DP, h->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(Y_out, h->d * 4, yd, h->DP * 4, h->d * 4, static_cast<size_t>(n), cudaMemcpyDefault, h->stream);
+        e = copy_rows_raw(Y_out, h->d, yd, h->DP, n, h->d, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(xd);
     cudaFree(yd);
@@ -1004,6 +1053,7 @@ int funcsne_mlp_debug_step(funcsne_t* h, funcsne_mlp_debug_t* out) {
 int funcsne_sync(funcsne_t* h) {
     if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
     FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->copy_stream) FSNE_CUDA(h, cudaStreamSynchronize(h->copy_stream));
     FSNE_CUDA(h, cudaGetLastError());
     return check_errors(h);
 }
@@ -1024,8 +1074,7 @@ int funcsne_insert(funcsne_t* h, const float* X_new, int64_t n_new, int32_t plac
         if ((rc = grow(h, nc))) return rc;
     }
     float* xdst = h->X32 + n_old * h->xpitch;
-    FSNE_CUDA(h, cudaMemcpy2DAsync(xdst, h->xpitch * sizeof(float), X_new, h->D * sizeof(float),
-                                   h->D * sizeof(float), static_cast<size_t>(n_new), cudaMemcpyDefault, h->stream));
+    FSNE_CUDA(h, copy_rows_raw(xdst, h->xpitch, X_new, h->D, n_new, h->D, h->stream));
     FSNE_CUDA(h, launch_check_finite(xdst, n_new * h->xpitch, &h->sc->err, h->stream));
     {
         DevScalars chk;
@@ -1228,6 +1277,41 @@ int funcsne_get_embedding(const funcsne_t* hc, float* Y_out, int64_t cap_rows) {
     int rc = copy_rows<float>(h, Y_out, h->d, h->Y, h->DP, rows, h->d);
     if (rc) return rc;
     FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return FUNCSNE_OK;
+}
+
+int funcsne_get_embedding_async(funcsne_t* h, float* Y_out, int64_t cap_rows) {
+    if (!h || !Y_out) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    const int64_t rows = cap_rows < h->N ? cap_rows : h->N;
+    if (rows <= 0) return FUNCSNE_OK;
+    if (!h->copy_stream) {
+        FSNE_CUDA(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        FSNE_CUDA(h, cudaEventCreateWithFlags(&h->snap_ev, cudaEventDisableTiming));
+        FSNE_CUDA(h, cudaEventCreateWithFlags(&h->copy_ev, cudaEventDisableTiming));
+    }
+    if (rows > h->snap_rows) {
+        // the old snapshot may still be in flight
+        FSNE_CUDA(h, cudaStreamSynchronize(h->copy_stream));
+        cudaFree(h->Ysnap);
+        h->Ysnap = nullptr;
+        h->snap_rows = 0;
+        FSNE_CUDA(h, dalloc(&h->Ysnap, static_cast<size_t>(h->cap) * h->d));
+        h->snap_rows = h->cap;
+    }
+    // the snapshot is overwritten only after the previous copy out of it
+    FSNE_CUDA(h, cudaStreamWaitEvent(h->stream, h->copy_ev, 0));
+    FSNE_CUDA(h, copy_rows_raw(h->Ysnap, h->d, h->Y, h->DP, rows, h->d, h->stream));
+    FSNE_CUDA(h, cudaEventRecord(h->snap_ev, h->stream));
+    FSNE_CUDA(h, cudaStreamWaitEvent(h->copy_stream, h->snap_ev, 0));
+    FSNE_CUDA(h, cudaMemcpyAsync(Y_out, h->Ysnap, static_cast<size_t>(rows) * h->d * sizeof(float),
+                                 cudaMemcpyDefault, h->copy_stream));
+    FSNE_CUDA(h, cudaEventRecord(h->copy_ev, h->copy_stream));
+    return FUNCSNE_OK;
+}
+
+int funcsne_wait_embedding(funcsne_t* h) {
+    if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
+    if (h->copy_ev) FSNE_CUDA(h, cudaEventSynchronize(h->copy_ev));
     return FUNCSNE_OK;
 }
 

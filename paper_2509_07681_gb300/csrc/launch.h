@@ -91,6 +91,9 @@ cudaError_t launch_quantize(const float* X32, int64_t N, int D, int xpitch, int 
 cudaError_t launch_check_lists(const int32_t* idx, int64_t N, int k, uint32_t* err, cudaStream_t s);
 cudaError_t launch_check_finite(const float* X, int64_t n, uint32_t* err, cudaStream_t s);
 // live changes of the point set (live_kernels.cu)
+// dst[r, c] = src[r, c] for r < rows, c < cols; pitches in 4-byte words.
+cudaError_t launch_repack_rows(void* dst, int64_t dpitch, const void* src, int64_t spitch, int64_t rows,
+                               int64_t cols, cudaStream_t s);
 cudaError_t launch_gather_rows(uint32_t* dst, const uint32_t* src, int64_t pitch, const int32_t* old,
                                int64_t n_rows, cudaStream_t s);
 cudaError_t launch_scatter_rows(float* X32, int xpitch, const int64_t* ids, const float* rows, int64_t n, int D,

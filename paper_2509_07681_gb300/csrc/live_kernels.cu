@@ -20,6 +20,17 @@ __global__ void gather_rows_kernel(uint32_t* __restrict__ dst, const uint32_t* _
     }
 }
 
+// dst[r, 0..cols) = src[r, 0..cols) (4-byte words): one warp per row, the
+// lanes over the columns; the padding columns of dst are not touched.
+__global__ void repack_rows_kernel(uint32_t* __restrict__ dst, int64_t dpitch, const uint32_t* __restrict__ src,
+                                   int64_t spitch, int64_t rows, int64_t cols) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t r = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows;
+         r += warps)
+        for (int64_t c = lane; c < cols; c += 32) dst[r * dpitch + c] = src[r * spitch + c];
+}
+
 // X32[ids[r], 0..D) = rows[r, 0..D) (the padding columns stay zero).
 __global__ void scatter_rows_kernel(float* __restrict__ X32, int xpitch, const int64_t* __restrict__ ids,
                                     const float* __restrict__ rows, int64_t n, int D) {
@@ -95,6 +106,15 @@ cudaError_t launch_gather_rows(uint32_t* dst, const uint32_t* src, int64_t pitch
                                int64_t n_rows, cudaStream_t s) {
     if (n_rows <= 0) return cudaSuccess;
     gather_rows_kernel<<<grid_for(n_rows * pitch, 256), 256, 0, s>>>(dst, src, pitch, old, n_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_repack_rows(void* dst, int64_t dpitch, const void* src, int64_t spitch, int64_t rows,
+                               int64_t cols, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    repack_rows_kernel<<<grid_for(rows * 32, 256), 256, 0, s>>>(static_cast<uint32_t*>(dst), dpitch,
+                                                                static_cast<const uint32_t*>(src), spitch, rows,
+                                                                cols);
     return cudaGetLastError();
 }
 

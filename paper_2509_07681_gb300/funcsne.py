@@ -68,6 +68,8 @@ ABI_FUNCTIONS = {
     "funcsne_update_points": (C.c_int, [_h, _vp, C.c_int64, _vp]),
     "funcsne_remove": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_get_embedding": (C.c_int, [_h, _vp, C.c_int64]),
+    "funcsne_get_embedding_async": (C.c_int, [_h, _vp, C.c_int64]),
+    "funcsne_wait_embedding": (C.c_int, [_h]),
     "funcsne_get_data": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_scale_embedding": (C.c_int, [_h, C.c_float]),
     "funcsne_get_knn": (C.c_int, [_h, C.c_int32, _vp, _vp]),
@@ -183,6 +185,16 @@ def funcsne_remove(h, ids):
 
 def funcsne_scale_embedding(h, factor):
     _check(load().funcsne_scale_embedding(h, float(factor)), h)
+
+
+def funcsne_get_embedding_async(h, out):
+    p, keep = _ptr(out)
+    _check(load().funcsne_get_embedding_async(h, p, out.shape[0]), h)
+    return keep
+
+
+def funcsne_wait_embedding(h):
+    _check(load().funcsne_wait_embedding(h), h)
 
 
 def funcsne_get_data(h, out):
@@ -340,6 +352,17 @@ class FuncSNE:
         if out is None:
             out = np.empty((self.N, self.d), dtype=np.float32)
         return funcsne_get_embedding(self.h, out)
+
+    def embedding_async(self, out):
+        """Queue a read-out of the current embedding into `out` (N x d float32;
+        pinned host memory or a CUDA tensor for the copy to overlap the next
+        steps). `out` is valid after wait_embedding() or sync()."""
+        self._pending_out = funcsne_get_embedding_async(self.h, out)
+        return out
+
+    def wait_embedding(self):
+        funcsne_wait_embedding(self.h)
+        self._pending_out = None
 
     def knn(self, space=SPACE_HD, with_d2=True):
         k = self.k_hd if space == SPACE_HD else self.k_ld

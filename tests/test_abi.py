@@ -76,4 +76,6 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.funcsne_remove(None, ids.ctypes.data, 2) == -1
     assert lib.funcsne_update_points(None, ids.ctypes.data, 2, rows.ctypes.data) == -1
     assert lib.funcsne_get_data(None, rows.ctypes.data, 2) == -1
+    assert lib.funcsne_get_embedding_async(None, rows.ctypes.data, 2) == -1
+    assert lib.funcsne_wait_embedding(None) == -1
     lib.funcsne_destroy(None)

@@ -237,3 +237,37 @@ def test_alpha_annealing_snapshots():
     assert m.get_option("alpha") == 0.25
     assert all(np.isfinite(s).all() for s in snaps) and not np.array_equal(snaps[1], snaps[2])
     m.close()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_async_embedding_readout(d):
+    """get_embedding_async snapshots Y after the steps queued before it: the
+    copy equals a synchronous read taken at the same point, though more steps
+    run while it is in flight; back-to-back read-outs into two buffers (the
+    second waits on the device for the first) each hold their own step."""
+    import torch
+    X = synth.blobs(n=3000, dim=20, n_clusters=5, seed=58)
+    m = F.FuncSNE(X, d, 16, 8, 8, 1.0, 8.0, seed=0)
+    bufs = [torch.empty((3000, d), dtype=torch.float32).pin_memory() for _ in range(2)]
+    m.step(3)
+    m.embedding_async(bufs[0])
+    ref = m.embedding()
+    m.step(5)
+    m.wait_embedding()
+    np.testing.assert_array_equal(bufs[0].numpy(), ref)
+    assert not np.array_equal(m.embedding(), ref)
+    refs = []
+    for k in range(4):
+        m.step(1)
+        m.embedding_async(bufs[k % 2])
+        refs.append(m.embedding())
+        if k % 2:
+            m.wait_embedding()
+            np.testing.assert_array_equal(bufs[0].numpy(), refs[k - 1])
+            np.testing.assert_array_equal(bufs[1].numpy(), refs[k])
+    part = torch.zeros((100, d), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    m.embedding_async(part)
+    m.sync()
+    np.testing.assert_array_equal(part.cpu().numpy(), m.embedding()[:100])
+    m.close()
