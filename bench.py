@@ -95,8 +95,9 @@ def algorithmic_bytes_per_point(D, d, k_hd, k_ld, n_neg, row_bytes, rerank_rows=
 
 
 def row_bytes_of(D):
-    """Bytes of one HD row per storage precision (payload + its scale or norm)."""
-    return {"fp32": 4 * D, "bf16": 2 * D + 4, "fp8": D + 4}
+    """Bytes of one HD row per storage precision (payload + its error bound,
+    and the FP8 scale)."""
+    return {"fp32": 4 * D, "bf16": 2 * D + 4, "fp8": D + 8}
 
 
 def kernel_source_hash():

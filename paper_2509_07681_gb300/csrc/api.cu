@@ -167,13 +167,6 @@ StepParams step_params(const funcsne* h) {
     p.log_perp = std::log(h->perplexity);
     const float gamma = static_cast<float>((h->xs_floats + 4) * std::ldexp(1.0, -24) * 1.01);
     p.q_gamma = gamma;
-    if (h->precision == FUNCSNE_BF16) {
-        p.q_u = static_cast<float>(std::ldexp(1.0, -8) * (1.0 + std::ldexp(1.0, -20)));
-        p.q_a = 0.f;
-    } else {
-        p.q_u = static_cast<float>(std::ldexp(1.0, -4) * (1.0 + std::ldexp(1.0, -20)) + std::ldexp(1.0, -22));
-        p.q_a = static_cast<float>(std::ldexp(1.0, -10) * (1.0 + std::ldexp(1.0, -20)));
-    }
     p.seed = h->seed;
     p.X32 = h->X32;
     p.Xq = h->Xq;
@@ -415,13 +408,14 @@ int quantize(funcsne* h) {
         return FUNCSNE_OK;
     }
     if (h->precision == FUNCSNE_BF16) {
-        // data chunks, then a 16-byte chunk holding the row-norm bound
+        // data chunks, then a 16-byte chunk holding the row-error bound
         h->nq = (2 * h->D + 15) / 16;
         h->qscale_off = 16 * h->nq;
         h->qpitch = h->qscale_off + 16;
     } else {
+        // code words, then the row-error bound and the scale in the last 8 bytes
         const int nw = (h->D + 3) / 4;
-        h->qpitch = round_up(4 * nw + 4, 16);
+        h->qpitch = round_up(4 * nw + 8, 16);
         h->nq = nw;
         h->qscale_off = h->qpitch - 4;
     }

@@ -332,24 +332,18 @@ struct ApproxDist {
     float band;  // bound on |d2 - exact FP32 distance to the master row|
 };
 
-// Error term of one dequantised coordinate: |x - x~| <= u |x~| + a.
-// Accumulates s1 = sum |x_i - x~| e and s2 = sum e^2; the distance error is
-// at most 2 s1 + 3 s2 (expand (D - e)^2 - D^2 with |e| bounded).
-__device__ __forceinline__ void approx_acc(float xi, float xq, float u, float a, float& acc,
-                                           float& s1, float& s2) {
-    const float d = __fsub_rn(xi, xq);
-    acc = __fmaf_rn(d, d, acc);
-    const float e = __fmaf_rn(u, fabsf(xq), a);
-    s1 = __fmaf_rn(fabsf(d), e, s1);
-    s2 = __fmaf_rn(e, e, s2);
-}
-
-__device__ __forceinline__ ApproxDist finish_band(float acc, float s1, float s2, float gamma) {
-    // FP32 rounding of the three sums and of both distance evaluations.
-    const float b = (2.f * s1 + 3.f * s2) * (1.f + 2.f * gamma);
+// Band of a distance to a dequantised row. acc: the FP32 sum of
+// (x_i - x~_c)^2 with the own row x_i exact; E: an upper bound of the
+// candidate row's own dequantisation error ||x_c - x~_c||, stored with the
+// row when it was quantised. Expanding ||(x_i - x~_c) - (x_c - x~_c)||^2
+// and Cauchy-Schwarz give |d2 - d~2| <= 2 ||x_i - x~_c|| E + E^2; the terms
+// in gamma cover the FP32 rounding of this sum and of the exact FP32
+// distance it is compared with.
+__device__ __forceinline__ ApproxDist band_from_row_error(float acc, float E, float gamma) {
+    const float b0 = 2.f * sqrtf(acc * (1.f + gamma)) * E + E * E;
     ApproxDist r;
     r.d2 = acc;
-    r.band = b + gamma * (2.f * acc + b) * (1.f + 4.f * gamma) + 1e-30f;
+    r.band = b0 * (1.f + 4.f * gamma) + gamma * (2.f * acc + 2.f * b0) + 1e-30f;
     return r;
 }
 
@@ -360,10 +354,10 @@ __device__ __forceinline__ void fp8x4_to_float(uint32_t w, float s, float (&o)[4
     const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w >> 16), __NV_E4M3);
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
-    o[0] = a.x * s;
-    o[1] = a.y * s;
-    o[2] = b.x * s;
-    o[3] = b.y * s;
+    o[0] = __fmul_rn(a.x, s);
+    o[1] = __fmul_rn(a.y, s);
+    o[2] = __fmul_rn(b.x, s);
+    o[3] = __fmul_rn(b.y, s);
 }
 
 
@@ -535,16 +529,14 @@ __device__ __forceinline__ float bf16_chunk_acc(const float* __restrict__ xs, co
     return acc;
 }
 
-// BF16 rows by groups: the distance to the dequantised row and its band,
-// for the candidate of every lane. BF16 rows hold nq chunks of 8 values,
-// then a 16-byte chunk whose first four bytes hold an upper bound N_c of the
-// rounded row's norm. With |x_f - x~_f| <= u |x~_f|, ||e|| <= u N_c = E and
-// |d~2 - d2| <= 2 ||x_i - x~_c|| E + E^2 (Cauchy-Schwarz), plus the FP32
-// rounding of both distance evaluations.
+// BF16 rows by groups: the distance to the dequantised row and its band
+// (band_from_row_error), for the candidate of every lane. BF16 rows hold nq
+// chunks of 8 values, then a 16-byte chunk whose first four bytes hold the
+// row's error bound E_c >= ||x_c - x~_c||.
 template <int G, bool BATCH>
 __device__ __forceinline__ ApproxDist group_dist_bf16(const float* __restrict__ xs,
                                                       const uint8_t* __restrict__ Xq, int qpitch, int nq,
-                                                      uint32_t cv, int lane, float u, float gamma) {
+                                                      uint32_t cv, int lane, float gamma) {
     constexpr int R = 32 / G;
     const int g = lane / G, s = lane & (G - 1);
     const int sn = nq & (G - 1);  // the lane of a group that reads the norm chunk
@@ -586,34 +578,29 @@ __device__ __forceinline__ ApproxDist group_dist_bf16(const float* __restrict__ 
             my_nrm = vn;
         }
     }
-    const float E = u * my_nrm;
-    const float b0 = 2.f * sqrtf(my_acc * (1.f + gamma)) * E + E * E;
-    ApproxDist r;
-    r.d2 = my_acc;
-    r.band = b0 * (1.f + 4.f * gamma) + gamma * (2.f * my_acc + 2.f * b0) + 1e-30f;
-    return r;
+    return band_from_row_error(my_acc, my_nrm, gamma);
 }
 
-// FP8-E4M3 rows by groups: distance to the dequantised row and the
-// element-wise band (see approx_acc and finish_band), for the candidate of
-// every lane.
+// FP8-E4M3 rows by groups: distance to the dequantised row and its band
+// (band_from_row_error), for the candidate of every lane. FP8 rows hold nw
+// words of 4 codes, then the row's error bound E_c >= ||x_c - x~_c|| four
+// bytes before the scale (scale_off).
 template <int G>
 __device__ __forceinline__ ApproxDist group_dist_fp8(const float* __restrict__ xs,
                                                      const uint8_t* __restrict__ Xq, int qpitch, int nw,
-                                                     int scale_off, uint32_t cv, int lane, float u,
-                                                     float a_rel, float gamma) {
+                                                     int scale_off, uint32_t cv, int lane, float gamma) {
     constexpr int R = 32 / G;
     const int g = lane / G, s = lane & (G - 1);
     const int nch = (nw + 3) >> 2;
-    float my_acc = 0.f, my_s1 = 0.f, my_s2 = 0.f;
+    float my_acc = 0.f, my_err = 0.f;
 #pragma unroll
     for (int p = 0; p < G; ++p) {
         const uint32_t cj = __shfl_sync(kFull, cv, p * R + g);
-        float acc = 0.f, s1 = 0.f, s2 = 0.f;
+        float acc = 0.f, err = 0.f;
         if (cj != kNoRow) {
             const uint8_t* row = Xq + static_cast<int64_t>(cj) * qpitch;
             const float sc = __ldg(reinterpret_cast<const float*>(row + scale_off));
-            const float a = a_rel * sc;
+            if (s == 0) err = __ldg(reinterpret_cast<const float*>(row + scale_off - 4));
             const uint4* b = reinterpret_cast<const uint4*>(row);
             for (int q = s; q < nch; q += G) {
                 const uint4 raw = __ldg(b + q);
@@ -624,28 +611,28 @@ __device__ __forceinline__ ApproxDist group_dist_fp8(const float* __restrict__ x
                         float v[4];
                         fp8x4_to_float(w4[m], sc, v);
                         const float4 xi = reinterpret_cast<const float4*>(xs)[4 * q + m];
-                        approx_acc(xi.x, v[0], u, a, acc, s1, s2);
-                        approx_acc(xi.y, v[1], u, a, acc, s1, s2);
-                        approx_acc(xi.z, v[2], u, a, acc, s1, s2);
-                        approx_acc(xi.w, v[3], u, a, acc, s1, s2);
+                        float d = __fsub_rn(xi.x, v[0]);
+                        acc = __fmaf_rn(d, d, acc);
+                        d = __fsub_rn(xi.y, v[1]);
+                        acc = __fmaf_rn(d, d, acc);
+                        d = __fsub_rn(xi.z, v[2]);
+                        acc = __fmaf_rn(d, d, acc);
+                        d = __fsub_rn(xi.w, v[3]);
+                        acc = __fmaf_rn(d, d, acc);
                     }
                 }
             }
         }
         acc = group_sum_rt(acc, G);
-        s1 = group_sum_rt(s1, G);
-        s2 = group_sum_rt(s2, G);
         const int src = (lane & (R - 1)) * G;
         const float va = __shfl_sync(kFull, acc, src);
-        const float v1 = __shfl_sync(kFull, s1, src);
-        const float v2 = __shfl_sync(kFull, s2, src);
+        const float ve = __shfl_sync(kFull, err, src);
         if (lane / R == p) {
             my_acc = va;
-            my_s1 = v1;
-            my_s2 = v2;
+            my_err = ve;
         }
     }
-    return finish_band(my_acc, my_s1, my_s2, gamma);
+    return band_from_row_error(my_acc, my_err, gamma);
 }
 
 // ---------------------------------------------------------------- warp hash sets

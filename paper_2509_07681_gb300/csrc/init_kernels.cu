@@ -223,30 +223,42 @@ __global__ void zinit_finish_kernel(const double* part, int n, DevScalars* sc) {
     sc->last_Z = s;
 }
 
+// Upper bound, in FP32, of sqrt(s) for an FP64 sum s of D <= 4096 exact
+// squares: the relative margins 2^-40 cover the sum's and the square
+// root's rounding.
+__device__ __forceinline__ float sqrt_bound(double s) {
+    constexpr double kUp = 1.0 + 1.0 / 1099511627776.0;
+    return __double2float_ru(sqrt(s * kUp) * kUp);
+}
+
 // BF16 copy, one warp per row: round to nearest even, zero padding up to
-// `norm_off`, then an upper bound of the rounded row's norm (FP64 sum,
-// rounded up to FP32) at byte `norm_off`.
+// `err_off`, then at byte `err_off` a bound E >= ||x - x~|| of the row's own
+// rounding error. Each difference of an FP32 value and its BF16 rounding is
+// exact in FP64, and so is its square.
 __global__ void quantize_bf16_kernel(const float* __restrict__ X, int64_t N, int D, int xpitch,
-                                     int qpitch, int norm_off, uint8_t* Q) {
+                                     int qpitch, int err_off, uint8_t* Q) {
     const int lane = threadIdx.x & 31;
     const int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= N) return;
     __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Q + i * qpitch);
     double s = 0.0;
-    for (int f = lane; f < norm_off / 2; f += 32) {
-        const __nv_bfloat16 b = __float2bfloat16_rn(f < D ? X[i * xpitch + f] : 0.f);
+    for (int f = lane; f < err_off / 2; f += 32) {
+        const float x = f < D ? X[i * xpitch + f] : 0.f;
+        const __nv_bfloat16 b = __float2bfloat16_rn(x);
         row[f] = b;
-        const double v = __bfloat162float(b);
-        s += v * v;
+        const double e = static_cast<double>(x) - static_cast<double>(__bfloat162float(b));
+        s += e * e;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    if (lane == 0) *reinterpret_cast<float*>(Q + i * qpitch + norm_off) = __double2float_ru(sqrt(s));
+    if (lane == 0) *reinterpret_cast<float*>(Q + i * qpitch + err_off) = sqrt_bound(s);
 }
 
 // FP8-E4M3 copy with per-row scale s = max|x| / 448 (s = 1 for a zero row),
-// codes = RNE(x / s) (saturating), zero codes up to byte scale_off, and the
-// scale in the row's last four bytes (scale_off = pitch - 4).
+// codes = RNE(x / s) (saturating), zero codes up to byte scale_off - 4, the
+// bound E >= ||x - x~|| of the row's own error at scale_off - 4 and the
+// scale at scale_off (the row's last eight bytes). x~ is decoded by
+// fp8x4_to_float, the same FP32 arithmetic as the distance kernels use.
 __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t N, int D, int xpitch,
                                     int qpitch, int scale_off, uint8_t* Q) {
     const int lane = threadIdx.x & 31;
@@ -258,11 +270,33 @@ __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t N, int 
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
     const float s = m > 0.f ? m / 448.f : 1.f;
     uint8_t* row = Q + i * qpitch;
-    for (int f = lane; f < scale_off; f += 32) {
-        const float v = f < D ? X[i * xpitch + f] / s : 0.f;
-        row[f] = static_cast<uint8_t>(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
+    const int err_off = scale_off - 4;
+    double es = 0.0;
+    for (int w = lane; w < err_off / 4; w += 32) {
+        float x[4];
+        uint32_t word = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int f = 4 * w + k;
+            x[k] = f < D ? X[i * xpitch + f] : 0.f;
+            const uint32_t c = __nv_cvt_float_to_fp8(x[k] / s, __NV_SATFINITE, __NV_E4M3);
+            word |= c << (8 * k);
+        }
+        *reinterpret_cast<uint32_t*>(row + 4 * w) = word;
+        float v[4];
+        fp8x4_to_float(word, s, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double e = static_cast<double>(x[k]) - static_cast<double>(v[k]);
+            es += e * e;
+        }
     }
-    if (lane == 0) *reinterpret_cast<float*>(row + scale_off) = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) es += __shfl_xor_sync(kFull, es, o);
+    if (lane == 0) {
+        *reinterpret_cast<float*>(row + err_off) = sqrt_bound(es);
+        *reinterpret_cast<float*>(row + scale_off) = s;
+    }
 }
 
 // Import check: every list entry in [0, N), not the point itself, distinct.

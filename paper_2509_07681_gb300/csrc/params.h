@@ -83,14 +83,14 @@ struct StepParams {
     int32_t xpitch;      // floats per FP32 row
     int32_t nq;          // BF16: 16-byte chunks per row; FP8: 4-byte code words per row
     int32_t qpitch;      // bytes per quantised row
-    int32_t qscale_off;  // byte offset of the FP8 row scale / the BF16 row-norm bound
+    int32_t qscale_off;  // byte offset of the FP8 row scale (error bound 4 bytes before) / the BF16 row-error bound
     int32_t hd_mode;
     double coin_p0, coin_p1;  // refinement probability coin_p0 + coin_p1 E
     int32_t smem_per_warp;  // bytes
     int32_t xs_floats;      // own-row floats staged per warp
     int32_t gf, ga;         // lanes per row: FP32 rows, reduced-precision rows (1, 2, 4 or 8)
     float alpha, inv_alpha, inv2N, neg_scale, log_perp;
-    float q_u, q_a, q_gamma;  // dequantisation error model (see dist_bf16 / dist_fp8)
+    float q_gamma;          // relative FP32 rounding bound of a distance evaluation
     uint64_t seed;
     const float* X32;
     const uint8_t* Xq;

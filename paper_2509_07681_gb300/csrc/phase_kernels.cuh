@@ -128,10 +128,9 @@ hd_refine_kernel(const StepParams p) {
             ApproxDist a;
             if constexpr (XM == 1)
                 // batched loads pay off with the 64 registers of the k_hd > 32 variant
-                a = group_dist_bf16<G, RH == 2>(xs, p.Xq, p.qpitch, p.nq, cv, lane, p.q_u, p.q_gamma);
+                a = group_dist_bf16<G, RH == 2>(xs, p.Xq, p.qpitch, p.nq, cv, lane, p.q_gamma);
             else  // nq = code words for FP8
-                a = group_dist_fp8<G>(xs, p.Xq, p.qpitch, p.nq, p.qscale_off, cv, lane, p.q_u, p.q_a,
-                                      p.q_gamma);
+                a = group_dist_fp8<G>(xs, p.Xq, p.qpitch, p.nq, p.qscale_off, cv, lane, p.q_gamma);
             const bool need = valid && __fsub_rd(a.d2, a.band) <= thr;
             c_scored += valid ? 1 : 0;
             c_rerank += need ? 1 : 0;

@@ -90,4 +90,4 @@ def test_bench_args_and_bytes():
     # 33 FP32 rows of D = 50 dominate HD refinement
     assert per["hd_refine"] == 33 * 200 + 8 * 32 + 4 * 32 + 80 + 8 * 32
     assert per["update"] == 7 * 64
-    assert bench.row_bytes_of(50) == {"fp32": 200, "bf16": 104, "fp8": 54}
+    assert bench.row_bytes_of(50) == {"fp32": 200, "bf16": 104, "fp8": 58}
