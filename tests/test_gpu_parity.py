@@ -164,6 +164,41 @@ def test_reduced_precision_sets_equal_fp32(precision, dim, k_hd):
     m.close()
 
 
+@pytest.mark.parametrize("precision", [F.BF16, F.FP8])
+def test_reduced_precision_bands_hold_on_hard_rows(precision):
+    """Rows that stress the stored rounding-error bound: a large common
+    offset (every candidate falls inside its band and is re-ranked), one
+    huge coordinate per row (the FP8 scale pushes the other values towards
+    subnormal codes), values halfway between BF16 neighbours (rounding ties)
+    and identical all-zero rows (distance-0 ties broken by index). The sets
+    and distances still equal the FP32 path's bit for bit."""
+    rng = np.random.default_rng(71)
+    n, D = 3000, 40
+    X = synth.blobs(n=n, dim=D, n_clusters=6, seed=71)
+    X[: n // 3] += 1000.0
+    X[n // 3: 2 * n // 3, 0] = (1e4 * (1.0 + rng.random(n // 3))).astype(np.float32)
+    ties = 1.0 + (2 * rng.integers(0, 64, (n // 6, D)) + 1) * 2.0 ** -8
+    X[2 * n // 3: 2 * n // 3 + n // 6] = ties.astype(np.float32)
+    X[-12:] = 0.0
+    p = dict(d=2, k_hd=16, k_ld=8, n_neg=8, alpha=1.0, perplexity=8.0)
+    m = _make(X, p, hd_mode=1)
+    m.step(3)
+    st = m.export_state()
+    m.step(1)
+    ref = m.export_state()
+    m.import_state(st)
+    m.set_option("precision", precision)
+    m.step(1)
+    got = m.export_state()
+    s = m.stats()
+    np.testing.assert_array_equal(got["hd_idx"], ref["hd_idx"])
+    np.testing.assert_array_equal(got["hd_d2"], ref["hd_d2"])
+    np.testing.assert_array_equal(got["ld_idx"], ref["ld_idx"])
+    # the offset block alone sends a third of the candidates to the re-rank
+    assert s["cand_reranked"] >= 0.25 * s["cand_scored"]
+    m.close()
+
+
 def test_integer_ties_are_broken_by_index():
     """Small-integer data: FP32 and FP64 distances are exact, ties are exact,
     and both sides must order them by index: bit-exact lists, no ambiguity."""
