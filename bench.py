@@ -746,7 +746,7 @@ def parse_args(argv=None):
     ap.add_argument("--insert-n", type=int, default=10000, help="--mode dynamic: points per insertion")
     ap.add_argument("--rounds", type=int, default=20, help="--mode dynamic: insertion rounds")
     ap.add_argument("--every", type=int, default=50, help="--mode dynamic: iterations between insertions")
-    ap.add_argument("--insert-rounds", type=int, default=16,
+    ap.add_argument("--insert-rounds", type=int, default=64,
                     help="--mode dynamic: neighbour-of-neighbour rounds of each insertion")
     ap.add_argument("--hd-mode", type=int, default=0, choices=[0, 1, 2],
                     help="--mode dynamic: 0 adaptive HD refinement, 1 every iteration, 2 never")

@@ -162,7 +162,7 @@ int funcsne_create(const float *X, int64_t N, int32_t D, int32_t d, int32_t k_hd
  *                    dimension) while both neighbour sets keep refining
  *                    (default 0: off)
  *   "insert_rounds"  neighbour-of-neighbour rounds that build an inserted
- *                    point's HD list (0..64, default 16)
+ *                    point's HD list (0..256, default 64)
  *   "hd_lanes"       lanes that read one gathered HD row in the refinement:
  *                    1, 2, 4 or 8, or 0 (default) to choose from the row
  *                    bytes. A tuning knob; it fixes the FP32 summation order,
@@ -206,7 +206,7 @@ int funcsne_sync(funcsne_t *h);
  * funcsne_insert -- append n_new points (Section 3: the algorithm admits new
  * points without a pre-computation phase). X_new is n_new x D FP32 (host or
  * device), copied. Each new point gets k_hd HD neighbours from random
- * candidates refined by "insert_rounds" (default 16) neighbour-of-neighbour
+ * candidates refined by "insert_rounds" (default 64) neighbour-of-neighbour
  * rounds against the existing points, its LD position by `placement`
  * (FUNCSNE_PLACE_MEAN: mean of its HD neighbours' positions;
  * FUNCSNE_PLACE_SURROGATE: the online MLP,

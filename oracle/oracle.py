@@ -384,7 +384,7 @@ class OracleState:
                           _p(flags, _bp), _p(info, _lp), _p(z, _dp))
         return dict(A=A, R=R, flags=flags, coin=bool(info[0]), n_new=int(info[1]), z=z)
 
-    def insert(self, X_new, rounds=16, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
+    def insert(self, X_new, rounds=64, tol=ORACLE_BISECT_TOL, maxit=ORACLE_BISECT_MAXIT):
         """Append the rows of X_new (mean placement) after `rounds`
         neighbour-of-neighbour rounds. Returns the first new index."""
         X_new = _f64(X_new)

@@ -61,7 +61,7 @@ struct funcsne {
     bool concurrent = false;  // run the two refinements side by side in the graph
     int32_t forces_cw = 8;    // floats of an LD row per lane in the forces kernel
     int32_t hd_lanes_opt = 0; // lanes per gathered HD row (0: chosen from the row bytes)
-    int32_t insert_rounds = 16; // neighbour-of-neighbour rounds of an insertion
+    int32_t insert_rounds = 64; // neighbour-of-neighbour rounds of an insertion
     int32_t jump_iters = 0, jump_parts = 2;  // jump start by linear projections
     bool frozen = false;      // an iteration of the jump start: no gradient step
     cudaStream_t stream = nullptr;
@@ -803,8 +803,8 @@ int funcsne_set_option(funcsne_t* h, const char* key, double v) {
             return fail(h, FUNCSNE_E_ARG, "%s must be an integer (jump_iters >= 0, jump_parts >= 1)", key);
         (k == "jump_iters" ? h->jump_iters : h->jump_parts) = static_cast<int32_t>(v);
     } else if (k == "insert_rounds") {
-        if (v < 0 || v > 64 || v != static_cast<int>(v))
-            return fail(h, FUNCSNE_E_ARG, "insert_rounds must be an integer in [0, 64]");
+        if (v < 0 || v > 256 || v != static_cast<int>(v))
+            return fail(h, FUNCSNE_E_ARG, "insert_rounds must be an integer in [0, 256]");
         h->insert_rounds = static_cast<int32_t>(v);
     } else if (k == "hd_lanes") {
         if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8)

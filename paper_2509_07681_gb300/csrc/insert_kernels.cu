@@ -4,14 +4,16 @@
 // For each new point i (indices n_old .. N-1), at iteration t:
 //   1. k_hd distinct existing points from counter (t, i, INSERT, l), offsets
 //      in [0, n_old) with linear probing (one thread per point);
-//   2. a warp per point: FP32 distances, (d2, idx) order, then 4 rounds of
-//      32 candidates, round r slot s from counter (t, i, INSERT, 64+32r+s):
+//   2. a warp per point: FP32 distances, (d2, idx) order, then q.rounds
+//      rounds (option insert_rounds, default 64) of 32 candidates, round r
+//      slot s from counter (t, i, INSERT, 64+32r+s):
 //      slots 0-23 a neighbour of a listed neighbour (an existing point's list
 //      of iteration t), slots 24-31 a uniform existing point; top-k merge;
 //   3. cold-start bisection (beta, P);
 //   4. y_i = mean of the HD neighbours' y; v_i = 0; A, R rows cleared;
 //   5. LD list = the first k_ld HD neighbours, completed when k_ld > k_hd by
-//      distinct random existing points from counter (t, i, INSERT, 256+l).
+//      distinct random existing points from counter (t, i, INSERT, 2^30+l),
+//      above the slots of every round.
 #include "device_common.cuh"
 #include "launch.h"
 

@@ -306,12 +306,12 @@ def test_whole_run_blobs_recall_and_structure():
     assert math.isfinite(s["Zhat"]) and s["error_word"] == 0
 
 
-@pytest.mark.parametrize("rounds", [16, 0, 5])
+@pytest.mark.parametrize("rounds", [64, 0, 5, 200])
 def test_insertion_matches_oracle(rounds):
     """funcsne_insert (mean placement) against the oracle from the same state:
     the new points' HD/LD lists, positions and bandwidths, the scalars, and
-    the next iteration over the grown state; with the default 16, no, and 5
-    neighbour-of-neighbour rounds."""
+    the next iteration over the grown state; with the default 64, no, 5 and
+    200 neighbour-of-neighbour rounds."""
     X = synth.blobs(n=2600, dim=30, n_clusters=6, seed=15)
     p = dict(d=2, k_hd=16, k_ld=8, n_neg=8, alpha=1.0, perplexity=8.0)
     m = _make(X[:2000], p, hd_mode=1)

@@ -415,7 +415,7 @@ def test_insertion_lists_placement_and_scalars():
         assert abs(st.P[i].sum() - 1) < 1e-9
     assert abs(st.Zhat - z0 * (700 * 699) / (600 * 599)) <= 1e-12 * st.Zhat
     assert st.E == max(e0, 100 / 700)
-    # the default 16 neighbour-of-neighbour rounds from a random start find a
+    # the default 64 neighbour-of-neighbour rounds from a random start find a
     # large share of the exact neighbours among the existing points (random
     # lists would find about 16/600 of them); later iterations refine the rest
     ex, _ = O.bruteforce_knn(X[:600], 16)
