@@ -85,6 +85,8 @@ struct funcsne {
         __nv_bfloat16 *Xb = nullptr, *H1 = nullptr, *H2 = nullptr, *G3 = nullptr, *G2 = nullptr, *G1 = nullptr;
         double *part = nullptr, *loss = nullptr;
         uint32_t* step = nullptr;
+        float* ws = nullptr;  // split-K slices of the weight gradients
+        int64_t ws_floats = 0;
     } mlp;
     std::string err;
 };
@@ -386,7 +388,7 @@ void free_all(funcsne* h) {
                     static_cast<void*>(q.wb), static_cast<void*>(q.idx), static_cast<void*>(q.T),
                     static_cast<void*>(q.O), static_cast<void*>(q.scale), static_cast<void*>(q.Xb),
                     static_cast<void*>(q.H1), static_cast<void*>(q.H2), static_cast<void*>(q.G3),
-                    static_cast<void*>(q.G2), static_cast<void*>(q.G1), static_cast<void*>(q.part),
+                    static_cast<void*>(q.G2), static_cast<void*>(q.G1), static_cast<void*>(q.part), static_cast<void*>(q.ws),
                     static_cast<void*>(q.loss), static_cast<void*>(q.step)})
         cudaFree(p);
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
@@ -495,6 +497,8 @@ MlpParams mlp_params(const funcsne* h) {
     p.G1 = q.G1;
     p.O = q.O;
     p.part = q.part;
+    p.ws = q.ws;
+    p.ws_floats = q.ws_floats;
     p.loss = q.loss;
     p.scale = q.scale;
     p.step = q.step;
@@ -525,6 +529,12 @@ int ensure_mlp(funcsne* h) {
     FSNE_CUDA(h, dalloc(&q.G2, B * H));
     FSNE_CUDA(h, dalloc(&q.G1, B * H));
     FSNE_CUDA(h, dalloc(&q.part, (B * d + 255) / 256 + (B + 255) / 256 + 8));
+    {
+        // up to 32 split-K slices of the largest weight gradient, 64 MB at most
+        const int64_t per = std::max(std::max(H * H, H * D), d * H) + std::max(H, d);
+        q.ws_floats = std::max<int64_t>(std::min<int64_t>(32 * per, int64_t(1) << 24), per);
+        FSNE_CUDA(h, dalloc(&q.ws, q.ws_floats));
+    }
     FSNE_CUDA(h, dalloc(&q.loss, 1));
     FSNE_CUDA(h, dalloc(&q.scale, 1));
     FSNE_CUDA(h, dalloc(&q.step, 1));

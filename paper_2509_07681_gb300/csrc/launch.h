@@ -131,6 +131,8 @@ struct MlpParams {
     __nv_bfloat16* G1;          // B x H
     float* O;                   // B x d outputs
     double* part;               // reduction partials
+    float* ws;                  // split-K slices of the weight gradients
+    int64_t ws_floats;
     double* loss;               // device scalar
     float* scale;               // device scalar: RMS of the last batch's targets
     uint32_t* step;             // device scalar: Adam steps taken

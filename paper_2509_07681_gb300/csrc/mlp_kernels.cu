@@ -11,8 +11,9 @@
 //   FP32 master parameters, then the bfloat16 copy is refreshed.
 // Parameters are one flat array: W1 (H x D) b1 (H) W2 (H x H) b2 (H)
 // W3 (d x H) b3 (d). The GEMMs are tiled CUDA-core kernels: a training
-// step is ~2 GFLOP every few iterations, far below 0.1% of an iteration's
-// time, so the dense-contraction hardware would not change the step time.
+// step is ~2.4 GFLOP every few iterations; the weight gradients (K = B) are
+// split over K so that they fill the GPU, and their kernels also sum the
+// bias gradients.
 #include "device_common.cuh"
 #include "launch.h"
 
@@ -21,17 +22,24 @@ namespace fsne {
 // ------------------------------------------------------------------ GEMM
 // C[m][n] = sum_k opA(m,k) opB(k,n); opA(m,k) = TA ? A[k][m] : A[m][k],
 // opB(k,n) = TB ? B[n][k] : B[k][n]; A, B bfloat16 row-major with leading
-// dimensions lda, ldb. 64 x 64 tiles, K-steps of 16, 256 threads (4 x 4 each).
-enum { kEpiBiasReluBf16 = 0, kEpiBiasF32 = 1, kEpiMaskBf16 = 2, kEpiF32 = 3 };
+// dimensions lda, ldb. 64 x 64 tiles, K-steps of 16, 256 threads (4 x 4
+// each). Tiles are loaded along each operand's contiguous dimension.
+// kEpiSplitF32: block z sums k in [z kc, (z + 1) kc) and stores its partial
+// tile at Cf + z M N (dense M x N); blocks of the first column of tiles also
+// store the partial row sums sum_k opA(m, k) at wsb + z M. gemm_reduce_kernel
+// then adds the slices in order (a deterministic split over K).
+enum { kEpiBiasReluBf16 = 0, kEpiBiasF32 = 1, kEpiMaskBf16 = 2, kEpiSplitF32 = 3 };
 
 struct GemmArgs {
     int M, N, K, lda, ldb, ldc;
+    int kc;                     // K columns per block (split-K slice)
     const __nv_bfloat16* A;
     const __nv_bfloat16* B;
     const float* bias;          // N (bias epilogues)
     const __nv_bfloat16* mask;  // M x N, ldc (mask epilogue): keep where mask > 0
     __nv_bfloat16* Cb;          // bfloat16 output
-    float* Cf;                  // FP32 output
+    float* Cf;                  // FP32 output; the slices for kEpiSplitF32
+    float* wsb;                 // row-sum slices (kEpiSplitF32)
 };
 
 template <int TA, int TB, int EPI>
@@ -40,27 +48,35 @@ __global__ void __launch_bounds__(256) gemm_bf16_kernel(const GemmArgs g) {
     __shared__ float Bs[16][64 + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[4][4];
+    const int kbeg = blockIdx.z * g.kc;
+    const int kend = min(g.K, kbeg + g.kc);
+    const bool row_sums = EPI == kEpiSplitF32 && blockIdx.x == 0 && tx == 0;
+    float acc[4][4], rs[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a) {
+        rs[a] = 0.f;
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    for (int k0 = 0; k0 < g.K; k0 += 16) {
-        // load a 64 x 16 tile of opA and a 16 x 64 tile of opB (4 elements per thread)
+    }
+    for (int k0 = kbeg; k0 < kend; k0 += 16) {
+        // a 64 x 16 tile of opA and a 16 x 64 tile of opB, 4 elements per
+        // thread; consecutive threads read consecutive addresses
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int e = threadIdx.x + 256 * q;  // 0..1023
-            const int kk = e & 15, mm = e >> 4;   // A tile: (mm, kk)
+            const int mm = TA ? (e & 63) : (e >> 4), kk = TA ? (e >> 6) : (e & 15);
             const int m = m0 + mm, k = k0 + kk;
             float va = 0.f;
-            if (m < g.M && k < g.K)
-                va = __bfloat162float(TA ? g.A[static_cast<int64_t>(k) * g.lda + m] : g.A[static_cast<int64_t>(m) * g.lda + k]);
+            if (m < g.M && k < kend)
+                va = __bfloat162float(TA ? g.A[static_cast<int64_t>(k) * g.lda + m]
+                                         : g.A[static_cast<int64_t>(m) * g.lda + k]);
             As[kk][mm] = va;
-            const int nn = e & 63, kb = e >> 6;   // B tile: (kb, nn)
+            const int nn = TB ? (e >> 4) : (e & 63), kb = TB ? (e & 15) : (e >> 6);
             const int n = n0 + nn, k2 = k0 + kb;
             float vb = 0.f;
-            if (n < g.N && k2 < g.K)
-                vb = __bfloat162float(TB ? g.B[static_cast<int64_t>(n) * g.ldb + k2] : g.B[static_cast<int64_t>(k2) * g.ldb + n]);
+            if (n < g.N && k2 < kend)
+                vb = __bfloat162float(TB ? g.B[static_cast<int64_t>(n) * g.ldb + k2]
+                                         : g.B[static_cast<int64_t>(k2) * g.ldb + n]);
             Bs[kb][nn] = vb;
         }
         __syncthreads();
@@ -75,6 +91,9 @@ __global__ void __launch_bounds__(256) gemm_bf16_kernel(const GemmArgs g) {
             for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[r][c] = __fmaf_rn(a[r], b[c], acc[r][c]);
+            if (row_sums)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) rs[r] += a[r];
         }
         __syncthreads();
     }
@@ -82,30 +101,72 @@ __global__ void __launch_bounds__(256) gemm_bf16_kernel(const GemmArgs g) {
     for (int r = 0; r < 4; ++r) {
         const int m = m0 + ty * 4 + r;
         if (m >= g.M) continue;
+        if (row_sums) g.wsb[static_cast<int64_t>(blockIdx.z) * g.M + m] = rs[r];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int n = n0 + tx * 4 + c;
             if (n >= g.N) continue;
-            const int64_t o = static_cast<int64_t>(m) * g.ldc + n;
             float v = acc[r][c];
-            if constexpr (EPI == kEpiBiasReluBf16) {
-                v += g.bias[n];
-                g.Cb[o] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
-            } else if constexpr (EPI == kEpiBiasF32) {
-                g.Cf[o] = v + g.bias[n];
-            } else if constexpr (EPI == kEpiMaskBf16) {
-                g.Cb[o] = __bfloat162float(g.mask[o]) > 0.f ? __float2bfloat16_rn(v) : __float2bfloat16_rn(0.f);
+            if constexpr (EPI == kEpiSplitF32) {
+                g.Cf[(static_cast<int64_t>(blockIdx.z) * g.M + m) * g.N + n] = v;
             } else {
-                g.Cf[o] = v;
+                const int64_t o = static_cast<int64_t>(m) * g.ldc + n;
+                if constexpr (EPI == kEpiBiasReluBf16) {
+                    v += g.bias[n];
+                    g.Cb[o] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+                } else if constexpr (EPI == kEpiBiasF32) {
+                    g.Cf[o] = v + g.bias[n];
+                } else {
+                    g.Cb[o] = __bfloat162float(g.mask[o]) > 0.f ? __float2bfloat16_rn(v) : __float2bfloat16_rn(0.f);
+                }
             }
         }
     }
 }
 
+// C[e] = sum over z = 0 .. S-1 of ws[z M N + e] (e < M N) and
+// rows[m] = sum over z of wsb[z M + m] (m < M), both in slice order.
+__global__ void gemm_reduce_kernel(const float* __restrict__ ws, const float* __restrict__ wsb, int S, int M, int N,
+                                   float* __restrict__ C, float* __restrict__ rows) {
+    const int64_t MN = static_cast<int64_t>(M) * N;
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e < MN) {
+        float s = 0.f;
+        for (int z = 0; z < S; ++z) s += ws[z * MN + e];
+        C[e] = s;
+    }
+    if (e < M) {
+        float s = 0.f;
+        for (int z = 0; z < S; ++z) s += wsb[static_cast<int64_t>(z) * M + e];
+        rows[e] = s;
+    }
+}
+
 template <int TA, int TB, int EPI>
 static void gemm(const GemmArgs& g, cudaStream_t s) {
+    GemmArgs a = g;
+    a.kc = g.K;
     const dim3 grid((g.N + 63) / 64, (g.M + 63) / 64);
-    gemm_bf16_kernel<TA, TB, EPI><<<grid, 256, 0, s>>>(g);
+    gemm_bf16_kernel<TA, TB, EPI><<<grid, 256, 0, s>>>(a);
+}
+
+// Weight gradient C (dense M x N) = sum over the K = B batch rows of
+// A[k][m] B[k][n], and rows[m] = sum_k A[k][m] (the bias gradient). Split
+// over K into slices of at least 128 rows (at most 32 slices, and no more
+// than the workspace of ws_floats holds).
+static void gemm_weight_grad(GemmArgs g, float* ws, int64_t ws_floats, float* C, float* rows, cudaStream_t s) {
+    const int64_t per = static_cast<int64_t>(g.M) * g.N + g.M;
+    int S = (g.K + 127) / 128;
+    if (S > 32) S = 32;
+    while (S > 1 && S * per > ws_floats) --S;
+    g.kc = ((g.K + S - 1) / S + 15) / 16 * 16;
+    S = (g.K + g.kc - 1) / g.kc;
+    g.Cf = ws;
+    g.wsb = ws + static_cast<int64_t>(S) * g.M * g.N;
+    const dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, S);
+    gemm_bf16_kernel<1, 0, kEpiSplitF32><<<grid, 256, 0, s>>>(g);
+    const int64_t n = static_cast<int64_t>(g.M) * g.N > g.M ? static_cast<int64_t>(g.M) * g.N : g.M;
+    gemm_reduce_kernel<<<static_cast<int>((n + 255) / 256), 256, 0, s>>>(g.Cf, g.wsb, S, g.M, g.N, C, rows);
 }
 
 // ------------------------------------------------------------------ data
@@ -174,7 +235,8 @@ __global__ void mlp_batch_kernel(MlpParams q) {
     if (threadIdx.x == 0) q.part[blockIdx.x] = red[0];
 }
 
-// s = RMS of the batch targets (1 when zero); targets divided by s.
+// s = RMS of the batch targets (1 when zero); targets divided by s. Every
+// block sums the partials in the same order, so all use the same s.
 __global__ void mlp_scale_kernel(MlpParams q, int nparts) {
     __shared__ float s_scale;
     if (threadIdx.x == 0) {
@@ -183,11 +245,12 @@ __global__ void mlp_scale_kernel(MlpParams q, int nparts) {
         const double ms = t / (static_cast<double>(q.B) * q.d);
         const float s = ms > 0.0 ? static_cast<float>(sqrt(ms)) : 1.f;
         s_scale = s;
-        *q.scale = s;
+        if (blockIdx.x == 0) *q.scale = s;
     }
     __syncthreads();
     const float inv = 1.f / s_scale;
-    for (int e = threadIdx.x; e < q.B * q.d; e += blockDim.x) q.T[e] *= inv;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < q.B * q.d) q.T[e] *= inv;
 }
 
 // G3 = bf16(2 (O - T) / (B d)); loss partials.
@@ -214,15 +277,6 @@ __global__ void mlp_loss_finish_kernel(MlpParams q, int nparts) {
     double t = 0.0;
     for (int b = 0; b < nparts; ++b) t += q.part[b];
     *q.loss = t / (static_cast<double>(q.B) * q.d);
-}
-
-// out[c] = sum over rows of G[r][c] (bias gradients), FP32.
-__global__ void mlp_colsum_kernel(const __nv_bfloat16* __restrict__ G, int rows, int cols, float* out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
-    float s = 0.f;
-    for (int r = 0; r < rows; ++r) s += __bfloat162float(G[static_cast<int64_t>(r) * cols + c]);
-    out[c] = s;
 }
 
 // Adam with bias correction; refreshes the bfloat16 copy; step advances in
@@ -287,7 +341,7 @@ cudaError_t launch_mlp_train_step(const MlpParams& q, cudaStream_t s) {
     const int B = q.B, D = q.D, H = q.H, d = q.d;
     const int nb = blocks_for(B, 256);
     mlp_batch_kernel<<<nb, 256, 0, s>>>(q);
-    mlp_scale_kernel<<<1, 256, 0, s>>>(q, nb);
+    mlp_scale_kernel<<<blocks_for(static_cast<int64_t>(B) * d, 256), 256, 0, s>>>(q, nb);
     mlp_inputs_kernel<<<blocks_for(static_cast<int64_t>(B) * D, 256), 256, 0, s>>>(q.X32, q.xpitch, D, q.idx, 0, B,
                                                                                    q.mu, q.sigma, q.Xb);
     mlp_forward(q, B, s);
@@ -304,28 +358,25 @@ cudaError_t launch_mlp_train_step(const MlpParams& q, cudaStream_t s) {
     float* gW3 = gb2 + H;
     float* gb3 = gW3 + static_cast<int64_t>(d) * H;
     GemmArgs g{};
-    // dW3 = G3^T H2 (d x H)
-    g.M = d; g.N = H; g.K = B; g.lda = d; g.ldb = H; g.ldc = H; g.A = q.G3; g.B = q.H2; g.Cf = gW3;
-    gemm<1, 0, kEpiF32>(g, s);
+    // dW3 = G3^T H2 (d x H), db3 = column sums of G3
+    g.M = d; g.N = H; g.K = B; g.lda = d; g.ldb = H; g.ldc = H; g.A = q.G3; g.B = q.H2;
+    gemm_weight_grad(g, q.ws, q.ws_floats, gW3, gb3, s);
     // G2 = (G3 W3) [H2 > 0]  (B x H)
     g = GemmArgs{};
     g.M = B; g.N = H; g.K = d; g.lda = d; g.ldb = H; g.ldc = H; g.A = q.G3; g.B = W3; g.mask = q.H2; g.Cb = q.G2;
     gemm<0, 0, kEpiMaskBf16>(g, s);
-    // dW2 = G2^T H1 (H x H)
+    // dW2 = G2^T H1 (H x H), db2 = column sums of G2
     g = GemmArgs{};
-    g.M = H; g.N = H; g.K = B; g.lda = H; g.ldb = H; g.ldc = H; g.A = q.G2; g.B = q.H1; g.Cf = gW2;
-    gemm<1, 0, kEpiF32>(g, s);
+    g.M = H; g.N = H; g.K = B; g.lda = H; g.ldb = H; g.ldc = H; g.A = q.G2; g.B = q.H1;
+    gemm_weight_grad(g, q.ws, q.ws_floats, gW2, gb2, s);
     // G1 = (G2 W2) [H1 > 0]  (B x H)
     g = GemmArgs{};
     g.M = B; g.N = H; g.K = H; g.lda = H; g.ldb = H; g.ldc = H; g.A = q.G2; g.B = W2; g.mask = q.H1; g.Cb = q.G1;
     gemm<0, 0, kEpiMaskBf16>(g, s);
-    // dW1 = G1^T X^ (H x D)
+    // dW1 = G1^T X^ (H x D), db1 = column sums of G1
     g = GemmArgs{};
-    g.M = H; g.N = D; g.K = B; g.lda = H; g.ldb = D; g.ldc = D; g.A = q.G1; g.B = q.Xb; g.Cf = gW1;
-    gemm<1, 0, kEpiF32>(g, s);
-    mlp_colsum_kernel<<<blocks_for(d, 128), 128, 0, s>>>(q.G3, B, d, gb3);
-    mlp_colsum_kernel<<<blocks_for(H, 128), 128, 0, s>>>(q.G2, B, H, gb2);
-    mlp_colsum_kernel<<<blocks_for(H, 128), 128, 0, s>>>(q.G1, B, H, gb1);
+    g.M = H; g.N = D; g.K = B; g.lda = H; g.ldb = D; g.ldc = D; g.A = q.G1; g.B = q.Xb;
+    gemm_weight_grad(g, q.ws, q.ws_floats, gW1, gb1, s);
     mlp_adam_kernel<<<blocks_for(q.n_params, 256), 256, 0, s>>>(q);
     mlp_step_kernel<<<1, 32, 0, s>>>(q);
     return cudaGetLastError();
