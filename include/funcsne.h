@@ -16,7 +16,10 @@
  *     detected with cudaPointerGetAttributes. Data passed in is copied;
  *     the caller keeps ownership of every buffer it passes.
  *   - Work is enqueued on the handle's CUDA stream (funcsne_set_stream);
- *     calls that write caller buffers synchronise that stream first.
+ *     calls that write caller buffers synchronise that stream first. That
+ *     stream does not wait for other streams: device inputs written on
+ *     another stream must be complete (or that stream passed to
+ *     funcsne_set_stream) before the call.
  *   - Point indices are int32 (N < 2^31).
  */
 #ifndef FUNCSNE_H

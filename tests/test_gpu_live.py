@@ -271,3 +271,36 @@ def test_async_embedding_readout(d):
     m.sync()
     np.testing.assert_array_equal(part.cpu().numpy(), m.embedding()[:100])
     m.close()
+
+
+def test_pitched_copies_round_trip():
+    """Rows of D = 30 floats live in rows of 32 on the device and LD rows of
+    d = 3 in rows of 4: copies between them and host or device buffers of
+    the caller (staged through a contiguous device buffer when a host side
+    is pitched) return the caller's values exactly."""
+    import torch
+    X = synth.blobs(n=2000, dim=30, n_clusters=4, seed=59)
+    Xn = X[1500:]
+    m = F.FuncSNE(X[:1500], 3, 16, 8, 8, 1.0, 8.0, seed=0)
+    np.testing.assert_array_equal(m.data(), X[:1500])
+    m.step(3)
+    st = m.export_state()
+    m.import_state(st)
+    np.testing.assert_array_equal(m.export_state()["Y"], st["Y"])
+    np.testing.assert_array_equal(m.embedding(), st["Y"])
+    m.insert(Xn[:200])
+    dev = torch.from_numpy(Xn[200:]).cuda()
+    torch.cuda.synchronize()
+    m.insert(dev)
+    np.testing.assert_array_equal(m.data(), X)
+    out = torch.empty((2000, 30), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    m.data(out=out)
+    np.testing.assert_array_equal(out.cpu().numpy(), X)
+    m.close()
+    # a device tensor as the input of create
+    Xd = torch.from_numpy(X).cuda()
+    torch.cuda.synchronize()
+    m2 = F.FuncSNE(Xd, 3, 16, 8, 8, 1.0, 8.0, seed=0)
+    np.testing.assert_array_equal(m2.data(), X)
+    m2.close()
