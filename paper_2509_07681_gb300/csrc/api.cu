@@ -435,6 +435,7 @@ int check_errors(funcsne* h) {
     if (rc) return rc;
     if (s.err & kErrIndex) return fail(h, FUNCSNE_E_RANGE, "device index check failed (error word 0x%x)", s.err);
     if (s.err & kErrNonFinite) return fail(h, FUNCSNE_E_NAN, "non-finite values (error word 0x%x)", s.err);
+    if (s.err & kErrTimeout) return fail(h, FUNCSNE_E_CUDA, "a device wait timed out (error word 0x%x)", s.err);
     return FUNCSNE_OK;
 }
 
@@ -499,6 +500,7 @@ MlpParams mlp_params(const funcsne* h) {
     p.part = q.part;
     p.ws = q.ws;
     p.ws_floats = q.ws_floats;
+    p.err = &h->sc->err;
     p.loss = q.loss;
     p.scale = q.scale;
     p.step = q.step;

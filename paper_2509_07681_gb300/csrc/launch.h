@@ -132,6 +132,7 @@ struct MlpParams {
     float* O;                   // B x d outputs
     double* part;               // reduction partials
     float* ws;                  // split-K slices of the weight gradients
+    uint32_t* err;              // device error word (kErrTimeout)
     int64_t ws_floats;
     double* loss;               // device scalar
     float* scale;               // device scalar: RMS of the last batch's targets

@@ -10,110 +10,194 @@
 //   dW1 = G1^T X^,  db = column sums of G;  Adam with bias correction on
 //   FP32 master parameters, then the bfloat16 copy is refreshed.
 // Parameters are one flat array: W1 (H x D) b1 (H) W2 (H x H) b2 (H)
-// W3 (d x H) b3 (d). The GEMMs are tiled CUDA-core kernels: a training
-// step is ~2.4 GFLOP every few iterations; the weight gradients (K = B) are
-// split over K so that they fill the GPU, and their kernels also sum the
-// bias gradients.
+// W3 (d x H) b3 (d). The GEMMs run on the tensor cores (tcgen05.mma with
+// TMEM accumulators, tc_gemm.cuh); the weight gradients (K = B) are split
+// over K so that they fill the GPU, and their kernels also sum the bias
+// gradients.
 #include "device_common.cuh"
 #include "launch.h"
+#include "tc_gemm.cuh"
 
 namespace fsne {
 
 // ------------------------------------------------------------------ GEMM
-// C[m][n] = sum_k opA(m,k) opB(k,n); opA(m,k) = TA ? A[k][m] : A[m][k],
-// opB(k,n) = TB ? B[n][k] : B[k][n]; A, B bfloat16 row-major with leading
-// dimensions lda, ldb. 64 x 64 tiles, K-steps of 16, 256 threads (4 x 4
-// each). Tiles are loaded along each operand's contiguous dimension.
-// kEpiSplitF32: block z sums k in [z kc, (z + 1) kc) and stores its partial
-// tile at Cf + z M N (dense M x N); blocks of the first column of tiles also
-// store the partial row sums sum_k opA(m, k) at wsb + z M. gemm_reduce_kernel
-// then adds the slices in order (a deterministic split over K).
+// C[m][n] = sum_k A(m, k) B(n, k) on the tensor cores (tcgen05.mma,
+// kind::f16: BF16 operands, FP32 accumulation in TMEM). Operand element
+// (r, k) is p[r rs + k ks]. A CTA of 256 threads computes a 128 x 64 tile of
+// C over the K values [z kc, (z + 1) kc) of its slice z (blockIdx.z),
+// staging 64 K values of A and B at a time into shared memory in the layout
+// of tc_gemm.cuh: two threads stage a row of A and four a row of B (16-byte
+// vectors when a row is contiguous in K and aligned, single values
+// otherwise, with consecutive threads on consecutive rows). Rows and K
+// values outside the matrices are staged as zeros. Thread 0 issues the four
+// MMAs of a chunk and commits them to an mbarrier that every thread waits on
+// (a bounded wait: on time-out the kernel records kErrTimeout and stops)
+// before the next chunk overwrites the operands. The accumulator tile goes
+// from TMEM through shared memory to coalesced global writes.
+// kEpiSplitF32 stores the partial tile of slice z at Cf + z M N (dense
+// M x N) and, from the first column of tiles, the partial row sums of A at
+// wsb + z M; gemm_reduce_kernel adds the slices in order.
 enum { kEpiBiasReluBf16 = 0, kEpiBiasF32 = 1, kEpiMaskBf16 = 2, kEpiSplitF32 = 3 };
 
+struct TcOperand {
+    const __nv_bfloat16* p;
+    int64_t rs, ks;   // strides of a row and of a K step, in elements
+    int vec;          // rows contiguous in K and 16-byte aligned: 8-value loads
+};
+
 struct GemmArgs {
-    int M, N, K, lda, ldb, ldc;
-    int kc;                     // K columns per block (split-K slice)
-    const __nv_bfloat16* A;
-    const __nv_bfloat16* B;
+    int M, N, K, kc;  // kc: K values per CTA (a multiple of 64)
+    TcOperand a, b;
+    int ldc;
     const float* bias;          // N (bias epilogues)
     const __nv_bfloat16* mask;  // M x N, ldc (mask epilogue): keep where mask > 0
     __nv_bfloat16* Cb;          // bfloat16 output
     float* Cf;                  // FP32 output; the slices for kEpiSplitF32
     float* wsb;                 // row-sum slices (kEpiSplitF32)
+    uint32_t* err;              // device error word
 };
 
-template <int TA, int TB, int EPI>
-__global__ void __launch_bounds__(256) gemm_bf16_kernel(const GemmArgs g) {
-    __shared__ float As[16][64 + 4];
-    __shared__ float Bs[16][64 + 4];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+// Operand regions of the dynamic shared memory: A (128 rows) and B (64
+// rows). A chunk takes 16 KB / 8 KB; each region is sized so that every
+// address the descriptors can reach stays inside it. After the last MMA the
+// A region holds the FP32 tile for the coalesced epilogue.
+constexpr int kTcRegionA = 48 * 1024;
+constexpr int kTcRegionB = 16 * 1024;
+constexpr int kTcSmem = kTcRegionA + kTcRegionB;
+constexpr int kTcThreads = 256;
+constexpr int kTcTileLd = kTcBN + 1;  // padded row of the FP32 tile (floats)
+constexpr uint32_t kTcWaitLimit = 1u << 24;
+
+// Stage K values [k0 + kq, k0 + kq + nk) of operand row `row` (R rows in
+// all) as row r of an Rt-row chunk at `dst` (zeros outside the matrix);
+// returns the sum of the staged values (row sums of A for the bias
+// gradients).
+__device__ __forceinline__ float tc_stage(unsigned char* dst, const TcOperand& o, int r, int Rt, int row, int R,
+                                          int k0, int kq, int nk, int kend) {
+    float sum = 0.f;
+    const bool in = row < R;
+    const __nv_bfloat16* src = o.p + static_cast<int64_t>(in ? row : 0) * o.rs;
+    if (o.vec) {
+        for (int q = kq; q < kq + nk; q += 8) {
+            const int k = k0 + q;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (in && k + 8 <= kend) {
+                v = __ldg(reinterpret_cast<const uint4*>(src + k));
+            } else if (in && k < kend) {
+                __nv_bfloat16 t[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) t[e] = k + e < kend ? src[k + e] : __float2bfloat16_rn(0.f);
+                v = *reinterpret_cast<const uint4*>(t);
+            }
+            *reinterpret_cast<uint4*>(dst + tc_offset(r, q, Rt)) = v;
+            const __nv_bfloat16* t = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) sum += __bfloat162float(t[e]);
+        }
+    } else {
+#pragma unroll 8
+        for (int q = kq; q < kq + nk; ++q) {
+            const int k = k0 + q;
+            const __nv_bfloat16 v = (in && k < kend) ? src[static_cast<int64_t>(k) * o.ks] : __float2bfloat16_rn(0.f);
+            *reinterpret_cast<__nv_bfloat16*>(dst + tc_offset(r, q, Rt)) = v;
+            sum += __bfloat162float(v);
+        }
+    }
+    return sum;
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const GemmArgs g) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float s_rows[2][kTcBM];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    unsigned char* As = tc_smem;
+    unsigned char* Bs = tc_smem + kTcRegionA;
+    if (warp == 0) tc_alloc(&tmem_base, kTcBN);
+    if (tid == 0) mbar_init(&bar, 1);
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t taddr = tmem_base;
+
+    const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * kTcBN;
     const int kbeg = blockIdx.z * g.kc;
     const int kend = min(g.K, kbeg + g.kc);
-    const bool row_sums = EPI == kEpiSplitF32 && blockIdx.x == 0 && tx == 0;
-    float acc[4][4], rs[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        rs[a] = 0.f;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    }
-    for (int k0 = kbeg; k0 < kend; k0 += 16) {
-        // a 64 x 16 tile of opA and a 16 x 64 tile of opB, 4 elements per
-        // thread; consecutive threads read consecutive addresses
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = threadIdx.x + 256 * q;  // 0..1023
-            const int mm = TA ? (e & 63) : (e >> 4), kk = TA ? (e >> 6) : (e & 15);
-            const int m = m0 + mm, k = k0 + kk;
-            float va = 0.f;
-            if (m < g.M && k < kend)
-                va = __bfloat162float(TA ? g.A[static_cast<int64_t>(k) * g.lda + m]
-                                         : g.A[static_cast<int64_t>(m) * g.lda + k]);
-            As[kk][mm] = va;
-            const int nn = TB ? (e >> 4) : (e & 63), kb = TB ? (e & 15) : (e >> 6);
-            const int n = n0 + nn, k2 = k0 + kb;
-            float vb = 0.f;
-            if (n < g.N && k2 < kend)
-                vb = __bfloat162float(TB ? g.B[static_cast<int64_t>(n) * g.ldb + k2]
-                                         : g.B[static_cast<int64_t>(k2) * g.ldb + n]);
-            Bs[kb][nn] = vb;
-        }
+    constexpr uint32_t lbo_a = (kTcBM / 8) * 128, lbo_b = (kTcBN / 8) * 128;
+    constexpr uint32_t idesc = tc_idesc_bf16(kTcBM, kTcBN);
+    const uint32_t a_addr = smem_u32(As), b_addr = smem_u32(Bs);
+    // A: two threads a row (32 K values each); B: four threads a row (16 each)
+    const int ar = tid & (kTcBM - 1), aq = (tid >> 7) * (kTcBK / 2);
+    const int br = tid & (kTcBN - 1), bq = (tid >> 6) * (kTcBK / 4);
+    float rsum = 0.f;
+    uint32_t phase = 0;
+    bool issued = false, timed_out = false;
+    for (int k0 = kbeg; k0 < kend; k0 += kTcBK) {
+        rsum += tc_stage(As, g.a, ar, kTcBM, m0 + ar, g.M, k0, aq, kTcBK / 2, kend);
+        tc_stage(Bs, g.b, br, kTcBN, n0 + br, g.N, k0, bq, kTcBK / 4, kend);
+        fence_proxy_async_smem();
         __syncthreads();
+        if (tid == 0) {
+            tc_fence_after_sync();
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = __fmaf_rn(a[r], b[c], acc[r][c]);
-            if (row_sums)
-#pragma unroll
-                for (int r = 0; r < 4; ++r) rs[r] += a[r];
+            for (int j = 0; j < kTcBK / 16; ++j) {
+                const uint64_t ad = tc_smem_desc(a_addr + 2 * j * lbo_a, lbo_a, 128);
+                const uint64_t bd = tc_smem_desc(b_addr + 2 * j * lbo_b, lbo_b, 128);
+                tc_mma_bf16(taddr, ad, bd, idesc, issued || j > 0);
+            }
+            tc_commit(&bar);
         }
-        __syncthreads();
+        issued = true;
+        const bool ok = mbar_wait(&bar, phase, kTcWaitLimit);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
     }
+    if (timed_out) {
+        if (tid == 0) atomicOr(g.err, kErrTimeout);
+        // the MMAs of the last chunk may still run: one more bounded wait
+        mbar_wait(&bar, phase ^ 1u, kTcWaitLimit);
+    } else {
+        // TMEM -> the FP32 tile in shared memory: warp w reads lanes
+        // 32 (w mod 4) + l (tile rows) and columns 32 (w / 4) .. + 31
+        tc_fence_after_sync();
+        float* Cs = reinterpret_cast<float*>(tc_smem);
+        const int row = 32 * (warp & 3) + (tid & 31);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int m = m0 + ty * 4 + r;
-        if (m >= g.M) continue;
-        if (row_sums) g.wsb[static_cast<int64_t>(blockIdx.z) * g.M + m] = rs[r];
+        for (int h = 0; h < 2; ++h) {
+            const int c0 = 32 * (warp >> 2) + 16 * h;
+            float v[16];
+            if (issued) {
+                tc_ld16(taddr + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + static_cast<uint32_t>(c0), v);
+            } else {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int n = n0 + tx * 4 + c;
-            if (n >= g.N) continue;
-            float v = acc[r][c];
+                for (int q = 0; q < 16; ++q) v[q] = 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) Cs[row * kTcTileLd + c0 + q] = v[q];
+        }
+        if (EPI == kEpiSplitF32) s_rows[tid >> 7][ar] = rsum;
+        __syncthreads();
+        // coalesced writes: consecutive threads take consecutive columns
+        const int z = blockIdx.z;
+        if (EPI == kEpiSplitF32 && blockIdx.x == 0 && tid < kTcBM && m0 + tid < g.M)
+            g.wsb[static_cast<int64_t>(z) * g.M + m0 + tid] = s_rows[0][tid] + s_rows[1][tid];
+        for (int e = tid; e < kTcBM * kTcBN; e += kTcThreads) {
+            const int r = e / kTcBN, c = e % kTcBN;
+            const int m = m0 + r, n = n0 + c;
+            if (m >= g.M || n >= g.N) continue;
+            const float v = Cs[r * kTcTileLd + c];
             if constexpr (EPI == kEpiSplitF32) {
-                g.Cf[(static_cast<int64_t>(blockIdx.z) * g.M + m) * g.N + n] = v;
+                g.Cf[(static_cast<int64_t>(z) * g.M + m) * g.N + n] = v;
             } else {
                 const int64_t o = static_cast<int64_t>(m) * g.ldc + n;
                 if constexpr (EPI == kEpiBiasReluBf16) {
-                    v += g.bias[n];
-                    g.Cb[o] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+                    const float t = v + g.bias[n];
+                    g.Cb[o] = __float2bfloat16_rn(t > 0.f ? t : 0.f);
                 } else if constexpr (EPI == kEpiBiasF32) {
                     g.Cf[o] = v + g.bias[n];
                 } else {
@@ -121,6 +205,12 @@ __global__ void __launch_bounds__(256) gemm_bf16_kernel(const GemmArgs g) {
                 }
             }
         }
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after_sync();
+        tc_dealloc(taddr, kTcBN);
     }
 }
 
@@ -142,16 +232,30 @@ __global__ void gemm_reduce_kernel(const float* __restrict__ ws, const float* __
     }
 }
 
-template <int TA, int TB, int EPI>
-static void gemm(const GemmArgs& g, cudaStream_t s) {
-    GemmArgs a = g;
-    a.kc = g.K;
-    const dim3 grid((g.N + 63) / 64, (g.M + 63) / 64);
-    gemm_bf16_kernel<TA, TB, EPI><<<grid, 256, 0, s>>>(a);
+static TcOperand operand(const __nv_bfloat16* p, int64_t rs, int64_t ks) {
+    TcOperand o;
+    o.p = p;
+    o.rs = rs;
+    o.ks = ks;
+    o.vec = ks == 1 && rs % 8 == 0 && reinterpret_cast<uintptr_t>(p) % 16 == 0;
+    return o;
+}
+
+template <int EPI>
+static void tc_launch(const GemmArgs& g, int slices, cudaStream_t s) {
+    cudaFuncSetAttribute(tc_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    const dim3 grid((g.N + kTcBN - 1) / kTcBN, (g.M + kTcBM - 1) / kTcBM, slices);
+    tc_gemm_kernel<EPI><<<grid, kTcThreads, kTcSmem, s>>>(g);
+}
+
+template <int EPI>
+static void gemm(GemmArgs g, cudaStream_t s) {
+    g.kc = (g.K + kTcBK - 1) / kTcBK * kTcBK;
+    tc_launch<EPI>(g, 1, s);
 }
 
 // Weight gradient C (dense M x N) = sum over the K = B batch rows of
-// A[k][m] B[k][n], and rows[m] = sum_k A[k][m] (the bias gradient). Split
+// A(m, k) B(n, k), and rows[m] = sum_k A(m, k) (the bias gradient). Split
 // over K into slices of at least 128 rows (at most 32 slices, and no more
 // than the workspace of ws_floats holds).
 static void gemm_weight_grad(GemmArgs g, float* ws, int64_t ws_floats, float* C, float* rows, cudaStream_t s) {
@@ -159,12 +263,11 @@ static void gemm_weight_grad(GemmArgs g, float* ws, int64_t ws_floats, float* C,
     int S = (g.K + 127) / 128;
     if (S > 32) S = 32;
     while (S > 1 && S * per > ws_floats) --S;
-    g.kc = ((g.K + S - 1) / S + 15) / 16 * 16;
+    g.kc = ((g.K + S - 1) / S + kTcBK - 1) / kTcBK * kTcBK;
     S = (g.K + g.kc - 1) / g.kc;
     g.Cf = ws;
     g.wsb = ws + static_cast<int64_t>(S) * g.M * g.N;
-    const dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, S);
-    gemm_bf16_kernel<1, 0, kEpiSplitF32><<<grid, 256, 0, s>>>(g);
+    tc_launch<kEpiSplitF32>(g, S, s);
     const int64_t n = static_cast<int64_t>(g.M) * g.N > g.M ? static_cast<int64_t>(g.M) * g.N : g.M;
     gemm_reduce_kernel<<<static_cast<int>((n + 255) / 256), 256, 0, s>>>(g.Cf, g.wsb, S, g.M, g.N, C, rows);
 }
@@ -328,13 +431,17 @@ static void mlp_forward(const MlpParams& q, int rows, cudaStream_t s) {
     const float* b2 = b1 + H + static_cast<int64_t>(H) * H;
     const float* b3 = b2 + H + static_cast<int64_t>(d) * H;
     GemmArgs g{};
-    g.M = rows; g.N = H; g.K = D; g.lda = D; g.ldb = D; g.ldc = H;
-    g.A = q.Xb; g.B = W1; g.bias = b1; g.Cb = q.H1;
-    gemm<0, 1, kEpiBiasReluBf16>(g, s);
-    g.K = H; g.lda = H; g.ldb = H; g.A = q.H1; g.B = W2; g.bias = b2; g.Cb = q.H2;
-    gemm<0, 1, kEpiBiasReluBf16>(g, s);
-    g.N = d; g.ldc = d; g.A = q.H2; g.B = W3; g.bias = b3; g.Cb = nullptr; g.Cf = q.O;
-    gemm<0, 1, kEpiBiasF32>(g, s);
+    g.err = q.err;
+    // H1 = relu(X^ W1^T + b1): A(b, f) = X^[b][f], B(h, f) = W1[h][f]
+    g.M = rows; g.N = H; g.K = D; g.ldc = H;
+    g.a = operand(q.Xb, D, 1); g.b = operand(W1, D, 1); g.bias = b1; g.Cb = q.H1;
+    gemm<kEpiBiasReluBf16>(g, s);
+    // H2 = relu(H1 W2^T + b2)
+    g.K = H; g.a = operand(q.H1, H, 1); g.b = operand(W2, H, 1); g.bias = b2; g.Cb = q.H2;
+    gemm<kEpiBiasReluBf16>(g, s);
+    // O = H2 W3^T + b3
+    g.N = d; g.ldc = d; g.a = operand(q.H2, H, 1); g.b = operand(W3, H, 1); g.bias = b3; g.Cb = nullptr; g.Cf = q.O;
+    gemm<kEpiBiasF32>(g, s);
 }
 
 cudaError_t launch_mlp_train_step(const MlpParams& q, cudaStream_t s) {
@@ -359,23 +466,30 @@ cudaError_t launch_mlp_train_step(const MlpParams& q, cudaStream_t s) {
     float* gb3 = gW3 + static_cast<int64_t>(d) * H;
     GemmArgs g{};
     // dW3 = G3^T H2 (d x H), db3 = column sums of G3
-    g.M = d; g.N = H; g.K = B; g.lda = d; g.ldb = H; g.ldc = H; g.A = q.G3; g.B = q.H2;
+    g.err = q.err;
+    g.M = d; g.N = H; g.K = B; g.a = operand(q.G3, 1, d); g.b = operand(q.H2, 1, H);
     gemm_weight_grad(g, q.ws, q.ws_floats, gW3, gb3, s);
     // G2 = (G3 W3) [H2 > 0]  (B x H)
     g = GemmArgs{};
-    g.M = B; g.N = H; g.K = d; g.lda = d; g.ldb = H; g.ldc = H; g.A = q.G3; g.B = W3; g.mask = q.H2; g.Cb = q.G2;
-    gemm<0, 0, kEpiMaskBf16>(g, s);
+    g.err = q.err;
+    g.M = B; g.N = H; g.K = d; g.ldc = H; g.a = operand(q.G3, d, 1); g.b = operand(W3, 1, H); g.mask = q.H2;
+    g.Cb = q.G2;
+    gemm<kEpiMaskBf16>(g, s);
     // dW2 = G2^T H1 (H x H), db2 = column sums of G2
     g = GemmArgs{};
-    g.M = H; g.N = H; g.K = B; g.lda = H; g.ldb = H; g.ldc = H; g.A = q.G2; g.B = q.H1;
+    g.err = q.err;
+    g.M = H; g.N = H; g.K = B; g.a = operand(q.G2, 1, H); g.b = operand(q.H1, 1, H);
     gemm_weight_grad(g, q.ws, q.ws_floats, gW2, gb2, s);
     // G1 = (G2 W2) [H1 > 0]  (B x H)
     g = GemmArgs{};
-    g.M = B; g.N = H; g.K = H; g.lda = H; g.ldb = H; g.ldc = H; g.A = q.G2; g.B = W2; g.mask = q.H1; g.Cb = q.G1;
-    gemm<0, 0, kEpiMaskBf16>(g, s);
+    g.err = q.err;
+    g.M = B; g.N = H; g.K = H; g.ldc = H; g.a = operand(q.G2, H, 1); g.b = operand(W2, 1, H); g.mask = q.H1;
+    g.Cb = q.G1;
+    gemm<kEpiMaskBf16>(g, s);
     // dW1 = G1^T X^ (H x D), db1 = column sums of G1
     g = GemmArgs{};
-    g.M = H; g.N = D; g.K = B; g.lda = H; g.ldb = D; g.ldc = D; g.A = q.G1; g.B = q.Xb;
+    g.err = q.err;
+    g.M = H; g.N = D; g.K = B; g.a = operand(q.G1, 1, H); g.b = operand(q.Xb, 1, D);
     gemm_weight_grad(g, q.ws, q.ws_floats, gW1, gb1, s);
     mlp_adam_kernel<<<blocks_for(q.n_params, 256), 256, 0, s>>>(q);
     mlp_step_kernel<<<1, 32, 0, s>>>(q);

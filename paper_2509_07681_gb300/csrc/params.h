@@ -65,6 +65,7 @@ struct DevScalars {
 
 constexpr uint32_t kErrNonFinite = 1u;
 constexpr uint32_t kErrIndex = 2u;
+constexpr uint32_t kErrTimeout = 4u;  // a bounded device wait ran out
 
 // Lanes per row for gathering rows of `bytes` bytes in the HD refinement
 // (measured on GB300 over 1M-2M points, rows of 64 to 3136 bytes): two lanes
