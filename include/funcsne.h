@@ -327,6 +327,15 @@ int funcsne_debug_step(funcsne_t *h, float *att, float *rep);
  * kernels. For measurement. */
 int funcsne_profile_step(funcsne_t *h, int32_t n_iters, double *ms_per_kernel);
 
+/* Exercise the bounded device wait on the handle's stream: a kernel polls
+ * an mbarrier that nothing arrives on, gives up after `polls` polls
+ * (1 .. 2^24) and sets the device error bit that the tensor-core kernels
+ * set when a wait runs out. The next funcsne_sync then returns
+ * FUNCSNE_E_CUDA ("a device wait timed out") and so do later ones on this
+ * handle; the CUDA context stays usable. For testing failure detection.
+ * Errors: FUNCSNE_E_ARG. */
+int funcsne_debug_bounded_wait(funcsne_t *h, uint32_t polls);
+
 /* Exact k nearest HD neighbours (FP32 distances, ties by index) of the n_q
  * query points `queries` (int32, host or device), by brute force over all
  * points: for measuring neighbour recall. idx: n_q x k, d2: n_q x k or NULL. */

@@ -1008,6 +1008,13 @@ int funcsne_mlp_predict(const funcsne_t* hc, const float* X, int64_t n, float* Y
     return FUNCSNE_OK;
 }
 
+int funcsne_debug_bounded_wait(funcsne_t* h, uint32_t polls) {
+    if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
+    if (polls < 1 || polls > (1u << 24)) return fail(h, FUNCSNE_E_ARG, "polls must be in [1, 2^24]");
+    FSNE_CUDA(h, launch_bounded_wait(&h->sc->err, polls, h->stream));
+    return FUNCSNE_OK;
+}
+
 int funcsne_mlp_debug_step(funcsne_t* h, funcsne_mlp_debug_t* out) {
     if (!h || !out) return fail(h, FUNCSNE_E_ARG, "NULL argument");
     int rc = ensure_mlp(h);

@@ -145,6 +145,7 @@ cudaError_t launch_mlp_train_step(const MlpParams& q, cudaStream_t s);
 cudaError_t launch_mlp_place(const MlpParams& q, const float* X, int xpitch, int64_t first, int64_t rows, float* Y,
                              int DP, cudaStream_t s);
 cudaError_t launch_bf16_to_f32(const __nv_bfloat16* in, int64_t n, float* out, cudaStream_t s);
+cudaError_t launch_bounded_wait(uint32_t* err, uint32_t polls, cudaStream_t s);
 
 // evaluation
 cudaError_t launch_exact_knn(const KnnParams& kp, cudaStream_t s);

@@ -214,6 +214,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(const GemmArgs g
     }
 }
 
+// A bounded wait that runs out: one thread polls an mbarrier that expects an
+// arrival nothing makes, `polls` times, then records kErrTimeout.
+__global__ void bounded_wait_kernel(uint32_t* err, uint32_t polls) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    if (!mbar_wait(&bar, 0u, polls)) atomicOr(err, kErrTimeout);
+}
+
+cudaError_t launch_bounded_wait(uint32_t* err, uint32_t polls, cudaStream_t s) {
+    bounded_wait_kernel<<<1, 32, 0, s>>>(err, polls);
+    return cudaGetLastError();
+}
+
 // C[e] = sum over z = 0 .. S-1 of ws[z M N + e] (e < M N) and
 // rows[m] = sum over z of wsb[z M + m] (m < M), both in slice order.
 __global__ void gemm_reduce_kernel(const float* __restrict__ ws, const float* __restrict__ wsb, int S, int M, int N,

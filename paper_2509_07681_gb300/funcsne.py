@@ -69,6 +69,7 @@ ABI_FUNCTIONS = {
     "funcsne_remove": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_get_embedding": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_get_embedding_async": (C.c_int, [_h, _vp, C.c_int64]),
+    "funcsne_debug_bounded_wait": (C.c_int, [_h, C.c_uint32]),
     "funcsne_wait_embedding": (C.c_int, [_h]),
     "funcsne_get_data": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_scale_embedding": (C.c_int, [_h, C.c_float]),
@@ -359,6 +360,10 @@ class FuncSNE:
         steps). `out` is valid after wait_embedding() or sync()."""
         self._pending_out = funcsne_get_embedding_async(self.h, out)
         return out
+
+    def debug_bounded_wait(self, polls=1000):
+        """A device wait that runs out; the next sync() raises FuncSNEError."""
+        _check(load().funcsne_debug_bounded_wait(self.h, int(polls)), self.h)
 
     def wait_embedding(self):
         funcsne_wait_embedding(self.h)

@@ -78,4 +78,5 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.funcsne_get_data(None, rows.ctypes.data, 2) == -1
     assert lib.funcsne_get_embedding_async(None, rows.ctypes.data, 2) == -1
     assert lib.funcsne_wait_embedding(None) == -1
+    assert lib.funcsne_debug_bounded_wait(None, 10) == -1
     lib.funcsne_destroy(None)

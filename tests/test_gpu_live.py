@@ -304,3 +304,25 @@ def test_pitched_copies_round_trip():
     m2 = F.FuncSNE(Xd, 3, 16, 8, 8, 1.0, 8.0, seed=0)
     np.testing.assert_array_equal(m2.data(), X)
     m2.close()
+
+
+def test_bounded_device_wait_is_reported_and_context_survives():
+    """Failure detection without a fault: a device wait on an mbarrier that
+    nothing arrives on gives up after its poll limit and sets the error bit
+    the tensor-core kernels use; funcsne_sync reports it, and the CUDA
+    context stays usable for a new handle."""
+    X = synth.blobs(n=1000, dim=20, n_clusters=4, seed=60)
+    m = F.FuncSNE(X, 2, 16, 8, 8, 1.0, 8.0, seed=0)
+    m.step(2)
+    m.sync()
+    with pytest.raises(F.FuncSNEError):
+        m.debug_bounded_wait(0)
+    m.debug_bounded_wait(1000)
+    with pytest.raises(F.FuncSNEError, match="timed out"):
+        m.sync()
+    m.close()
+    m2 = F.FuncSNE(X, 2, 16, 8, 8, 1.0, 8.0, seed=0)
+    m2.step(3)
+    m2.sync()
+    assert np.isfinite(m2.embedding()).all()
+    m2.close()
