@@ -533,7 +533,9 @@ __device__ __forceinline__ float bf16_chunk_acc(const float* __restrict__ xs, co
 // (band_from_row_error), for the candidate of every lane. BF16 rows hold nq
 // chunks of 8 values, then a 16-byte chunk whose first four bytes hold the
 // row's error bound E_c >= ||x_c - x~_c||.
-template <int G, bool BATCH>
+// KB > 0: a lane issues the loads of KB of its chunks before using any
+// (KB = 0: two at a time).
+template <int G, int KB>
 __device__ __forceinline__ ApproxDist group_dist_bf16(const float* __restrict__ xs,
                                                       const uint8_t* __restrict__ Xq, int qpitch, int nq,
                                                       uint32_t cv, int lane, float gamma) {
@@ -547,9 +549,9 @@ __device__ __forceinline__ ApproxDist group_dist_bf16(const float* __restrict__ 
         float acc = 0.f, nrm = 0.f;
         if (cj != kNoRow) {
             const uint4* b = reinterpret_cast<const uint4*>(Xq + static_cast<int64_t>(cj) * qpitch);
-            if constexpr (BATCH) {
+            if constexpr (KB > 0) {
                 // all of a batch's chunk loads in flight before any is used
-                constexpr int kB = 8;
+                constexpr int kB = KB;
                 for (int q0 = s; q0 < nq; q0 += kB * G) {
                     uint4 raw[kB];
 #pragma unroll

@@ -127,8 +127,10 @@ hd_refine_kernel(const StepParams p) {
             const float thr = warp_get<RH>(hd2, static_cast<uint32_t>(k_hd - 1));
             ApproxDist a;
             if constexpr (XM == 1)
-                // batched loads pay off with the 64 registers of the k_hd > 32 variant
-                a = group_dist_bf16<G, RH == 2>(xs, p.Xq, p.qpitch, p.nq, cv, lane, p.q_gamma);
+                // batched loads pay off with the 64 registers of the k_hd > 32
+                // variant, and in batches of 4 for rows read by lane pairs
+                a = group_dist_bf16<G, RH == 2 ? 8 : (G == 2 ? 4 : 0)>(xs, p.Xq, p.qpitch, p.nq, cv, lane,
+                                                                       p.q_gamma);
             else  // nq = code words for FP8
                 a = group_dist_fp8<G>(xs, p.Xq, p.qpitch, p.nq, p.qscale_off, cv, lane, p.q_gamma);
             const bool need = valid && __fsub_rd(a.d2, a.band) <= thr;
