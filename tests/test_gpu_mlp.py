@@ -28,9 +28,12 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-def test_mlp_step_matches_oracle():
-    X = synth.swissroll(n=3000, dim=24, n_clusters=8, seed=30)
-    D, d, H, B = 24, 4, 64, 512
+@pytest.mark.parametrize("D,d,H,B", [(24, 4, 64, 512), (50, 3, 100, 300)])
+def test_mlp_step_matches_oracle(D, d, H, B):
+    """One training step against the oracle; the second shape leaves ragged
+    tensor-core tiles (rows, columns and K values past the matrices) and rows
+    that are not 16-byte multiples (single-value operand staging)."""
+    X = synth.swissroll(n=3000, dim=D, n_clusters=8, seed=30)
     m = F.FuncSNE(X, d, 16, 8, 8, 1.0, 10.0, seed=3)
     m.set_option("mlp_batch", B)
     m.set_option("mlp_hidden", H)
