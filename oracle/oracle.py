@@ -336,9 +336,10 @@ class OracleState:
             self._s.E = E
         if t is not None:
             self._s.t = t
-        for a in range(0, self.N, 32768):
-            diff = self.X[a:a + 32768, None, :] - self.X[self.hd_idx[a:a + 32768]]
-            self.hd_d2[a:a + 32768] = np.einsum("nkd,nkd->nk", diff, diff)
+        step = max(1, (1 << 24) // max(1, self.hd_idx.shape[1] * self.D))  # at most 128 MB a chunk
+        for a in range(0, self.N, step):
+            diff = self.X[a:a + step, None, :] - self.X[self.hd_idx[a:a + step]]
+            self.hd_d2[a:a + step] = np.einsum("nkd,nkd->nk", diff, diff)
 
     def coin(self):
         return bool(lib().oracle_coin(C.byref(self._s)))

@@ -1,5 +1,6 @@
-"""Parity at the benchmark's full size and launch configuration: the 1M-point
-spectrum workload (D=50, d=16, k_hd=k_ld=n_neg=32), BF16 rows, HD refinement
+"""Parity at full size and in the benchmark's launch configuration: the
+1M-point spectrum workload (D=50, d=16, k_hd=k_ld=n_neg=32) and the 70,000
+pixel rows (D=784, d=2, k_hd=32, k_ld=n_neg=16), BF16 rows, HD refinement
 every iteration. One GPU iteration; on a sample of points (including the
 first and last rows, so the grid's ragged tail), the oracle recomputes each
 point's HD and LD refinement and its forces one by one."""
@@ -15,10 +16,10 @@ from gpu_util import fp32_band, lib, oracle_from_state, rel_err_rows
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", [F.BF16])
-def test_full_size_sampled_parity(precision):
+@pytest.mark.parametrize("workload,precision", [("spectrum-1m", F.BF16), ("pixels-70k", F.BF16)])
+def test_full_size_sampled_parity(workload, precision):
     lib()
-    X, p = synth.make("spectrum-1m")
+    X, p = synth.make(workload)
     N, D = X.shape
     m = F.FuncSNE(X, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0)
     m.set_option("hd_mode", 1)

@@ -39,6 +39,9 @@ CASES = {
     # the 1M-point workload's shape at small N: d=16, k 32/32, n_neg 32
     "spectrum-shape": (lambda: synth.spectrum(n=3000, dim=50, n_clusters=12, seed=5),
                        dict(d=16, k_hd=32, k_ld=32, n_neg=32, alpha=1.0, perplexity=30.0)),
+    # pixel rows: D=784 (multiples of 1/255, about half zeros), d=2
+    "pixels-shape": (lambda: synth.pixels(n=2500, dim=784, seed=10),
+                     dict(d=2, k_hd=32, k_ld=16, n_neg=16, alpha=1.0, perplexity=30.0)),
     # dynamic-dataset shape: D=128, d=8
     "swissroll-shape": (lambda: synth.swissroll(n=2500, dim=128, seed=6),
                         dict(d=8, k_hd=32, k_ld=16, n_neg=16, alpha=100.0, perplexity=30.0)),
