@@ -80,3 +80,15 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.funcsne_wait_embedding(None) == -1
     assert lib.funcsne_debug_bounded_wait(None, 10) == -1
     lib.funcsne_destroy(None)
+
+
+def test_header_compiles_as_c_and_cxx():
+    """The boundary is a plain C header: it compiles as C99 and as C++."""
+    import shutil
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "funcsne.h")
+    for cc, lang, std in (("gcc", "c", "-std=c99"), ("g++", "c++", "-std=c++17")):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not found")
+        r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Werror", "-x", lang, std, hdr], capture_output=True,
+                           text=True)
+        assert r.returncode == 0, r.stderr
