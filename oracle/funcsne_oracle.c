@@ -1082,6 +1082,99 @@ double oracle_mlp_grad(int B, int D, int H, int d, const double *theta, const do
     return loss / ((double)B * d);
 }
 
+/*
+ * Magnitudes of the batch gradient and outputs of oracle_mlp_grad (rounded
+ * network): the same forward and backward passes with every weight, bias,
+ * input, target and intermediate replaced by its absolute value, gated by
+ * the ReLU pattern of the actual pass:
+ *   A1 = |b1| + |W1| |x|, A2 = |b2| + |W2| (A1 [H1 > 0]), AO = |b3| + |W3| (A2 [H2 > 0]),
+ *   AG3 = 2 (AO + |T|) / (B d), AG2 = (AG3 |W3|) [H2 > 0], AG1 = (AG2 |W2|) [H1 > 0],
+ *   M(dW3) = sum_b AG3 A2^T, M(dW2) = sum_b AG2 A1^T, M(dW1) = sum_b AG1 |x|^T,
+ *   M(db) = sum_b AG.
+ * Every result of the network is a sum of products whose magnitudes these
+ * sums bound, so a relative perturbation rho of each rounded intermediate
+ * (a different summation order, or a value rounded to the neighbouring
+ * bfloat16) moves a result by at most about (rounding levels) rho times its
+ * magnitude. Writes gmag (size of the parameters) and Omag (B x d).
+ */
+void oracle_mlp_grad_mag(int B, int D, int H, int d, const double *theta, const double *X, const double *T,
+                         double *gmag, double *Omag)
+{
+    const double *W1 = theta, *b1 = W1 + (size_t)H * D, *W2 = b1 + H, *b2 = W2 + (size_t)H * H;
+    const double *W3 = b2 + H, *b3 = W3 + (size_t)d * H;
+    double *mW1 = gmag, *mb1 = mW1 + (size_t)H * D, *mW2 = mb1 + H, *mb2 = mW2 + (size_t)H * H;
+    double *mW3 = mb2 + H, *mb3 = mW3 + (size_t)d * H;
+    size_t np = (size_t)H * D + H + (size_t)H * H + H + (size_t)d * H + d;
+    memset(gmag, 0, sizeof(double) * np);
+    double *H1 = (double *)malloc(sizeof(double) * (size_t)H);
+    double *A1 = (double *)malloc(sizeof(double) * (size_t)H);
+    double *A2 = (double *)malloc(sizeof(double) * (size_t)H);
+    double *G2 = (double *)malloc(sizeof(double) * (size_t)H);
+    double *G1 = (double *)malloc(sizeof(double) * (size_t)H);
+    double *G3 = (double *)malloc(sizeof(double) * (size_t)d);
+    char *on1 = (char *)malloc((size_t)H);
+    char *on2 = (char *)malloc((size_t)H);
+    for (int b = 0; b < B; ++b) {
+        const double *x = X + (size_t)b * D;
+        /* the actual (rounded) pass, for the gates */
+        for (int h = 0; h < H; ++h) {
+            double z = b1[h], a = fabs(b1[h]);
+            for (int f = 0; f < D; ++f) {
+                z += W1[(size_t)h * D + f] * x[f];
+                a += fabs(W1[(size_t)h * D + f]) * fabs(x[f]);
+            }
+            on1[h] = z > 0.0;
+            H1[h] = oracle_bf16(z > 0.0 ? z : 0.0);
+            A1[h] = on1[h] ? a : 0.0;
+        }
+        for (int h = 0; h < H; ++h) {
+            double z = b2[h], a = fabs(b2[h]);
+            for (int g = 0; g < H; ++g) {
+                z += W2[(size_t)h * H + g] * H1[g];
+                a += fabs(W2[(size_t)h * H + g]) * A1[g];
+            }
+            on2[h] = z > 0.0;
+            A2[h] = on2[h] ? a : 0.0;
+        }
+        for (int c = 0; c < d; ++c) {
+            double a = fabs(b3[c]);
+            for (int g = 0; g < H; ++g) a += fabs(W3[(size_t)c * H + g]) * A2[g];
+            Omag[(size_t)b * d + c] = a;
+            G3[c] = 2.0 * (a + fabs(T[(size_t)b * d + c])) / ((double)B * d);
+        }
+        for (int c = 0; c < d; ++c) {
+            for (int g = 0; g < H; ++g) mW3[(size_t)c * H + g] += G3[c] * A2[g];
+            mb3[c] += G3[c];
+        }
+        for (int g = 0; g < H; ++g) {
+            double s = 0.0;
+            for (int c = 0; c < d; ++c) s += G3[c] * fabs(W3[(size_t)c * H + g]);
+            G2[g] = on2[g] ? s : 0.0;
+        }
+        for (int h = 0; h < H; ++h) {
+            for (int g = 0; g < H; ++g) mW2[(size_t)h * H + g] += G2[h] * A1[g];
+            mb2[h] += G2[h];
+        }
+        for (int g = 0; g < H; ++g) {
+            double s = 0.0;
+            for (int h = 0; h < H; ++h) s += G2[h] * fabs(W2[(size_t)h * H + g]);
+            G1[g] = on1[g] ? s : 0.0;
+        }
+        for (int h = 0; h < H; ++h) {
+            for (int f = 0; f < D; ++f) mW1[(size_t)h * D + f] += G1[h] * fabs(x[f]);
+            mb1[h] += G1[h];
+        }
+    }
+    free(H1);
+    free(A1);
+    free(A2);
+    free(G2);
+    free(G1);
+    free(G3);
+    free(on1);
+    free(on2);
+}
+
 /* Forward pass only (placement): O = MLP(X) with the same roundings. */
 void oracle_mlp_forward(int B, int D, int H, int d, const double *theta, const double *X, int round, double *O)
 {

@@ -11,7 +11,7 @@ import numpy as np
 
 from .build import build_oracle
 
-__all__ = ["lib", "philox", "OracleState", "bf16", "mlp_size", "mlp_init", "mlp_grad", "mlp_forward", "adam", "bisect", "entropy", "topk_merge", "ld_merge",
+__all__ = ["lib", "philox", "OracleState", "bf16", "mlp_size", "mlp_init", "mlp_grad", "mlp_grad_mag", "mlp_forward", "adam", "bisect", "entropy", "topk_merge", "ld_merge",
            "exact_z", "kl_divergence", "exact_grad", "bruteforce_knn", "query_knn",
            "ORACLE_BISECT_TOL", "ORACLE_BISECT_MAXIT", "STREAMS", "CAND_HD", "CAND_LD"]
 
@@ -106,6 +106,8 @@ def _declare(L):
     L.oracle_mlp_init.restype = None
     L.oracle_mlp_grad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, C.c_int, _dp, _dp]
     L.oracle_mlp_grad.restype = C.c_double
+    L.oracle_mlp_grad_mag.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
+    L.oracle_mlp_grad_mag.restype = None
     L.oracle_mlp_forward.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, _dp]
     L.oracle_mlp_forward.restype = None
     L.oracle_adam.argtypes = [C.c_int64, _dp, _dp, _dp, _dp, C.c_int, C.c_double, C.c_double, C.c_double,
@@ -246,6 +248,19 @@ def mlp_grad(theta, X, T, H, round_bf16=True):
     return loss, g, O
 
 
+def mlp_grad_mag(theta, X, T, H):
+    """(gradient magnitudes, output magnitudes) of one batch: the sums of the
+    magnitudes of the terms behind each gradient element and output of the
+    rounded network (oracle_mlp_grad_mag)."""
+    theta, X, T = _f64(theta), _f64(X), _f64(T)
+    B, D = X.shape
+    d = T.shape[1]
+    g = np.zeros_like(theta)
+    O = np.zeros((B, d))
+    lib().oracle_mlp_grad_mag(B, D, H, d, _p(theta, _dp), _p(X, _dp), _p(T, _dp), _p(g, _dp), _p(O, _dp))
+    return g, O
+
+
 def mlp_forward(theta, X, H, d, round_bf16=True):
     theta, X = _f64(theta), _f64(X)
     B, D = X.shape
@@ -315,9 +330,11 @@ class OracleState:
             setattr(self._s, k, v)
 
     def load(self, Y=None, V=None, hd_idx=None, ld_idx=None, beta=None, P=None, Zhat=None,
-             E=None, t=None):
+             E=None, t=None, d2=True):
         """Overwrite parts of the state (for example with the GPU's exported state).
-        HD distances are recomputed in FP64 from X; the list order is kept."""
+        HD distances are recomputed in FP64 from X (unless d2 is False: a
+        state that will only give forces, which do not read them); the list
+        order is kept."""
         if Y is not None:
             self.Y[...] = Y
         if V is not None:
@@ -336,6 +353,8 @@ class OracleState:
             self._s.E = E
         if t is not None:
             self._s.t = t
+        if not d2:
+            return
         step = max(1, (1 << 24) // max(1, self.hd_idx.shape[1] * self.D))  # at most 128 MB a chunk
         for a in range(0, self.N, step):
             diff = self.X[a:a + step, None, :] - self.X[self.hd_idx[a:a + step]]

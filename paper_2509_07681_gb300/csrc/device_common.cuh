@@ -679,8 +679,8 @@ __device__ __forceinline__ bool hset_has(const uint32_t* tab, uint32_t x) {
 // Start from beta0 (> 0: warm restart) or 1/mean(sh); keep a bracket
 // [lo, hi] on the root of H = ln perp; take the Newton step when it stays
 // inside the bracket, else double (no upper bound yet) or halve the bracket;
-// stop when |H - ln perp| < tol. The oracle reaches the same tolerance by
-// plain bisection.
+// stop when |H - ln perp| < tol, after one last Newton step from the sums of
+// that evaluation. The oracle reaches its tolerance by plain bisection.
 template <int R>
 __device__ __forceinline__ float warp_bisect(const float (&d2)[R], int k, float log_perp,
                                              float beta0, float (&p)[R], int lane) {
@@ -725,14 +725,21 @@ __device__ __forceinline__ float warp_bisect(const float (&d2)[R], int k, float 
         }
         const float invS = __fdividef(1.f, S);
         const float mu = U * invS;
-        const float H = __logf(S) + beta * mu;
+        const float H = logf(S) + beta * mu;
         const float f = H - log_perp;
-        if (fabsf(f) < kBisectTol) break;
+        const float slope = -beta * (V * invS - mu * mu);
+        if (fabsf(f) < kBisectTol) {
+            // converged: one more Newton step from the sums at hand (no new
+            // evaluation) takes the entropy error from below the tolerance
+            // down to the FP32 evaluation noise
+            const float nb2 = beta - __fdividef(f, slope);
+            if (slope < 0.f && nb2 > 0.f && isfinite(nb2)) beta = nb2;
+            break;
+        }
         if (f > 0.f)
             lo = beta;
         else
             hi = beta;
-        const float slope = -beta * (V * invS - mu * mu);
         float nxt = beta - __fdividef(f, slope);
         if (!(slope < 0.f) || !(nxt > lo) || !(nxt < hi)) nxt = isinf(hi) ? 2.f * beta : 0.5f * (lo + hi);
         beta = nxt;

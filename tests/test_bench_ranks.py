@@ -87,7 +87,13 @@ def test_bench_args_and_bytes():
     a = bench.parse_args(["--mode", "timing", "--sizes", "1000,2000", "--iters", "30"])
     assert a.mode == "timing" and a.sizes == "1000,2000" and a.iters == 30
     per = bench.algorithmic_bytes_per_point(50, 16, 32, 32, 32, 200)
-    # 33 FP32 rows of D = 50 dominate HD refinement
-    assert per["hd_refine"] == 33 * 200 + 8 * 32 + 4 * 32 + 80 + 8 * 32
-    assert per["update"] == 7 * 64
+    # the survey's per-point rule at the 1M-point workload: 33 FP32 rows of
+    # D = 50 and the HD lists in the HD refinement; 64 gathered and 32
+    # scattered LD rows (6,144 bytes) in the forces
+    assert per["hd_refine"] == 33 * 200 + 8 * 32 + 8 * 32 + 4 * 32
+    assert per["forces"] == 6144 and per["ld_refine"] == 33 * 64 + 8 * 32
+    assert per["update"] == 6 * 64
+    full = bench.full_bytes_per_point(50, 16, 32, 32, 32, 200)
+    assert full["hd_refine"] == 33 * 200 + 8 * 32 + 4 * 32 + 80 + 8 * 32
+    assert full["update"] == 7 * 64 and all(full[k] >= per[k] for k in per)
     assert bench.row_bytes_of(50) == {"fp32": 200, "bf16": 104, "fp8": 58}

@@ -638,6 +638,30 @@ def test_mlp_forward_is_the_composition_of_layers():
     np.testing.assert_allclose(O.mlp_forward(th, x, H, d, round_bf16=False), ref, rtol=1e-12, atol=1e-14)
 
 
+def test_mlp_magnitudes_bound_and_equal_without_cancellation():
+    """oracle_mlp_grad_mag: with nonnegative weights, biases and inputs and
+    negative targets nothing cancels and every ReLU is open, so the
+    magnitudes equal the gradient and outputs themselves; with signed
+    parameters they bound them (triangle inequality)."""
+    rng = np.random.default_rng(26)
+    D, H, d, B = 5, 9, 3, 11
+    n = O.mlp_size(D, H, d)
+    th = np.abs(rng.standard_normal(n)) * 0.3
+    X = np.abs(rng.standard_normal((B, D)))
+    T = -np.abs(rng.standard_normal((B, d))) - 0.5
+    _, g, out = O.mlp_grad(th, X, T, H, round_bf16=False)
+    gm, om = O.mlp_grad_mag(th, X, T, H)
+    np.testing.assert_allclose(gm, g, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(om, out, rtol=1e-12, atol=0)
+    th = rng.standard_normal(n) * 0.3
+    X = rng.standard_normal((B, D))
+    T = rng.standard_normal((B, d))
+    _, g, out = O.mlp_grad(th, X, T, H, round_bf16=False)
+    gm, om = O.mlp_grad_mag(th, X, T, H)
+    assert np.all(np.abs(g) <= gm * (1 + 1e-12)) and np.all(np.abs(out) <= om * (1 + 1e-12))
+    assert np.mean(np.abs(g) < 0.5 * gm) > 0.1  # signed terms do cancel
+
+
 def test_mlp_init_ranges():
     D, H, d = 50, 256, 8
     th = O.mlp_init(D, H, d, 0)
