@@ -156,7 +156,20 @@ int funcsne_create(const float *X, int64_t N, int32_t D, int32_t d, int32_t k_hd
  *   "concurrent"     1: the HD and LD refinements (which only read the state
  *                    of the iteration) run side by side (default 0)
  *   "forces_cw"      floats of an LD row each lane reads in the forces
- *                    kernel: 4, 8 (default) or 16 (a tuning knob)
+ *                    kernel: 4, 8 (default) or 16 (a tuning knob; used when
+ *                    "forces_pair" is 0 or rows are narrower than 8 floats)
+ *   "forces_pair"    1 (default): LD rows of 8 floats (d = 5 ... 8) are
+ *                    read by two lanes with one 16-byte load each, two rows
+ *                    per lane and pass; 0 (and every other row width): the
+ *                    "forces_cw" split
+ *   "ld_pair"        1 (default): the LD refinement reads rows of 8 or more
+ *                    floats the same way; 0: two lanes per row
+ *   "hd_prefetch"    1 (default): the HD refinement loads the next point's
+ *                    lists and copies its own row into a second shared-memory
+ *                    buffer while the current point is scored, where two
+ *                    lanes read a gathered row (rows up to 224 bytes) and the
+ *                    two buffers leave room for four blocks per SM
+ *                    (read-only "hd_prefetch_used" tells); 0: off
  *   "jump_iters"     jump start (Section 3): during the first jump_iters
  *                    iterations no gradient is applied; instead, at the start
  *                    of each of "jump_parts" (default 2) equal parts, Y is

@@ -60,6 +60,10 @@ struct funcsne {
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     bool concurrent = false;  // run the two refinements side by side in the graph
     int32_t forces_cw = 8;    // floats of an LD row per lane in the forces kernel
+    int32_t forces_pair = 1;  // the row-pair layout of the forces (rows of 8+ floats)
+    int32_t ld_pair = 1;      // the row-pair layout of the LD refinement's distances
+    int32_t hd_prefetch = 1;  // HD refinement pipelined over the points of a warp (option)
+    int32_t hd_pf_used = 0;   // ... in use: rows read by two lanes, room for four blocks
     int32_t hd_lanes_opt = 0; // lanes per gathered HD row (0: chosen from the row bytes)
     int32_t insert_rounds = 64; // neighbour-of-neighbour rounds of an insertion
     int32_t jump_iters = 0, jump_parts = 2;  // jump start by linear projections
@@ -159,7 +163,8 @@ StepParams step_params(const funcsne* h) {
     p.coin_p0 = h->coin_floor;
     p.coin_p1 = 1.0 - h->coin_floor;
     p.xs_floats = h->xs_floats;
-    p.smem_per_warp = h->xs_floats * 4 + kHashSlots * 4;
+    p.smem_per_warp = (h->hd_pf_used ? 2 : 1) * h->xs_floats * 4 + kHashSlots * 4;
+    p.hd_prefetch = h->hd_pf_used;
     p.gf = hd_lanes_f32(h);
     p.ga = hd_lanes(h);
     p.alpha = h->alpha;
@@ -219,6 +224,13 @@ UpdateParams update_params(const funcsne* h, float* dbg_att, float* dbg_rep) {
     return u;
 }
 
+// The row-pair forces kernel runs fewer instructions only on rows of 8
+// floats (measured on GB300: 0.166 against 0.180 ms on the 200,000-point
+// swiss roll at d = 8; slower at d = 16 and 32, where its extra shuffles
+// outweigh the halved cache-line wavefronts).
+bool use_forces_pair(const funcsne* h) { return h->forces_pair && h->DP == 8; }
+bool use_ld_pair(const funcsne* h) { return h->ld_pair && h->DP >= 8; }
+
 // The phase kernels of one iteration: 0 HD refinement, 1 LD refinement,
 // 2 forces, 3 update.
 constexpr int kPhases = 4;
@@ -231,8 +243,10 @@ cudaError_t launch_phase(const funcsne* h, int phase, const StepParams& p, cudaS
                 case FUNCSNE_BF16: return hd_refine_launch_bf16(p, h->RH, p.ga, h->hd_blocks, h->hd_smem, s);
                 default: return hd_refine_launch_fp8(p, h->RH, p.ga, h->hd_blocks, h->hd_smem, s);
             }
-        case 1: return ld_refine_launch(p, h->DP, h->RH, h->ld_blocks, h->ld_smem, s);
-        case 2: return forces_launch(p, h->DP, h->RH, h->forces_cw, h->fo_blocks, h->fo_smem, s);
+        case 1: return ld_refine_launch(p, h->DP, h->RH, use_ld_pair(h), h->ld_blocks, h->ld_smem, s);
+        case 2:
+            if (use_forces_pair(h)) return forces_pair_launch(p, h->DP, h->RH, h->fo_blocks, h->fo_smem, s);
+            return forces_launch(p, h->DP, h->RH, h->forces_cw, h->fo_blocks, h->fo_smem, s);
         default: return update_launch(update_params(h, nullptr, nullptr), h->update_blocks, s);
     }
 }
@@ -249,19 +263,33 @@ int grid_for_occupancy(const funcsne* h, int occ) {
 }
 
 int configure_step(funcsne* h) {
-    h->hd_smem = static_cast<size_t>(8) * (h->xs_floats * 4 + kHashSlots * 4);
-    h->ld_smem = h->fo_smem = static_cast<size_t>(8) * kHashSlots * 4;
-    int occ = 0;
-    switch (h->precision) {
-        case FUNCSNE_FP32: occ = hd_refine_occupancy_f32(h->RH, hd_lanes(h), h->hd_smem); break;
-        case FUNCSNE_BF16: occ = hd_refine_occupancy_bf16(h->RH, hd_lanes(h), h->hd_smem); break;
-        default: occ = hd_refine_occupancy_fp8(h->RH, hd_lanes(h), h->hd_smem); break;
-    }
+    auto hd_occ = [&](bool pf, size_t smem) {
+        switch (h->precision) {
+            case FUNCSNE_FP32: return hd_refine_occupancy_f32(h->RH, hd_lanes(h), pf, smem);
+            case FUNCSNE_BF16: return hd_refine_occupancy_bf16(h->RH, hd_lanes(h), pf, smem);
+            default: return hd_refine_occupancy_fp8(h->RH, hd_lanes(h), pf, smem);
+        }
+    };
+    const size_t smem1 = static_cast<size_t>(8) * (h->xs_floats * 4 + kHashSlots * 4);
+    const size_t smem2 = static_cast<size_t>(8) * (2 * h->xs_floats * 4 + kHashSlots * 4);
+    // Pipelining pays where two lanes read a gathered row (rows up to 224
+    // bytes). Measured on GB300, HD refinement per iteration: 1M points at
+    // D = 50, FP32 1.228 to 1.133 ms, BF16 1.231 to 1.190 ms; 200,000
+    // points at D = 128 with FP8 rows 0.501 to 0.471 ms. Rows read by four
+    // or eight lanes gained at most 1% or lost (FP32 at D = 128: 0.319 to
+    // 0.412 ms). The kernel is built for four resident blocks; rows whose two
+    // buffers leave room for fewer run the single-buffer kernel.
+    h->hd_pf_used = h->hd_prefetch && hd_lanes(h) <= 2 && hd_occ(true, smem2) >= 4 ? 1 : 0;
+    h->hd_smem = h->hd_pf_used ? smem2 : smem1;
+    h->ld_smem = static_cast<size_t>(8) * kHashSlots * 4;
+    h->fo_smem = static_cast<size_t>(8) * (kHashSlots + (use_forces_pair(h) ? kRepRing : 0)) * 4;
+    const int occ = hd_occ(h->hd_pf_used != 0, h->hd_smem);
     // the two refinements share the SMs when they run side by side
-    const int ld_occ = ld_refine_occupancy(h->DP, h->RH, h->ld_smem);
+    const int ld_occ = ld_refine_occupancy(h->DP, h->RH, use_ld_pair(h), h->ld_smem);
     h->hd_blocks = grid_for_occupancy(h, h->concurrent ? (occ + 1) / 2 : occ);
     h->ld_blocks = grid_for_occupancy(h, h->concurrent ? (ld_occ + 1) / 2 : ld_occ);
-    h->fo_blocks = grid_for_occupancy(h, forces_occupancy(h->DP, h->RH, h->forces_cw, h->fo_smem));
+    h->fo_blocks = grid_for_occupancy(h, use_forces_pair(h) ? forces_pair_occupancy(h->DP, h->RH, h->fo_smem)
+                                                            : forces_occupancy(h->DP, h->RH, h->forces_cw, h->fo_smem));
     int64_t ub = (h->yelem / 4 + 255) / 256;
     if (ub > 4L * h->num_sms) ub = 4L * h->num_sms;
     if (ub < 1) ub = 1;
@@ -804,6 +832,10 @@ int funcsne_set_option(funcsne_t* h, const char* key, double v) {
         if (v != 4 && v != 8 && v != 16) return fail(h, FUNCSNE_E_ARG, "forces_cw must be 4, 8 or 16");
         h->forces_cw = static_cast<int32_t>(v);
         configure_step(h);
+    } else if (k == "forces_pair" || k == "ld_pair" || k == "hd_prefetch") {
+        if (v != 0 && v != 1) return fail(h, FUNCSNE_E_ARG, "%s must be 0 or 1", key);
+        (k == "forces_pair" ? h->forces_pair : k == "ld_pair" ? h->ld_pair : h->hd_prefetch) = static_cast<int32_t>(v);
+        configure_step(h);
     } else if (k == "perplexity") {
         if (!(v > 1) || !(v < h->k_hd + 1))
             return fail(h, FUNCSNE_E_ARG, "perplexity must be in (1, k_hd + 1)");
@@ -874,6 +906,10 @@ int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
     else if (k == "precision") *v = h->precision;
     else if (k == "concurrent") *v = h->concurrent ? 1 : 0;
     else if (k == "forces_cw") *v = h->forces_cw;
+    else if (k == "forces_pair") *v = h->forces_pair;
+    else if (k == "ld_pair") *v = h->ld_pair;
+    else if (k == "hd_prefetch") *v = h->hd_prefetch;
+    else if (k == "hd_prefetch_used") *v = h->hd_pf_used;
     else if (k == "hd_lanes") *v = h->hd_lanes_opt;
     else if (k == "hd_lanes_used") *v = hd_lanes(h);
     else if (k == "insert_rounds") *v = h->insert_rounds;

@@ -637,6 +637,19 @@ __device__ __forceinline__ ApproxDist group_dist_fp8(const float* __restrict__ x
     return band_from_row_error(my_acc, my_err, gamma);
 }
 
+// ---------------------------------------------------------------- asynchronous copies
+// 16-byte global-to-shared copies that complete in the background
+// (cp.async, L2 only): issued for the next point while the current one is
+// processed, then waited for by group.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // ---------------------------------------------------------------- warp hash sets
 // Open-addressing set of point indices in shared memory (256 slots, linear
 // probing, EMPTY = 0xffffffff). At most 96 entries are ever inserted, so an

@@ -71,13 +71,16 @@ struct InsertParams {
 cudaError_t hd_refine_launch_f32(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s);
 cudaError_t hd_refine_launch_bf16(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s);
 cudaError_t hd_refine_launch_fp8(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s);
-int hd_refine_occupancy_f32(int RH, int G, size_t smem);
-int hd_refine_occupancy_bf16(int RH, int G, size_t smem);
-int hd_refine_occupancy_fp8(int RH, int G, size_t smem);
-cudaError_t ld_refine_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
+int hd_refine_occupancy_f32(int RH, int G, bool pf, size_t smem);
+int hd_refine_occupancy_bf16(int RH, int G, bool pf, size_t smem);
+int hd_refine_occupancy_fp8(int RH, int G, bool pf, size_t smem);
+cudaError_t ld_refine_launch(const StepParams& p, int DP, int RH, bool pair, int blocks, size_t smem, cudaStream_t s);
 cudaError_t forces_launch(const StepParams& p, int DP, int RH, int CW, int blocks, size_t smem, cudaStream_t s);
-int ld_refine_occupancy(int DP, int RH, size_t smem);
+int ld_refine_occupancy(int DP, int RH, bool pair, size_t smem);
 int forces_occupancy(int DP, int RH, int CW, size_t smem);
+// forces with the row-pair layout (DP = 8, 16 or 32)
+cudaError_t forces_pair_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
+int forces_pair_occupancy(int DP, int RH, size_t smem);
 cudaError_t update_launch(const UpdateParams& u, int blocks, cudaStream_t s);
 
 // set-up

@@ -44,6 +44,9 @@ constexpr int kBisectMaxIt = 64;
 constexpr int kHdAdaptive = 0, kHdAlways = 1, kHdNever = 2;
 
 constexpr int kHashSlots = 256;  // per-warp membership set in shared memory
+// Per-warp queue of repulsion-only rows in the row-pair forces kernel: it
+// holds fewer than (rows per pass) + 32 <= 64 entries at any time.
+constexpr int kRepRing = 64;
 
 // Device-resident scalars of the method (one per handle).
 struct DevScalars {
@@ -88,6 +91,7 @@ struct StepParams {
     int32_t hd_mode;
     double coin_p0, coin_p1;  // refinement probability coin_p0 + coin_p1 E
     int32_t smem_per_warp;  // bytes
+    int32_t hd_prefetch;    // HD refinement pipelined over a warp's points (two row buffers)
     int32_t xs_floats;      // own-row floats staged per warp
     int32_t gf, ga;         // lanes per row: FP32 rows, reduced-precision rows (1, 2, 4 or 8)
     float alpha, inv_alpha, inv2N, neg_scale, log_perp;

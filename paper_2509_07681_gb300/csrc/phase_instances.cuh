@@ -15,28 +15,32 @@ namespace fsne {
 
 template <int XM>
 cudaError_t hd_refine_launch_xm(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s) {
-#define FSNE_CASE(rh, g)                                                                \
-    if (RH == rh && G == g) {                                                           \
-        FSNE_SET_SMEM((hd_refine_kernel<rh, XM, g>), smem);                             \
-        hd_refine_kernel<rh, XM, g><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);       \
+#define FSNE_CASE2(rh, g, pf)                                                           \
+    if (RH == rh && G == g && (p.hd_prefetch != 0) == pf) {                             \
+        FSNE_SET_SMEM((hd_refine_kernel<rh, XM, g, pf>), smem);                         \
+        hd_refine_kernel<rh, XM, g, pf><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);   \
         return cudaGetLastError();                                                      \
     }
+#define FSNE_CASE(rh, g) FSNE_CASE2(rh, g, false) FSNE_CASE2(rh, g, true)
     FSNE_HD_CASES(FSNE_CASE)
 #undef FSNE_CASE
+#undef FSNE_CASE2
     return cudaErrorInvalidValue;
 }
 
 template <int XM>
-int hd_refine_occupancy_xm(int RH, int G, size_t smem) {
+int hd_refine_occupancy_xm(int RH, int G, bool pf, size_t smem) {
     int n = 0;
-#define FSNE_CASE(rh, g)                                                                           \
-    if (RH == rh && G == g) {                                                                      \
-        FSNE_SET_SMEM((hd_refine_kernel<rh, XM, g>), smem);                                        \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hd_refine_kernel<rh, XM, g>, kWarpsPerBlock * 32, smem); \
+#define FSNE_CASE2(rh, g, PF)                                                                      \
+    if (RH == rh && G == g && pf == PF) {                                                          \
+        FSNE_SET_SMEM((hd_refine_kernel<rh, XM, g, PF>), smem);                                    \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hd_refine_kernel<rh, XM, g, PF>, kWarpsPerBlock * 32, smem); \
         return n;                                                                                  \
     }
+#define FSNE_CASE(rh, g) FSNE_CASE2(rh, g, false) FSNE_CASE2(rh, g, true)
     FSNE_HD_CASES(FSNE_CASE)
 #undef FSNE_CASE
+#undef FSNE_CASE2
     return 0;
 }
 

@@ -54,20 +54,27 @@ __device__ __forceinline__ ListView list_view(const StepParams& p, int hc, int l
 // ------------------------------------------------------------------ HD refinement
 // Resident blocks per SM the registers are sized for: the kernel waits
 // mostly on memory; the reduced-precision variants with k_hd <= 32 fit five
-// blocks (40 warps) with little spilling, the others four.
-template <int XM, int RH>
-constexpr int hd_refine_min_blocks() { return (XM != 0 && RH == 1) ? 5 : 4; }
+// blocks (40 warps) with little spilling, the others four. The pipelined
+// variant (PF) holds the next point's lists in registers and keeps four
+// blocks (64 registers), which it hides latency with instead.
+template <int XM, int RH, bool PF>
+constexpr int hd_refine_min_blocks() { return (XM != 0 && RH == 1 && !PF) ? 5 : 4; }
 
 // G: lanes per gathered row, of the FP32 rows (XM = 0) or of the BF16 / FP8
 // rows (the exact re-rank then takes the FP32 rows' p.gf at run time).
-template <int RH, int XM, int G>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, hd_refine_min_blocks<XM, RH>())
+// PF: software pipelining over the points of a warp: the next point's lists
+// are loaded into registers and its own row is copied into the second of two
+// shared-memory row buffers (cp.async) while the current point is scored,
+// which takes two memory round trips off every point's chain of dependent
+// loads.
+template <int RH, int XM, int G, bool PF>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, hd_refine_min_blocks<XM, RH, PF>())
 hd_refine_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    float* xs = reinterpret_cast<float*>(smem + wib * p.smem_per_warp);
-    uint32_t* tab = reinterpret_cast<uint32_t*>(xs + p.xs_floats);
+    float* const xbuf = reinterpret_cast<float*>(smem + wib * p.smem_per_warp);
+    uint32_t* tab = reinterpret_cast<uint32_t*>(xbuf + (PF ? 2 : 1) * p.xs_floats);
     __shared__ unsigned long long s_cnt[kWarpsPerBlock][3];
 
     const DevScalars* sc = p.sc;
@@ -77,26 +84,70 @@ hd_refine_kernel(const StepParams p) {
     const uint32_t N = static_cast<uint32_t>(p.N);
     const int k_hd = p.k_hd, k_ld = p.k_ld;
 
-    for (int f = p.xpitch + lane; f < p.xs_floats; f += 32) xs[f] = 0.f;
+    for (int f = p.xpitch + lane; f < p.xs_floats; f += 32) {
+        xbuf[f] = 0.f;
+        if (PF) xbuf[p.xs_floats + f] = 0.f;
+    }
     unsigned long long c_new = 0, c_scored = 0, c_rerank = 0;
 
-    const int64_t tw = static_cast<int64_t>(gridDim.x) * kWarpsPerBlock;
-    for (int64_t gi = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + wib; gi < p.N; gi += tw) {
-        const uint32_t i = static_cast<uint32_t>(gi);
-        uint32_t hidx[RH];
-        float hd2[RH];
+    // the lists of point g (HD indices and distances, LD indices)
+    auto load_lists = [&](int64_t g, uint32_t (&hi)[RH], float (&h2)[RH], uint32_t& li) {
 #pragma unroll
         for (int r = 0; r < RH; ++r) {
             const int e = r * 32 + lane;
-            hidx[r] = e < k_hd ? static_cast<uint32_t>(__ldg(L.hd_idx_c + gi * k_hd + e)) : 0xffffffffu;
-            hd2[r] = e < k_hd ? __ldg(L.hd_d2_c + gi * k_hd + e) : __uint_as_float(0x7f800000u);
+            hi[r] = e < k_hd ? static_cast<uint32_t>(__ldg(L.hd_idx_c + g * k_hd + e)) : 0xffffffffu;
+            h2[r] = e < k_hd ? __ldg(L.hd_d2_c + g * k_hd + e) : __uint_as_float(0x7f800000u);
         }
-        const uint32_t lidx = lane < k_ld ? static_cast<uint32_t>(__ldg(L.ld_idx_c + gi * k_ld + lane)) : 0xffffffffu;
+        li = lane < k_ld ? static_cast<uint32_t>(__ldg(L.ld_idx_c + g * k_ld + lane)) : 0xffffffffu;
+    };
+    // point g's own FP32 row into the row buffer dst, asynchronously; one
+    // commit group per call on every lane (empty for g >= N)
+    auto stage_row = [&](int64_t g, float* dst) {
+        if (g < p.N) {
+            const float* xrow = p.X32 + g * p.xpitch;
+            for (int f = lane * 4; f < p.xpitch; f += 128) cp_async16(dst + f, xrow + f);
+        }
+        cp_async_commit();
+    };
+    const int64_t tw = static_cast<int64_t>(gridDim.x) * kWarpsPerBlock;
+    const int64_t g0 = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    uint32_t n_hidx[RH];
+    float n_hd2[RH];
+    uint32_t n_lidx = 0;
+    int buf = 0;
+    if constexpr (PF) {
+        if (g0 < p.N) load_lists(g0, n_hidx, n_hd2, n_lidx);
+        stage_row(g0, xbuf);
+    }
+    for (int64_t gi = g0; gi < p.N; gi += tw) {
+        const uint32_t i = static_cast<uint32_t>(gi);
+        uint32_t hidx[RH];
+        float hd2[RH];
+        uint32_t lidx;
+        float* xs = xbuf;
+        if constexpr (PF) {
+#pragma unroll
+            for (int r = 0; r < RH; ++r) {
+                hidx[r] = n_hidx[r];
+                hd2[r] = n_hd2[r];
+            }
+            lidx = n_lidx;
+            const int64_t gn = gi + tw;
+            if (gn < p.N) load_lists(gn, n_hidx, n_hd2, n_lidx);
+            stage_row(gn, xbuf + (buf ^ 1) * p.xs_floats);
+            xs = xbuf + buf * p.xs_floats;
+        } else {
+            load_lists(gi, hidx, hd2, lidx);
+        }
         const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
-        __syncwarp();
-        const float* xrow = p.X32 + gi * p.xpitch;
-        for (int f = lane * 4; f < p.xpitch; f += 128)
-            *reinterpret_cast<float4*>(xs + f) = __ldg(reinterpret_cast<const float4*>(xrow + f));
+        if constexpr (PF) {
+            cp_async_wait<1>();  // this point's row has landed
+        } else {
+            __syncwarp();
+            const float* xrow = p.X32 + gi * p.xpitch;
+            for (int f = lane * 4; f < p.xpitch; f += 128)
+                *reinterpret_cast<float4*>(xs + f) = __ldg(reinterpret_cast<const float4*>(xrow + f));
+        }
         hset_clear(tab, lane);
         __syncwarp();
 #pragma unroll
@@ -175,7 +226,9 @@ hd_refine_kernel(const StepParams p) {
             ++c_new;
         }
         __syncwarp();
+        buf ^= 1;
     }
+    if constexpr (PF) cp_async_wait<0>();
     unsigned long long cs = c_scored, cr = c_rerank;
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) {
@@ -288,7 +341,60 @@ __device__ __forceinline__ float group_ld_dist(const float (&yi)[DP / G], const 
 template <int DP>
 __host__ __device__ constexpr int ld_lanes() { return DP >= 8 ? 2 : 1; }
 
-template <int DP, int RH>
+// Reduce-scatter of G values over the G lanes of a row group (xor partners
+// G/2, ..., 1, recursive halving): afterwards v[0] of lane s of the group
+// holds the group sum of element s.
+template <int G, int C = G>
+__device__ __forceinline__ void group_reduce_scatter(float (&v)[G], int s) {
+    if constexpr (C > 1) {
+        constexpr int H = C / 2;
+        const bool up = (s & H) != 0;
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const float send = up ? v[k] : v[k + H];
+            const float keep = up ? v[k + H] : v[k];
+            v[k] = keep + __shfl_xor_sync(kFull, send, H);
+        }
+        group_reduce_scatter<G, H>(v, s);
+    }
+}
+
+// Squared LD distances from y_i to row cv of Y for the row of every lane
+// (0 where cv == kNoRow), rows of DP >= 8 floats read by G = DP/4 lanes with
+// one 16-byte load each: G warp loads of R1 = 32/G whole rows each (one
+// cache-line wavefront per row). Lane l holds components 4 (l mod G) ... of
+// y_i in yi. The partial sums are reduce-scattered inside each group and one
+// shuffle hands every lane its own row's sum. All lanes call it.
+template <int DP>
+__device__ __forceinline__ float ld_dist_rows(const float4 yi, const float* __restrict__ Y, uint32_t cv,
+                                              int lane) {
+    constexpr int G = DP / 4, R1 = 32 / G;
+    const int g = lane / G, s = lane % G;
+    float ps[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        const uint32_t cj = __shfl_sync(kFull, cv, q * R1 + g);
+        const float4 v = cj != kNoRow ? __ldg(reinterpret_cast<const float4*>(Y + static_cast<int64_t>(cj) * DP + 4 * s))
+                                      : yi;
+        float d = __fsub_rn(yi.x, v.x);
+        float a = __fmul_rn(d, d);
+        d = __fsub_rn(yi.y, v.y);
+        a = __fmaf_rn(d, d, a);
+        d = __fsub_rn(yi.z, v.z);
+        a = __fmaf_rn(d, d, a);
+        d = __fsub_rn(yi.w, v.w);
+        ps[q] = __fmaf_rn(d, d, a);
+    }
+    group_reduce_scatter<G>(ps, s);
+    // lane (g, s) now holds row s R1 + g; row l sits on lane (l mod R1) G + l / R1
+    return __shfl_sync(kFull, ps[0], (lane % R1) * G + lane / R1);
+}
+
+// PAIR: rows of 8 or more floats are gathered by ld_dist_rows (DP/4 lanes
+// per row, one 16-byte load each), and the neighbour-of-neighbour index
+// loads are issued before the old list's rows are gathered, so the two
+// memory round trips overlap. Otherwise group_ld_dist with ld_lanes lanes.
+template <int DP, int RH, bool PAIR>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
 ld_refine_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -313,28 +419,59 @@ ld_refine_kernel(const StepParams p) {
             hidx[r] = e < k_hd ? static_cast<uint32_t>(__ldg(L.hd_idx_c + gi * k_hd + e)) : 0xffffffffu;
         }
         const uint32_t lidx = lane < k_ld ? static_cast<uint32_t>(__ldg(L.ld_idx_c + gi * k_ld + lane)) : 0xffffffffu;
-        constexpr int GL = ld_lanes<DP>();
-        float yi[DP / GL];
-        load_chunk<DP / GL>(Y + gi * DP + (DP / GL) * (lane % GL), yi);
-        const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
-        hset_clear(tab, lane);
-        __syncwarp();
-        if (lane < k_ld) hset_insert(tab, lidx);
-        const uint32_t e0 = lane < kLdNnEnd ? map_index(w.z, k_ld) : map_index(w.z, k_hd);
-        const uint32_t lv = __shfl_sync(kFull, lidx, static_cast<int>(e0 & 31u));
-        const uint32_t hv = warp_get<RH>(hidx, e0);
-        uint32_t c;
-        if (lane < kLdNnEnd)
-            c = static_cast<uint32_t>(__ldg(L.ld_idx_c + static_cast<int64_t>(lv) * k_ld + map_index(w.w, k_ld)));
-        else if (lane < kLdHdNbEnd)
-            c = hv;
-        else
-            c = map_other(w.z, N, i);
-        __syncwarp();
-        bool valid = (c != i) && (c < N) && !hset_has(tab, c);
-        valid &= (__match_any_sync(kFull, c) & ((1u << lane) - 1u)) == 0u;
-        const float d_old = group_ld_dist<DP, GL>(yi, Y, lane < k_ld ? lidx : kNoRow, lane);
-        const float d_c = group_ld_dist<DP, GL>(yi, Y, valid ? c : kNoRow, lane);
+        float d_old, d_c;
+        uint32_t cand_c;
+        bool cand_valid;
+        if constexpr (PAIR) {
+            const float4 yi = __ldg(reinterpret_cast<const float4*>(Y + gi * DP + 4 * (lane % (DP / 4))));
+            const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+            const uint32_t e0 = lane < kLdNnEnd ? map_index(w.z, k_ld) : map_index(w.z, k_hd);
+            const uint32_t lv = __shfl_sync(kFull, lidx, static_cast<int>(e0 & 31u));
+            const uint32_t hv = warp_get<RH>(hidx, e0);
+            // in flight while the old list's rows are gathered
+            const uint32_t cnn =
+                lane < kLdNnEnd
+                    ? static_cast<uint32_t>(__ldg(L.ld_idx_c + static_cast<int64_t>(lv) * k_ld + map_index(w.w, k_ld)))
+                    : 0u;
+            d_old = ld_dist_rows<DP>(yi, Y, lane < k_ld ? lidx : kNoRow, lane);
+            hset_clear(tab, lane);
+            __syncwarp();
+            if (lane < k_ld) hset_insert(tab, lidx);
+            const uint32_t c = lane < kLdNnEnd ? cnn : (lane < kLdHdNbEnd ? hv : map_other(w.z, N, i));
+            __syncwarp();
+            bool valid = (c != i) && (c < N) && !hset_has(tab, c);
+            valid &= (__match_any_sync(kFull, c) & ((1u << lane) - 1u)) == 0u;
+            d_c = ld_dist_rows<DP>(yi, Y, valid ? c : kNoRow, lane);
+            cand_c = c;
+            cand_valid = valid;
+        } else {
+            constexpr int GL = ld_lanes<DP>();
+            float yi[DP / GL];
+            load_chunk<DP / GL>(Y + gi * DP + (DP / GL) * (lane % GL), yi);
+            const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+            hset_clear(tab, lane);
+            __syncwarp();
+            if (lane < k_ld) hset_insert(tab, lidx);
+            const uint32_t e0 = lane < kLdNnEnd ? map_index(w.z, k_ld) : map_index(w.z, k_hd);
+            const uint32_t lv = __shfl_sync(kFull, lidx, static_cast<int>(e0 & 31u));
+            const uint32_t hv = warp_get<RH>(hidx, e0);
+            uint32_t c;
+            if (lane < kLdNnEnd)
+                c = static_cast<uint32_t>(__ldg(L.ld_idx_c + static_cast<int64_t>(lv) * k_ld + map_index(w.w, k_ld)));
+            else if (lane < kLdHdNbEnd)
+                c = hv;
+            else
+                c = map_other(w.z, N, i);
+            __syncwarp();
+            bool valid = (c != i) && (c < N) && !hset_has(tab, c);
+            valid &= (__match_any_sync(kFull, c) & ((1u << lane) - 1u)) == 0u;
+            d_old = group_ld_dist<DP, GL>(yi, Y, lane < k_ld ? lidx : kNoRow, lane);
+            d_c = group_ld_dist<DP, GL>(yi, Y, valid ? c : kNoRow, lane);
+            cand_c = c;
+            cand_valid = valid;
+        }
+        const uint32_t c = cand_c;
+        const bool valid = cand_valid;
         uint64_t lk[1] = {lane < k_ld ? make_key(d_old, lidx) : kSentinel};
         const uint64_t ck = valid ? make_key(d_c, c) : kSentinel;
         // the old list ordered under the distances at Y_t, then the candidates
@@ -537,6 +674,216 @@ forces_kernel(const StepParams p) {
                     atomicAdd(p.A + gi * DP + co + e, v[q]);
                 else
                     p.R[gi * DP + co + e - CW] = v[q];
+            }
+        }
+        z = warp_sum(z);
+        z_acc += static_cast<double>(z);
+        __syncwarp();
+    }
+    if (lane == 0) s_z[wib] = z_acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double zb = 0.0;
+        for (int v = 0; v < kWarpsPerBlock; ++v) zb += s_z[v];
+        p.zpart[blockIdx.x] = zb;
+    }
+}
+
+// ------------------------------------------------------------------ forces, row-pair layout
+// The same forces as forces_kernel, laid out for the L1 data pipe, which
+// bounds this kernel: every gathered LD row (DP floats) is read by G = DP/4
+// lanes with one 16-byte load each, so one warp load touches R1 = 32/G whole
+// rows (one cache-line wavefront per row instead of one per 16-byte column
+// of a row), and each lane takes two rows per pass (slots m = 0, 1 at rows
+// b + m R1 + lane/G), which keeps the rows per pass of the two-lane split.
+// The repulsion-only rows (LD neighbours outside the HD list, then the
+// negatives outside S_i) are appended to a per-warp queue in shared memory
+// as they are found and consumed R rows at a time, so slots that contribute
+// nothing cost no pass.
+template <int DP>
+struct PairSplit {
+    static constexpr int G = DP / 4;    // lanes per row, one float4 each
+    static constexpr int R1 = 32 / G;   // rows per warp load
+    static constexpr int R = 2 * R1;    // rows per pass (two slots per lane)
+};
+
+template <int DP, int RH>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+forces_pair_kernel(const StepParams p) {
+    using S = PairSplit<DP>;
+    constexpr int G = S::G, R1 = S::R1, R = S::R;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint32_t* tab = reinterpret_cast<uint32_t*>(smem) + wib * (kHashSlots + kRepRing);
+    uint32_t* ring = tab + kHashSlots;
+    __shared__ double s_z[kWarpsPerBlock];
+
+    const DevScalars* sc = p.sc;
+    const uint32_t t = sc->t;
+    const bool fire = hd_coin(t, sc->E, p.seed, p.hd_mode, p.coin_p0, p.coin_p1);
+    // lists of iteration t+1: the HD buffer flips only when the coin fired
+    const int32_t* __restrict__ hd_new = (sc->hd_cur ^ (fire ? 1 : 0)) ? p.hd_idx1 : p.hd_idx0;
+    const int32_t* __restrict__ ld_new = sc->ld_cur ? p.ld_idx0 : p.ld_idx1;
+    const float invZ = static_cast<float>(1.0 / sc->Zhat);
+    const uint32_t N = static_cast<uint32_t>(p.N);
+    const int k_hd = p.k_hd, k_ld = p.k_ld;
+    const float* __restrict__ Y = p.Y;
+    const float alpha = p.alpha, inv_alpha = p.inv_alpha;
+    const int gq = lane / G;          // row slot of this lane within a warp load
+    const int co = 4 * (lane % G);    // first component owned by this lane
+    const bool leader = (lane % G) == 0;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    double z_acc = 0.0;
+    const int64_t tw = static_cast<int64_t>(gridDim.x) * kWarpsPerBlock;
+    for (int64_t gi = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + wib; gi < p.N; gi += tw) {
+        const uint32_t i = static_cast<uint32_t>(gi);
+        uint32_t nh[RH];
+        float pv[RH];
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            const int e = r * 32 + lane;
+            nh[r] = e < k_hd ? static_cast<uint32_t>(__ldg(hd_new + gi * k_hd + e)) : 0xffffffffu;
+            pv[r] = e < k_hd ? p.P[gi * k_hd + e] : 0.f;
+        }
+        const uint32_t nl = lane < k_ld ? static_cast<uint32_t>(__ldg(ld_new + gi * k_ld + lane)) : 0xffffffffu;
+        const float4 yi = __ldg(reinterpret_cast<const float4*>(Y + gi * DP + co));
+        const uint4 wq = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+        // S_i = HD u LD lists of t+1 as a warp hash set
+        hset_clear(tab, lane);
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < RH; ++r)
+            if (r * 32 + lane < k_hd) hset_insert(tab, nh[r]);
+        __syncwarp();
+        const bool ld_in_hd = lane < k_ld && hset_has(tab, nl);
+        __syncwarp();
+        if (lane < k_ld) hset_insert(tab, nl);
+
+        float att[4] = {0.f, 0.f, 0.f, 0.f}, rep[4] = {0.f, 0.f, 0.f, 0.f};
+        float z = 0.f;
+        // Two rows per lane: r2, w and w^{1/alpha} of rows j[0], j[1]
+        // (kNoRow: no row, contributes nothing) and this lane's components
+        // of y_i - y_j. Every lane executes it (group reductions are shuffles).
+        auto interact2 = [&](const uint32_t (&j)[2], float (&dy)[2][4], float (&w)[2], float (&winv)[2]) {
+            float4 yj[2];
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+                yj[m] = j[m] != kNoRow ? __ldg(reinterpret_cast<const float4*>(Y + static_cast<int64_t>(j[m]) * DP + co))
+                                       : yi;
+            float r2[2];
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                dy[m][0] = __fsub_rn(yi.x, yj[m].x);
+                dy[m][1] = __fsub_rn(yi.y, yj[m].y);
+                dy[m][2] = __fsub_rn(yi.z, yj[m].z);
+                dy[m][3] = __fsub_rn(yi.w, yj[m].w);
+                float a = __fmul_rn(dy[m][0], dy[m][0]);
+                a = __fmaf_rn(dy[m][1], dy[m][1], a);
+                a = __fmaf_rn(dy[m][2], dy[m][2], a);
+                r2[m] = __fmaf_rn(dy[m][3], dy[m][3], a);
+            }
+#pragma unroll
+            for (int q = 1; q < G; q <<= 1) {
+                r2[0] += __shfl_xor_sync(kFull, r2[0], q);
+                r2[1] += __shfl_xor_sync(kFull, r2[1], q);
+            }
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const bool on = j[m] != kNoRow;
+                winv[m] = on ? __fdividef(1.f, __fmaf_rn(r2[m], inv_alpha, 1.f)) : 0.f;
+                w[m] = (alpha == 1.f || !on) ? winv[m] : exp2f(alpha * __log2f(winv[m]));
+            }
+        };
+        // HD neighbours: attraction (both directions of p_ij) and repulsion
+        for (int b = 0; b < k_hd; b += R) {
+            uint32_t j[2];
+            float pe[2];
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int e = b + m * R1 + gq;
+                const uint32_t jj = warp_get<RH>(nh, static_cast<uint32_t>(e));
+                pe[m] = warp_get<RH>(pv, static_cast<uint32_t>(e));
+                j[m] = e < k_hd ? jj : kNoRow;
+            }
+            float dy[2][4], w[2], winv[2];
+            interact2(j, dy, w, winv);
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const float fa = 4.f * pe[m] * p.inv2N * winv[m];
+                const float fr = 4.f * w[m] * invZ * winv[m];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    att[c] = __fmaf_rn(fa, dy[m][c], att[c]);
+                    rep[c] = __fmaf_rn(fr, dy[m][c], rep[c]);
+                }
+                if (leader) z += w[m];
+                if (j[m] != kNoRow)
+                    atomicAdd(reinterpret_cast<float4*>(p.A + static_cast<int64_t>(j[m]) * DP + co),
+                              make_float4(-fa * dy[m][0], -fa * dy[m][1], -fa * dy[m][2], -fa * dy[m][3]));
+            }
+        }
+        // repulsion-only rows through the queue: positions [head, tail) of
+        // the stream (LD rows outside the HD list first, nld of them, then
+        // the negatives outside S_i scaled by (N-1)/n_neg)
+        int head = 0, tail = 0, nld = 0;
+        auto consume = [&](bool last) {
+            while (tail - head >= R || (last && tail > head)) {
+                __syncwarp();
+                uint32_t j[2];
+                float scl[2];
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int pos = head + m * R1 + gq;
+                    j[m] = pos < tail ? ring[pos & (kRepRing - 1)] : kNoRow;
+                    scl[m] = pos < nld ? 1.f : p.neg_scale;
+                }
+                float dy[2][4], w[2], winv[2];
+                interact2(j, dy, w, winv);
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const float fr = scl[m] * 4.f * w[m] * invZ * winv[m];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) rep[c] = __fmaf_rn(fr, dy[m][c], rep[c]);
+                    if (leader) z = __fmaf_rn(scl[m], w[m], z);
+                }
+                head = min(head + R, tail);
+            }
+        };
+        {
+            const bool keep = lane < k_ld && !ld_in_hd;
+            const unsigned mk = __ballot_sync(kFull, keep);
+            if (keep) ring[(tail + __popc(mk & lt_mask)) & (kRepRing - 1)] = nl;
+            tail += __popc(mk);
+            nld = tail;
+        }
+        __syncwarp();
+        for (int s0 = 0; s0 < p.n_neg; s0 += 32) {
+            consume(false);
+            const int sidx = s0 + lane;
+            const uint32_t j = map_other(negative_word(wq.y, wq.w, static_cast<uint32_t>(s0 >> 5)), N, i);
+            const bool on = sidx < p.n_neg && !hset_has(tab, j);
+            const unsigned mk = __ballot_sync(kFull, on);
+            if (on) ring[(tail + __popc(mk & lt_mask)) & (kRepRing - 1)] = j;
+            tail += __popc(mk);
+        }
+        consume(true);
+        // sum over the row groups, scattered over the lanes that share lane
+        // mod G: each lane ends with elements of (A_i, R_i) restricted to its
+        // components, which it adds to A_i or stores into R_i
+        float v[8] = {att[0], att[1], att[2], att[3], rep[0], rep[1], rep[2], rep[3]};
+        int base = 0;
+        bool owner = true;
+        reduce_scatter_stages<8, 8, 16, G>(v, lane, base, owner);
+        if (owner) {
+#pragma unroll
+            for (int q = 0; q < scatter_count<8, G>(); ++q) {
+                const int e = base + q;
+                if (e < 4)
+                    atomicAdd(p.A + gi * DP + co + e, v[q]);
+                else
+                    p.R[gi * DP + co + e - 4] = v[q];
             }
         }
         z = warp_sum(z);

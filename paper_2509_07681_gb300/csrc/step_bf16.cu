@@ -6,6 +6,6 @@ namespace fsne {
 cudaError_t hd_refine_launch_bf16(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s) {
     return hd_refine_launch_xm<1>(p, RH, G, blocks, smem, s);
 }
-int hd_refine_occupancy_bf16(int RH, int G, size_t smem) { return hd_refine_occupancy_xm<1>(RH, G, smem); }
+int hd_refine_occupancy_bf16(int RH, int G, bool pf, size_t smem) { return hd_refine_occupancy_xm<1>(RH, G, pf, smem); }
 
 }  // namespace fsne

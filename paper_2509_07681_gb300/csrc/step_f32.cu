@@ -7,20 +7,28 @@ namespace fsne {
 cudaError_t hd_refine_launch_f32(const StepParams& p, int RH, int G, int blocks, size_t smem, cudaStream_t s) {
     return hd_refine_launch_xm<0>(p, RH, G, blocks, smem, s);
 }
-int hd_refine_occupancy_f32(int RH, int G, size_t smem) { return hd_refine_occupancy_xm<0>(RH, G, smem); }
+int hd_refine_occupancy_f32(int RH, int G, bool pf, size_t smem) { return hd_refine_occupancy_xm<0>(RH, G, pf, smem); }
 
 #define FSNE_DP_RH(X)                                                                           \
     X(2, 1) X(4, 1) X(8, 1) X(16, 1) X(32, 1) X(2, 2) X(4, 2) X(8, 2) X(16, 2) X(32, 2)
 
-cudaError_t ld_refine_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s) {
-#define FSNE_CASE(dp, rh)                                                                       \
-    if (DP == dp && RH == rh) {                                                                 \
-        FSNE_SET_SMEM((ld_refine_kernel<dp, rh>), smem);                                        \
-        ld_refine_kernel<dp, rh><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);                  \
+// The row-pair layout of the LD distances (rows of 8, 16 or 32 floats).
+#define FSNE_PAIR_DP_RH(X) X(8, 1) X(16, 1) X(32, 1) X(8, 2) X(16, 2) X(32, 2)
+
+cudaError_t ld_refine_launch(const StepParams& p, int DP, int RH, bool pair, int blocks, size_t smem, cudaStream_t s) {
+#define FSNE_CASE2(dp, rh, pr)                                                                  \
+    if (DP == dp && RH == rh && pair == pr) {                                                   \
+        FSNE_SET_SMEM((ld_refine_kernel<dp, rh, pr>), smem);                                    \
+        ld_refine_kernel<dp, rh, pr><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);              \
         return cudaGetLastError();                                                              \
     }
+#define FSNE_CASE(dp, rh) FSNE_CASE2(dp, rh, false)
+#define FSNE_CASE_P(dp, rh) FSNE_CASE2(dp, rh, true)
     FSNE_DP_RH(FSNE_CASE)
+    FSNE_PAIR_DP_RH(FSNE_CASE_P)
+#undef FSNE_CASE_P
 #undef FSNE_CASE
+#undef FSNE_CASE2
     return cudaErrorInvalidValue;
 }
 
@@ -41,15 +49,44 @@ cudaError_t forces_launch(const StepParams& p, int DP, int RH, int CW, int block
     return cudaErrorInvalidValue;
 }
 
-int ld_refine_occupancy(int DP, int RH, size_t smem) {
+cudaError_t forces_pair_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s) {
+#define FSNE_CASE(dp, rh)                                                                       \
+    if (DP == dp && RH == rh) {                                                                 \
+        FSNE_SET_SMEM((forces_pair_kernel<dp, rh>), smem);                                      \
+        forces_pair_kernel<dp, rh><<<blocks, kWarpsPerBlock * 32, smem, s>>>(p);                \
+        return cudaGetLastError();                                                              \
+    }
+    FSNE_PAIR_DP_RH(FSNE_CASE)
+#undef FSNE_CASE
+    return cudaErrorInvalidValue;
+}
+
+int forces_pair_occupancy(int DP, int RH, size_t smem) {
     int n = 0;
 #define FSNE_CASE(dp, rh)                                                                       \
     if (DP == dp && RH == rh) {                                                                 \
-        FSNE_SET_SMEM((ld_refine_kernel<dp, rh>), smem);                                        \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ld_refine_kernel<dp, rh>, kWarpsPerBlock * 32, smem); \
+        FSNE_SET_SMEM((forces_pair_kernel<dp, rh>), smem);                                      \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, forces_pair_kernel<dp, rh>, kWarpsPerBlock * 32, smem); \
     }
-    FSNE_DP_RH(FSNE_CASE)
+    FSNE_PAIR_DP_RH(FSNE_CASE)
 #undef FSNE_CASE
+    return n;
+}
+
+int ld_refine_occupancy(int DP, int RH, bool pair, size_t smem) {
+    int n = 0;
+#define FSNE_CASE2(dp, rh, pr)                                                                  \
+    if (DP == dp && RH == rh && pair == pr) {                                                   \
+        FSNE_SET_SMEM((ld_refine_kernel<dp, rh, pr>), smem);                                    \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ld_refine_kernel<dp, rh, pr>, kWarpsPerBlock * 32, smem); \
+    }
+#define FSNE_CASE(dp, rh) FSNE_CASE2(dp, rh, false)
+#define FSNE_CASE_P(dp, rh) FSNE_CASE2(dp, rh, true)
+    FSNE_DP_RH(FSNE_CASE)
+    FSNE_PAIR_DP_RH(FSNE_CASE_P)
+#undef FSNE_CASE_P
+#undef FSNE_CASE
+#undef FSNE_CASE2
     return n;
 }
 

@@ -458,7 +458,7 @@ class FuncSNE:
 
     CHECKPOINT_OPTIONS = ("lr", "momentum", "att_ratio", "rep_ratio", "exaggeration", "exag_iters", "hd_mode",
                           "precision", "alpha", "perplexity", "concurrent", "surrogate", "mlp_every", "mlp_lr",
-                          "mlp_batch", "mlp_hidden", "forces_cw", "hd_lanes", "insert_rounds",
+                          "mlp_batch", "mlp_hidden", "forces_cw", "forces_pair", "ld_pair", "hd_lanes", "insert_rounds",
                           "jump_iters", "jump_parts", "coin_floor", "gamma_e", "gamma_z")
 
     def save(self, path):
@@ -481,7 +481,7 @@ class FuncSNE:
         d, k_hd, k_ld, n_neg = (int(v) for v in z["params"])
         m = cls(z["X"], d, k_hd, k_ld, n_neg, float(z["alpha0"]), float(z["perplexity0"]), seed=int(z["seed"]))
         opts = dict(zip(z["opt_keys"].tolist(), z["opt_vals"].tolist()))
-        for k in ("precision", "hd_lanes", "forces_cw", "concurrent", "mlp_batch", "mlp_hidden"):
+        for k in ("precision", "hd_lanes", "forces_cw", "forces_pair", "ld_pair", "concurrent", "mlp_batch", "mlp_hidden"):
             m.set_option(k, opts.pop(k))
         perp = opts.pop("perplexity")
         for k, v in opts.items():
