@@ -37,6 +37,30 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads over points. Every loop that runs in parallel writes only its own
+ * point's results, and every sum over points or neighbours runs in a fixed
+ * index order, so the results do not depend on the thread count. */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------ */
 /* Philox4x32-10, from Salmon, Moraes, Dror, Shaw, "Parallel random     */
@@ -150,6 +174,7 @@ typedef struct {
     double coin_floor;    /* refinement probability floor + (1-floor) E    */
     double gamma_e;       /* smoothing rate of E[N_new/N]                  */
     double gamma_z;       /* smoothing rate of the normalisation estimate  */
+    int32_t fresh_iters;  /* iterations a new point is refined for (0: off) */
     /* state */
     const double *X;      /* N x D                                          */
     double *Y, *V;        /* N x d                                          */
@@ -160,6 +185,8 @@ typedef struct {
     double *P;            /* N x k_hd: p_{j|i} aligned with hd_idx           */
     double Zhat, E;
     uint32_t t;
+    int64_t fresh_lo;     /* points fresh_lo .. N-1 were inserted recently   */
+    uint32_t fresh_until; /* ... and are refined while t < fresh_until      */
 } oracle_state;
 
 /* Squared Euclidean distance, the plain definition. */
@@ -483,74 +510,102 @@ double oracle_forces(const oracle_state *st, uint32_t t, uint32_t neg_stream, do
     int64_t N = st->N;
     int d = st->d, kh = st->k_hd, kl = st->k_ld;
     double alpha = st->alpha;
-    memset(A, 0, sizeof(double) * (size_t)(N * d));
-    memset(R, 0, sizeof(double) * (size_t)(N * d));
-    double ztotal = 0.0;
-    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)(kh + kl));
-    char *inS = NULL;
-    if (st->neg_mode == 1) inS = (char *)malloc((size_t)N);
-    for (int64_t i = 0; i < N; ++i) {
-        const double *yi = st->Y + i * d;
-        /* attraction over the HD list */
-        for (int a = 0; a < kh; ++a) {
-            int64_t j = st->hd_idx[i * kh + a];
-            const double *yj = st->Y + j * d;
-            double r2 = sqdist(yi, yj, d);
-            double coef = 4.0 * (st->P[i * kh + a] / (2.0 * (double)N)) * kernel_w_inv_alpha(r2, alpha);
-            for (int c = 0; c < d; ++c) {
-                double f = coef * (yi[c] - yj[c]);
-                A[i * d + c] += f;
-                A[j * d + c] -= f;
-            }
-        }
-        /* S_i = HD list, then LD entries not in the HD list */
-        int ns = 0;
-        for (int a = 0; a < kh; ++a) S[ns++] = st->hd_idx[i * kh + a];
-        for (int a = 0; a < kl; ++a) {
-            int32_t j = st->ld_idx[i * kl + a];
-            if (!contains(st->hd_idx + i * kh, kh, j)) S[ns++] = j;
-        }
-        double zi = 0.0;
-        for (int a = 0; a < ns; ++a) {
-            const double *yj = st->Y + (int64_t)S[a] * d;
-            double r2 = sqdist(yi, yj, d);
-            double w = kernel_w(r2, alpha);
-            double coef = 4.0 * (w / zhat) * kernel_w_inv_alpha(r2, alpha);
-            for (int c = 0; c < d; ++c) R[i * d + c] += coef * (yi[c] - yj[c]);
-            zi += w;
-        }
-        if (st->neg_mode == 1) {
-            memset(inS, 0, (size_t)N);
-            for (int a = 0; a < ns; ++a) inS[S[a]] = 1;
-            for (int64_t j = 0; j < N; ++j) {
-                if (j == i || inS[j]) continue;
+    /* the lists that hold each point: (source i, slot a) with
+     * hd_idx[i kh + a] = j, by increasing i, for the reverse attraction */
+    int64_t *rstart = (int64_t *)calloc((size_t)(N + 1), sizeof(int64_t));
+    int64_t *rsrc = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N * kh > 0 ? N * kh : 1));
+    for (int64_t e = 0; e < N * kh; ++e) rstart[st->hd_idx[e] + 1] += 1;
+    for (int64_t j = 0; j < N; ++j) rstart[j + 1] += rstart[j];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+        memcpy(fill, rstart, sizeof(int64_t) * (size_t)N);
+        for (int64_t e = 0; e < N * kh; ++e) rsrc[fill[st->hd_idx[e]]++] = e;
+        free(fill);
+    }
+    double *zpt = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+#pragma omp parallel
+    {
+        int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)(kh + kl));
+        char *inS = NULL;
+        if (st->neg_mode == 1) inS = (char *)malloc((size_t)N);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < N; ++i) {
+            const double *yi = st->Y + i * d;
+            double *Ai = A + i * d, *Ri = R + i * d;
+            for (int c = 0; c < d; ++c) Ai[c] = Ri[c] = 0.0;
+            /* attraction: the pairs of i's own list, in list order ... */
+            for (int a = 0; a < kh; ++a) {
+                int64_t j = st->hd_idx[i * kh + a];
                 const double *yj = st->Y + j * d;
+                double r2 = sqdist(yi, yj, d);
+                double coef = 4.0 * (st->P[i * kh + a] / (2.0 * (double)N)) * kernel_w_inv_alpha(r2, alpha);
+                for (int c = 0; c < d; ++c) Ai[c] += coef * (yi[c] - yj[c]);
+            }
+            /* ... then the pairs of the lists that hold i (p_{i|s} of Eq. 1,
+             * symmetrised), by increasing source s */
+            for (int64_t q = rstart[i]; q < rstart[i + 1]; ++q) {
+                int64_t e = rsrc[q], src = e / kh;
+                const double *ys = st->Y + src * d;
+                double r2 = sqdist(ys, yi, d);
+                double coef = 4.0 * (st->P[e] / (2.0 * (double)N)) * kernel_w_inv_alpha(r2, alpha);
+                for (int c = 0; c < d; ++c) Ai[c] -= coef * (ys[c] - yi[c]);
+            }
+            /* S_i = HD list, then LD entries not in the HD list */
+            int ns = 0;
+            for (int a = 0; a < kh; ++a) S[ns++] = st->hd_idx[i * kh + a];
+            for (int a = 0; a < kl; ++a) {
+                int32_t j = st->ld_idx[i * kl + a];
+                if (!contains(st->hd_idx + i * kh, kh, j)) S[ns++] = j;
+            }
+            double zi = 0.0;
+            for (int a = 0; a < ns; ++a) {
+                const double *yj = st->Y + (int64_t)S[a] * d;
                 double r2 = sqdist(yi, yj, d);
                 double w = kernel_w(r2, alpha);
                 double coef = 4.0 * (w / zhat) * kernel_w_inv_alpha(r2, alpha);
-                for (int c = 0; c < d; ++c) R[i * d + c] += coef * (yi[c] - yj[c]);
+                for (int c = 0; c < d; ++c) Ri[c] += coef * (yi[c] - yj[c]);
                 zi += w;
             }
-        } else {
-            double scale = (double)(N - 1) / (double)st->n_neg;
-            for (int s = 0; s < st->n_neg; ++s) {
-                uint32_t w4[4];
-                draw4(st->seed, t, (uint32_t)i, neg_stream, (uint32_t)(s % 32), w4);
-                int64_t j = map_other(negative_word(w4[1], w4[3], (uint32_t)(s / 32)), N, i);
-                if (contains(S, ns, j)) continue;
-                const double *yj = st->Y + j * d;
-                double r2 = sqdist(yi, yj, d);
-                double w = kernel_w(r2, alpha);
-                double coef = scale * 4.0 * (w / zhat) * kernel_w_inv_alpha(r2, alpha);
-                for (int c = 0; c < d; ++c) R[i * d + c] += coef * (yi[c] - yj[c]);
-                zi += scale * w;
+            if (st->neg_mode == 1) {
+                memset(inS, 0, (size_t)N);
+                for (int a = 0; a < ns; ++a) inS[S[a]] = 1;
+                for (int64_t j = 0; j < N; ++j) {
+                    if (j == i || inS[j]) continue;
+                    const double *yj = st->Y + j * d;
+                    double r2 = sqdist(yi, yj, d);
+                    double w = kernel_w(r2, alpha);
+                    double coef = 4.0 * (w / zhat) * kernel_w_inv_alpha(r2, alpha);
+                    for (int c = 0; c < d; ++c) Ri[c] += coef * (yi[c] - yj[c]);
+                    zi += w;
+                }
+            } else {
+                double scale = (double)(N - 1) / (double)st->n_neg;
+                for (int s = 0; s < st->n_neg; ++s) {
+                    uint32_t w4[4];
+                    draw4(st->seed, t, (uint32_t)i, neg_stream, (uint32_t)(s % 32), w4);
+                    int64_t j = map_other(negative_word(w4[1], w4[3], (uint32_t)(s / 32)), N, i);
+                    if (contains(S, ns, j)) continue;
+                    const double *yj = st->Y + j * d;
+                    double r2 = sqdist(yi, yj, d);
+                    double w = kernel_w(r2, alpha);
+                    double coef = scale * 4.0 * (w / zhat) * kernel_w_inv_alpha(r2, alpha);
+                    for (int c = 0; c < d; ++c) Ri[c] += coef * (yi[c] - yj[c]);
+                    zi += scale * w;
+                }
             }
+            zpt[i] = zi;
         }
-        if (z_per_point) z_per_point[i] = zi;
-        ztotal += zi;
+        free(S);
+        free(inS);
     }
-    free(S);
-    free(inS);
+    double ztotal = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (z_per_point) z_per_point[i] = zpt[i];
+        ztotal += zpt[i];
+    }
+    free(zpt);
+    free(rstart);
+    free(rsrc);
     return ztotal;
 }
 
@@ -606,6 +661,7 @@ void oracle_init(oracle_state *st, double bisect_tol, int bisect_maxit)
 {
     int64_t N = st->N;
     int D = st->D, d = st->d, kh = st->k_hd, kl = st->k_ld;
+#pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < N; ++i) {
         oracle_initial_list(st->seed, N, i, kh, STREAM_INIT_HD, st->hd_idx + i * kh);
         sort_hd_list(st, i);
@@ -613,6 +669,7 @@ void oracle_init(oracle_state *st, double bisect_tol, int bisect_maxit)
     }
     project_y(st, 0u);
     memset(st->V, 0, sizeof(double) * (size_t)(N * d));
+#pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < N; ++i)
         oracle_bisect(st->hd_d2 + i * kh, kh, st->perplexity, 0.0, bisect_tol, bisect_maxit,
                       st->beta + i, st->P + i * kh);
@@ -645,7 +702,10 @@ int oracle_coin(const oracle_state *st)
  * writes iteration t+1):
  *   1. coin; if it fires, HD refinement of every point from the lists of t,
  *      flags for points whose set changed, and warm-restart recalibration of
- *      beta and P for flagged points;
+ *      beta and P for flagged points; if it does not fire but points were
+ *      inserted within the last fresh_iters iterations (t < fresh_until),
+ *      the same refinement of only those points (fresh_lo .. N-1), which
+ *      leaves E unchanged;
  *   2. LD refinement of every point from the lists of t and Y_t;
  *   3. forces with the new lists, P and Y_t, Zhat_t;
  *   4. g = att * exag * A - rep * R; V = momentum V - lr g; Y += V;
@@ -679,39 +739,54 @@ void oracle_step(oracle_state *st, double bisect_tol, int bisect_maxit, double *
             if ((int64_t)st->t == ((int64_t)p * st->jump_iters) / parts) project_y(st, (uint32_t)(p + 1));
     }
     int fire = oracle_coin(st);
+    /* recently inserted points are refined in every iteration of their
+     * window (an addition for points added on the fly, Section 3) */
+    int fresh = !fire && st->fresh_iters > 0 && st->t < st->fresh_until && st->fresh_lo < N;
+    int64_t lo = fire ? 0 : st->fresh_lo;
     int64_t n_new = 0;
-    int64_t cand[CAND_HD > CAND_LD ? CAND_HD : CAND_LD];
-    double cd2[CAND_HD > CAND_LD ? CAND_HD : CAND_LD];
-    double *old_d2 = (double *)malloc(sizeof(double) * (size_t)(kh > kl ? kh : kl));
-    double *ld_new_d2 = (double *)malloc(sizeof(double) * (size_t)kl);
-    if (fire) {
-        for (int64_t i = 0; i < N; ++i) {
-            oracle_hd_candidates(st, i, cand);
-            for (int s = 0; s < CAND_HD; ++s)
-                cd2[s] = (cand[s] == i) ? 0.0 : sqdist(st->X + i * D, st->X + cand[s] * D, D);
-            for (int a = 0; a < kh; ++a)
-                old_d2[a] = sqdist(st->X + i * D, st->X + (int64_t)st->hd_idx[i * kh + a] * D, D);
-            flags[i] = (uint8_t)oracle_topk_merge(i, kh, st->hd_idx + i * kh, old_d2, CAND_HD,
-                                                  cand, cd2, nh_idx + i * kh, nh_d2 + i * kh);
-            n_new += flags[i];
+    if (fire || fresh) {
+#pragma omp parallel
+        {
+            int64_t cand[CAND_HD];
+            double cd2[CAND_HD];
+            double *old_d2 = (double *)malloc(sizeof(double) * (size_t)kh);
+#pragma omp for schedule(dynamic, 64)
+            for (int64_t i = lo; i < N; ++i) {
+                oracle_hd_candidates(st, i, cand);
+                for (int s = 0; s < CAND_HD; ++s)
+                    cd2[s] = (cand[s] == i) ? 0.0 : sqdist(st->X + i * D, st->X + cand[s] * D, D);
+                for (int a = 0; a < kh; ++a)
+                    old_d2[a] = sqdist(st->X + i * D, st->X + (int64_t)st->hd_idx[i * kh + a] * D, D);
+                flags[i] = (uint8_t)oracle_topk_merge(i, kh, st->hd_idx + i * kh, old_d2, CAND_HD,
+                                                      cand, cd2, nh_idx + i * kh, nh_d2 + i * kh);
+            }
+            free(old_d2);
         }
-        for (int64_t i = 0; i < N; ++i)
+        for (int64_t i = lo; i < N; ++i) n_new += flags[i];
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t i = lo; i < N; ++i)
             if (flags[i])
                 oracle_bisect(nh_d2 + i * kh, kh, st->perplexity, st->beta[i], bisect_tol,
                               bisect_maxit, st->beta + i, st->P + i * kh);
     }
-    for (int64_t i = 0; i < N; ++i) {
-        oracle_ld_candidates(st, i, cand);
-        for (int s = 0; s < CAND_LD; ++s)
-            cd2[s] = (cand[s] == i) ? 0.0 : sqdist(st->Y + i * d, st->Y + cand[s] * d, d);
-        for (int a = 0; a < kl; ++a) {
-            nl_idx[i * kl + a] = st->ld_idx[i * kl + a];
-            ld_new_d2[a] = sqdist(st->Y + i * d, st->Y + (int64_t)st->ld_idx[i * kl + a] * d, d);
+#pragma omp parallel
+    {
+        int64_t cand[CAND_LD];
+        double cd2[CAND_LD];
+        double *ld_new_d2 = (double *)malloc(sizeof(double) * (size_t)kl);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < N; ++i) {
+            oracle_ld_candidates(st, i, cand);
+            for (int s = 0; s < CAND_LD; ++s)
+                cd2[s] = (cand[s] == i) ? 0.0 : sqdist(st->Y + i * d, st->Y + cand[s] * d, d);
+            for (int a = 0; a < kl; ++a) {
+                nl_idx[i * kl + a] = st->ld_idx[i * kl + a];
+                ld_new_d2[a] = sqdist(st->Y + i * d, st->Y + (int64_t)st->ld_idx[i * kl + a] * d, d);
+            }
+            oracle_ld_merge(i, kl, nl_idx + i * kl, ld_new_d2, CAND_LD, cand, cd2);
         }
-        oracle_ld_merge(i, kl, nl_idx + i * kl, ld_new_d2, CAND_LD, cand, cd2);
+        free(ld_new_d2);
     }
-    free(old_d2);
-    free(ld_new_d2);
     /* install the lists of iteration t+1 before the forces */
     memcpy(st->hd_idx, nh_idx, sizeof(int32_t) * (size_t)(N * kh));
     memcpy(st->hd_d2, nh_d2, sizeof(double) * (size_t)(N * kh));
@@ -949,6 +1024,12 @@ void oracle_insert(oracle_state *st, int64_t n_old, int rounds, double bisect_to
     st->Zhat = st->Zhat * ratio;
     double frac = (double)(N - n_old) / (double)N;
     if (frac > st->E) st->E = frac;
+    /* the new points' refinement window: the next fresh_iters iterations; a
+     * window still open keeps its older points in it */
+    if (st->fresh_iters > 0) {
+        if (!(st->t < st->fresh_until)) st->fresh_lo = n_old;
+        st->fresh_until = st->t + (uint32_t)st->fresh_iters;
+    }
     free(list);
     free(ld2);
     free(nl);
@@ -1348,6 +1429,9 @@ int64_t oracle_remove(oracle_state *st, const uint8_t *removed, double bisect_to
     st->Zhat *= ((double)Nk * (double)(Nk - 1)) / ((double)N * (double)(N - 1));
     if (nr / (double)N > st->E) st->E = nr / (double)N;
     st->N = Nk;
+    /* renumbering closes the refinement window of recent insertions */
+    st->fresh_lo = Nk;
+    st->fresh_until = st->t;
     oracle_recalibrate(st, bisect_tol, bisect_maxit);
     free(map);
     return Nk;

@@ -11,7 +11,7 @@ import numpy as np
 
 from .build import build_oracle
 
-__all__ = ["lib", "philox", "OracleState", "bf16", "mlp_size", "mlp_init", "mlp_grad", "mlp_grad_mag", "mlp_forward", "adam", "bisect", "entropy", "topk_merge", "ld_merge",
+__all__ = ["lib", "set_threads", "threads", "philox", "OracleState", "bf16", "mlp_size", "mlp_init", "mlp_grad", "mlp_grad_mag", "mlp_forward", "adam", "bisect", "entropy", "topk_merge", "ld_merge",
            "exact_z", "kl_divergence", "exact_grad", "bruteforce_knn", "query_knn",
            "ORACLE_BISECT_TOL", "ORACLE_BISECT_MAXIT", "STREAMS", "CAND_HD", "CAND_LD"]
 
@@ -47,13 +47,18 @@ class _State(C.Structure):
                 ("momentum", C.c_double), ("att_ratio", C.c_double), ("rep_ratio", C.c_double),
                 ("exaggeration", C.c_double), ("exag_iters", C.c_int32), ("hd_mode", C.c_int32),
                 ("neg_mode", C.c_int32), ("jump_iters", C.c_int32), ("jump_parts", C.c_int32),
-                ("coin_floor", C.c_double), ("gamma_e", C.c_double), ("gamma_z", C.c_double), ("X", _dp), ("Y", _dp), ("V", _dp), ("hd_idx", _ip),
+                ("coin_floor", C.c_double), ("gamma_e", C.c_double), ("gamma_z", C.c_double),
+                ("fresh_iters", C.c_int32), ("X", _dp), ("Y", _dp), ("V", _dp), ("hd_idx", _ip),
                 ("hd_d2", _dp), ("ld_idx", _ip), ("beta", _dp), ("P", _dp), ("Zhat", C.c_double),
-                ("E", C.c_double), ("t", C.c_uint32)]
+                ("E", C.c_double), ("t", C.c_uint32), ("fresh_lo", C.c_int64), ("fresh_until", C.c_uint32)]
 
 
 def _declare(L):
     sp = C.POINTER(_State)
+    L.oracle_set_threads.argtypes = [C.c_int]
+    L.oracle_set_threads.restype = None
+    L.oracle_threads.argtypes = []
+    L.oracle_threads.restype = C.c_int
     L.oracle_philox4x32_10.argtypes = [_up, _up, _up]
     L.oracle_philox4x32_10.restype = None
     L.oracle_entropy.argtypes = [_dp, C.c_int, C.c_double, _dp]
@@ -121,6 +126,16 @@ def _p(a, t):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_threads(n):
+    """Threads the oracle uses over points (its results do not depend on
+    it); n <= 0 restores one per core."""
+    lib().oracle_set_threads(int(n))
+
+
+def threads():
+    return int(lib().oracle_threads())
 
 
 def philox(ctr, key):
@@ -281,7 +296,7 @@ class OracleState:
     def __init__(self, X, d, k_hd, k_ld, n_neg, alpha, perplexity, seed=0, lr=None,
                  momentum=0.8, att_ratio=1.0, rep_ratio=1.0, exaggeration=1.0, exag_iters=0,
                  hd_mode=0, neg_mode=0, jump_iters=0, jump_parts=2, coin_floor=0.05, gamma_e=0.1,
-                 gamma_z=0.1, init=True):
+                 gamma_z=0.1, fresh_iters=0, init=True):
         self.X = _f64(X)
         N, D = self.X.shape
         self.N, self.D = N, D
@@ -301,6 +316,7 @@ class OracleState:
         s.exaggeration, s.exag_iters, s.hd_mode, s.neg_mode = exaggeration, exag_iters, hd_mode, neg_mode
         s.jump_iters, s.jump_parts = jump_iters, jump_parts
         s.coin_floor, s.gamma_e, s.gamma_z = coin_floor, gamma_e, gamma_z
+        s.fresh_iters, s.fresh_lo, s.fresh_until = fresh_iters, N, 0
         self._s = s
         self._bind()
         if init:
@@ -321,7 +337,8 @@ class OracleState:
     def __getattr__(self, name):
         if name in ("Zhat", "E", "t", "lr", "momentum", "att_ratio", "rep_ratio", "exaggeration",
                     "exag_iters", "hd_mode", "neg_mode", "jump_iters", "jump_parts", "coin_floor", "gamma_e",
-                    "gamma_z", "alpha", "perplexity", "seed", "n_neg", "k_hd", "k_ld", "d"):
+                    "gamma_z", "fresh_iters", "fresh_lo", "fresh_until", "alpha", "perplexity", "seed", "n_neg",
+                    "k_hd", "k_ld", "d"):
             return getattr(self.__dict__["_s"], name)
         raise AttributeError(name)
 
@@ -330,7 +347,7 @@ class OracleState:
             setattr(self._s, k, v)
 
     def load(self, Y=None, V=None, hd_idx=None, ld_idx=None, beta=None, P=None, Zhat=None,
-             E=None, t=None, d2=True):
+             E=None, t=None, d2=True, fresh_lo=None, fresh_until=None):
         """Overwrite parts of the state (for example with the GPU's exported state).
         HD distances are recomputed in FP64 from X (unless d2 is False: a
         state that will only give forces, which do not read them); the list
@@ -353,6 +370,10 @@ class OracleState:
             self._s.E = E
         if t is not None:
             self._s.t = t
+        if fresh_lo is not None:
+            self._s.fresh_lo = fresh_lo
+        if fresh_until is not None:
+            self._s.fresh_until = fresh_until
         if not d2:
             return
         step = max(1, (1 << 24) // max(1, self.hd_idx.shape[1] * self.D))  # at most 128 MB a chunk

@@ -463,6 +463,51 @@ def test_insertion_rounds():
     assert rec[0] < 0.1 and rec[-1] > 0.9 and rec[-1] >= rec[2] >= rec[1]
 
 
+def test_fresh_window_refines_only_recent_points():
+    """With the coin off (hd_mode 2), an insertion opens a window of
+    fresh_iters iterations in which exactly the new points refine their HD
+    lists: each new point's list of t+1 is the top-k merge of its list of t
+    with its 32 candidates (recomputed here from the state of t), the other
+    points' lists stay, E stays, and changed points are recalibrated to the
+    target entropy. After the window nothing changes; a second insertion
+    inside a window keeps the older points in it; a removal closes it."""
+    X = synth.blobs(n=960, dim=10, n_clusters=4, seed=18)
+    st = O.OracleState(X[:800], 2, 12, 6, 6, 1.0, 6.0, seed=18, hd_mode=2, fresh_iters=4)
+    for _ in range(5):
+        st.step()
+    st.insert(X[800:900], rounds=0)
+    assert st.fresh_lo == 800 and st.fresh_until == st.t + 4
+    for it in range(4):
+        pre = st.copy()
+        e0 = st.E
+        out = st.step()
+        np.testing.assert_array_equal(st.hd_idx[:800], pre.hd_idx[:800])
+        assert st.E == e0 and not out["coin"]
+        changed = 0
+        for i in range(800, 900):
+            cand = pre.hd_candidates(i)
+            cd2 = ((pre.X[cand] - pre.X[i]) ** 2).sum(1)
+            od2 = ((pre.X[pre.hd_idx[i]] - pre.X[i]) ** 2).sum(1)
+            ni, _, ch = O.topk_merge(i, pre.hd_idx[i], od2, cand, cd2)
+            np.testing.assert_array_equal(st.hd_idx[i], ni)
+            if ch:
+                changed += 1
+                h, _ = O.entropy(((st.X[ni] - st.X[i]) ** 2).sum(1), st.beta[i])
+                assert abs(h - np.log(6.0)) < 1e-8
+        assert changed > 0 or it > 0
+    before = st.hd_idx.copy()
+    st.step()
+    np.testing.assert_array_equal(st.hd_idx, before)  # window closed
+    st.step()
+    st.insert(X[900:930], rounds=0)
+    assert st.fresh_lo == 900
+    st.step()
+    st.insert(X[930:], rounds=0)  # inside the open window: it keeps point 900 on
+    assert st.fresh_lo == 900 and st.fresh_until == st.t + 4
+    st.remove(np.array([3, 950]))
+    assert st.fresh_until == st.t and st.fresh_lo == st.N
+
+
 def test_insertion_with_more_ld_than_hd_neighbours():
     X = synth.blobs(n=300, dim=6, n_clusters=3, seed=14)
     st = O.OracleState(X[:250], 2, 8, 12, 4, 1.0, 5.0, seed=14)
@@ -709,3 +754,25 @@ def test_sampled_forces_equal_full_forces():
     As, Rs = st.forces_points(pts, zhat=123.0, t=7)
     np.testing.assert_allclose(As, A[pts], rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(Rs, R[pts], rtol=1e-12, atol=1e-15)
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """The oracle runs its per-point loops on several threads; every sum
+    keeps a fixed index order, so one and four threads give the same bits."""
+    X = synth.spectrum(n=1500, dim=12, n_clusters=6, seed=27)
+    runs = []
+    for nt in (1, 4):
+        O.set_threads(nt)
+        st = O.OracleState(X, 3, 16, 12, 20, 0.8, 9.0, seed=27, hd_mode=0, fresh_iters=3)
+        outs = [st.step() for _ in range(6)]
+        st.insert(synth.spectrum(n=100, dim=12, n_clusters=6, seed=28), rounds=4)
+        outs += [st.step() for _ in range(3)]
+        runs.append((st, outs))
+    O.set_threads(0)
+    (a, oa), (b, ob) = runs
+    for name in ("Y", "V", "hd_idx", "ld_idx", "beta", "P"):
+        np.testing.assert_array_equal(getattr(a, name), getattr(b, name))
+    assert a.Zhat == b.Zhat and a.E == b.E
+    for x, y in zip(oa, ob):
+        np.testing.assert_array_equal(x["A"], y["A"])
+        np.testing.assert_array_equal(x["z"], y["z"])
