@@ -43,14 +43,16 @@ METRIC_OTHER = "iters/s (KNN refine+gradient)"
 UNIT = "iter/s"
 WORKLOAD = "spectrum-1m"
 BURN_IN = 200          # untimed iterations after set-up, so lists are near steady state
+FIG8_ITERS = 3000      # the paper's timing budget (Fig. 8), for the convergence read-out
 RECALL_QUERIES = 1000  # sampled queries for HD-KNN recall against brute force
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129 * 2 ** 20
 # storage precision each workload is quoted on
 HEADLINE = {"blobs-2k": "fp32", "lowrank-2m": "fp8"}
-# points in the CPU oracle's sample: about 10-30 s of oracle work per workload
+# points in the one-core oracle sample: a few seconds of oracle work per workload
 CPU_SAMPLE = {"blobs-2k": 2000, "pixels-70k": 6000, "spectrum-1m": 100000, "swissroll-200k": 40000,
               "lowrank-2m": 12000}
+REF_BUDGET_S = 120.0   # reference arm: seconds of oracle iterations (warm-up + timed)
 
 
 def _env_int(name, default):
@@ -306,6 +308,13 @@ def run_ours(args, rank, world):
         results[name]["lists_equal_fp32_after_steps"] = bool(
             np.array_equal(results[name]["hd_idx"], results["fp32"]["hd_idx"]))
 
+    # convergence at the paper's timing budget (Fig. 8: 3,000 iterations),
+    # headline precision, outside the timed region
+    m.import_state(base)
+    m.set_option("precision", {"fp32": F.FP32, "bf16": F.BF16, "fp8": F.FP8}[headline])
+    m.step(max(0, FIG8_ITERS - int(base["t"])))
+    rec3000 = recall(m.knn(F.SPACE_HD, with_d2=False)[q], exact)
+
     # end to end through the C ABI with host buffers: create from pinned host
     # X (H2D), then every step's embedding lands in pinned host memory (two
     # buffers; frame k is copied out while step k + 1 runs, and the host waits
@@ -313,10 +322,14 @@ def run_ours(args, rank, world):
     m.close()
     Xp = torch.from_numpy(X).pin_memory()
     Yp = [torch.empty((N, p["d"]), dtype=torch.float32).pin_memory() for _ in range(2)]
+    prec_head = {"fp32": F.FP32, "bf16": F.BF16, "fp8": F.FP8}[headline]
     barrier()
     t0 = time.perf_counter()
     m2 = F.FuncSNE(Xp, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0,
-                   hd_mode=1, precision={"fp32": F.FP32, "bf16": F.BF16, "fp8": F.FP8}[headline])
+                   hd_mode=1, precision=prec_head)
+    m2.set_stream(stream)
+    m2.sync()
+    t1 = time.perf_counter()
     for k in range(K):
         m2.step(1)
         if k:
@@ -324,8 +337,25 @@ def run_ours(args, rank, world):
         m2.embedding_async(Yp[k % 2])
     m2.wait_embedding()
     m2.sync()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    t2 = time.perf_counter()
+    e2e_s = max_over_ranks(t2 - t0, dist, "cuda")
     m2.close()
+    # the split of the end-to-end time: the same K iterations from a fresh
+    # state on the device alone (no read-back), against the warm device rate
+    m3 = F.FuncSNE(X, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0,
+                   hd_mode=1, precision=prec_head)
+    m3.set_stream(stream)
+    m3.sync()
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    m3.step(K)
+    c1.record(stream)
+    c1.synchronize()
+    cold_ms = c0.elapsed_time(c1)
+    m3.close()
+    e2e_split = {"create_ms": round((t1 - t0) * 1e3, 2), "steps_with_readback_ms": round((t2 - t1) * 1e3, 2),
+                 "cold_device_steps_ms": round(cold_ms, 2)}
 
     if rank != 0:
         if dist is not None:
@@ -364,7 +394,7 @@ def run_ours(args, rank, world):
                            "rows stay largely in L2"}
     cpu = None
     if world == 1:
-        cpu = cpu_baseline(args, X, p, sample_n=min(N, CPU_SAMPLE.get(args.workload, 20000)), steps=2)
+        cpu = cpu_baseline(args, X, p, single_n=min(N, CPU_SAMPLE.get(args.workload, 20000)), steps=2)
     xq = {"fp32": 4 * D, "bf16": 2 * D + 16, "fp8": D + 4}[headline]
     ws = N * (4 * D + xq + 8 * p["k_hd"] * 2 + 4 * p["k_ld"] * 2 + 4 * p["k_hd"] + 16 * p["d"])
     l2 = ("working set > L2 (%.0f MB vs 129 MB), no flush" % (ws / 1e6) if ws > L2_BYTES else
@@ -392,12 +422,21 @@ def run_ours(args, rank, world):
                        for n, r in results.items()},
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "recall_at_k_hd_after_3000_iterations": round(rec3000, 5),
         "e2e": {"value": round(whole_job_rate(world, K, e2e_s), 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(X.nbytes / K), "d2h_bytes_per_step": int(N * p["d"] * 4),
                 "note": f"create from pinned host X (H2D, init) + K x (step + embedding read-back to pinned host "
-                        f"memory, overlapped with the next step), {headline}"},
-        # kernels of the headline precision's timed region: 4 per iteration
-        "gpu_launches": 4 * K,
+                        f"memory, overlapped with the next step), {headline}",
+                "split": dict(e2e_split, warm_device_steps_ms=round(head["total_ms"], 2),
+                              readback_cost_ms=round(e2e_split["steps_with_readback_ms"]
+                                                     - e2e_split["cold_device_steps_ms"], 2),
+                              cold_start_cost_ms=round(e2e_split["cold_device_steps_ms"] - head["total_ms"], 2),
+                              rule="e2e = create + steps with read-back; read-back cost = those steps minus the "
+                                   "same steps from a fresh state on the device alone; cold-start cost = the "
+                                   "latter minus the same number of warm steps (after the burn-in)")},
+        # kernels of the headline precision's timed region: 5 per iteration
+        # (HD refinement, LD refinement, insertion-window list copy, forces, update)
+        "gpu_launches": 5 * K,
         "clocks": clk,
         "kernel_hash": khash,
     }
@@ -440,7 +479,7 @@ def run_dynamic(args, rank, world):
     clocks.start()
     for arm, place in (("mean", F.PLACE_MEAN), ("surrogate", F.PLACE_SURROGATE)):
         m = F.FuncSNE(X0, p["d"], kh, kl, p["n_neg"], p["alpha"], p["perplexity"], seed=0, precision=F.BF16,
-                      hd_mode=args.hd_mode, insert_rounds=args.insert_rounds)
+                      hd_mode=args.hd_mode, insert_rounds=args.insert_rounds, fresh_iters=args.fresh_iters)
         m.set_stream(stream)
         if arm == "surrogate":
             m.set_option("surrogate", 1)
@@ -539,7 +578,8 @@ def run_dynamic(args, rank, world):
                        "check_every": check, "storage": "bf16 rows + fp32 boundary re-rank",
                        "hd_refine": {0: "adaptive coin", 1: "every iteration", 2: "never"}[args.hd_mode],
                        "mlp": f"{D}-256-256-{p['d']}, batch 4096, every 10 iters",
-                       "mlp_pretrain_steps": args.mlp_pretrain, "insert_rounds": args.insert_rounds},
+                       "mlp_pretrain_steps": args.mlp_pretrain, "insert_rounds": args.insert_rounds,
+                       "fresh_iters": args.fresh_iters},
             "arms": arms, "clocks": clk}
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -547,42 +587,82 @@ def run_dynamic(args, rank, world):
     return line
 
 
-def cpu_baseline(args, X, p, sample_n=None, steps=1):
-    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the
-    workload (the same generator at N=sample_n), timed iterations after its
-    own initialisation, scaled linearly to the full N (the iteration is O(N))."""
-    import oracle as O
-    from paper_2509_07681_gb300 import synth
+def host_cores():
+    """(threads the oracle may use, a one-line description of the host CPU)."""
+    n = os.cpu_count() or 1
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return n, f"{n} logical CPUs" + (f", {model}" if model else "")
 
-    n = sample_n or args.cpu_sample
-    Xs, _ = synth.make(args.workload, n=n)
-    o = O.OracleState(Xs, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0,
-                      hd_mode=1)
+
+def time_oracle(X, p, steps, threads):
+    """Seconds per oracle iteration (HD refinement every iteration), timed
+    after the oracle's own initialisation, on `threads` host threads."""
+    import oracle as O
+    O.set_threads(threads)
+    o = O.OracleState(X, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0, hd_mode=1)
     t0 = time.perf_counter()
     for _ in range(steps):
         o.step()
     dt = (time.perf_counter() - t0) / steps
-    scale = X.shape[0] / n
-    return {"value": round(1.0 / (dt * scale), 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{args.workload} generator at N={n} (same D, d, k, n_neg), {steps} oracle iteration(s) "
-                      f"after its own init, {dt:.2f} s/iter scaled x{scale:.1f} to N={X.shape[0]}"}
+    O.set_threads(0)
+    return dt
+
+
+def cpu_baseline(args, X, p, single_n=None, steps=2):
+    """The FP64 oracle, as it stands, on the host cores: `steps` iterations of
+    the full workload on every core (no extrapolation), and a bounded sample
+    of the same generator (N = single_n) on one core, scaled linearly to the
+    full N (the iteration is O(N)) and labelled as such."""
+    from paper_2509_07681_gb300 import synth
+
+    cores, desc = host_cores()
+    N = X.shape[0]
+    dt = time_oracle(X, p, steps, cores)
+    n1 = min(N, single_n or args.cpu_sample)
+    Xs = X if n1 == N else synth.make(args.workload, n=n1)[0]
+    dt1 = time_oracle(Xs, p, 1, 1)
+    return {"value": round(1.0 / dt, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the full {args.workload} workload (N={N}), {steps} oracle iterations after its own init "
+                      f"on {cores} threads, {dt:.2f} s/iter; host: {desc}",
+            "single_core": {"value": round(1.0 / (dt1 * N / n1), 6), "unit": UNIT, "cores": 1,
+                            "sample": f"N={n1} of the same generator, 1 iteration on 1 thread, {dt1:.2f} s/iter, "
+                                      f"scaled x{N / n1:.1f} to N={N} (extrapolated)"}}
 
 
 def run_reference(args, rank, world):
-    """The oracle on the host cores as the reference arm (rank 0 only)."""
+    """The oracle on the host cores as the reference arm (rank 0 only). Each
+    step is one oracle iteration of a sample of the workload (the same
+    generator at N = n_s <= N), sized from a timed probe so that the warm-up
+    and timed steps take about REF_BUDGET_S seconds; the line's config
+    names that sample, and the rate scaled to the full N is a labelled
+    extra field."""
     if rank != 0:
         return None
-    import oracle as O
     from oracle.build import build_oracle
     from paper_2509_07681_gb300 import synth
 
     build_oracle()
     _, kw, _ = synth.WORKLOADS[args.workload]
-    Xfull_n = kw["n"] if args.n is None else args.n
-    n = min(args.cpu_sample, Xfull_n)
-    Xs, p = synth.make(args.workload, n=n)
+    full_n = kw["n"] if args.n is None else args.n
+    _, p = synth.make(args.workload, n=min(full_n, 2000))
     if args.alpha is not None:
         p = dict(p, alpha=args.alpha)
+    cores, desc = host_cores()
+    # probe: per-point cost of one iteration on every core
+    n_probe = min(full_n, 20000)
+    c = time_oracle(synth.make(args.workload, n=n_probe)[0], p, 1, cores) / n_probe
+    n = int(min(full_n, max(2000, REF_BUDGET_S / (max(args.steps + args.warmup, 1) * c))))
+    Xs, _ = synth.make(args.workload, n=n)
+    import oracle as O
+    O.set_threads(cores)
     o = O.OracleState(Xs, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0, hd_mode=1)
     for _ in range(args.warmup):
         o.step()
@@ -590,18 +670,19 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         o.step()
     dt = (time.perf_counter() - t0) / args.steps
-    scale = Xfull_n / n
-    value = 1.0 / (dt * scale)
-    sample = (f"{args.workload} generator at N={n}, {args.steps} timed oracle iterations after {args.warmup} "
-              f"warm-up, {dt:.3f} s/iter scaled x{scale:.1f} to N={Xfull_n}")
+    value = 1.0 / dt
+    sample = (f"{args.workload} generator at N={n} (full N={full_n}), {args.steps} timed oracle iterations after "
+              f"{args.warmup} warm-up on {cores} threads, {dt:.3f} s/iter; host: {desc}")
     line = {"impl": "reference", "metric": METRIC if args.workload == WORKLOAD else METRIC_OTHER,
             "value": round(value, 6), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * scale * 1e3, 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "N": Xfull_n, "hd_refine": "every iteration"},
-            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "config": {"workload": args.workload, "N": n, "sample_of_N": full_n, "hd_refine": "every iteration"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
+            "extrapolated_to_full_N": {"value": round(value * n / full_n, 6), "unit": UNIT, "N": full_n,
+                                       "rule": "linear in N (the iteration is O(N))"},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return line
@@ -609,20 +690,23 @@ def run_reference(args, rank, world):
 
 def run_feedback(args, rank, world):
     """The feedback loop between the two neighbour searches (Section 3,
-    Fig. 4 and Fig. 7), measured on synthetic data:
-      * HD-KNN recall@k_hd (sampled queries against brute force) along the
-        iterations on the 70,000-point pixels workload, with Y optimised,
-        held at its random-projection start (learning rate 1e-12), or
-        optimised after a 100-iteration jump start of two projections, for
-        d = 2 and d = 8;
-      * HD-KNN recall after 3,000 and 9,000 iterations on 5 overlapping
-        blobs (N = 20,000, centres N(0, I)) and on 1,000 disjoint blobs of
-        30 points (centres N(0, 100 I)), D = 30, d = 2.
-    HD refinement runs every iteration."""
+    Fig. 4 and Fig. 7), measured on synthetic data with the paper's quality
+    measure: R_NX(K) of the estimated HD neighbour lists against the exact
+    ones, K = 1 .. k_hd (the lists hold k_hd entries; the paper's curves
+    reach K = 256 with longer lists), and its AUC on log K.
+      * Fig. 4: AUC of R_NX along the iterations on the 70,000-point pixels
+        workload (2,000 sampled points), with Y optimised, held at its
+        random-projection start (learning rate 1e-12), or optimised after a
+        100-iteration jump start of two projections, for d = 2 and d = 8;
+      * Fig. 7: R_NX(K) (mean and standard deviation across the sampled
+        points) after 3,000 and 9,000 iterations on 5 overlapping blobs
+        (N = 20,000, centres N(0, I)) and on 1,000 disjoint blobs of 30 points
+        (centres N(0, 100 I)), D = 30, d = 2.
+    HD refinement runs every iteration. Recall@k_hd is reported alongside."""
     import torch
     from paper_2509_07681_gb300 import funcsne as F
     from paper_2509_07681_gb300 import synth
-    from paper_2509_07681_gb300.quality import recall
+    from paper_2509_07681_gb300.quality import recall, rnx_auc, rnx_points
 
     local, dist = _setup_gpu(world)
     stream = torch.cuda.Stream()
@@ -644,15 +728,19 @@ def run_feedback(args, rank, world):
                 m.set_option("jump_parts", 2)
             if exact is None:
                 exact, _ = m.exact_knn(q, p["k_hd"])
-            curve, done = [], 0
+            auc, rec, done = [], [], 0
             for c in checkpoints:
                 m.step(c - done)
                 done = c
-                curve.append(round(recall(m.knn(F.SPACE_HD, with_d2=False)[q], exact), 4))
-            out["fig4"][f"d={d} {mode}"] = dict(zip(map(str, checkpoints), curve))
+                hd = m.knn(F.SPACE_HD, with_d2=False)[q]
+                auc.append(round(rnx_auc(hd, exact, N), 4))
+                rec.append(round(recall(hd, exact), 4))
+            out["fig4"][f"d={d} {mode}"] = {"rnx_auc": dict(zip(map(str, checkpoints), auc)),
+                                            "recall": dict(zip(map(str, checkpoints), rec))}
             m.close()
     sets = {"5 overlapping blobs": synth.blobs(n=20000, dim=30, n_clusters=5, centre_std=1.0, seed=7),
             "1000 disjoint blobs x 30": synth.blobs(n=30000, dim=30, n_clusters=1000, centre_std=10.0, seed=8)}
+    ks = [1, 2, 4, 8, 16, 32]
     for name, Xb in sets.items():
         m = F.FuncSNE(Xb, 2, 32, 16, 16, 1.0, 30.0, seed=0, hd_mode=1)
         m.set_stream(stream)
@@ -663,13 +751,19 @@ def run_feedback(args, rank, world):
         for c in (0, 3000, 9000):
             m.step(c - done)
             done = c
-            res[str(c)] = round(recall(m.knn(F.SPACE_HD, with_d2=False)[qb], ex), 4)
+            hd = m.knn(F.SPACE_HD, with_d2=False)[qb]
+            per = rnx_points(hd, ex, len(Xb))
+            res[str(c)] = {"rnx_auc": round(rnx_auc(hd, ex, len(Xb)), 4), "recall": round(recall(hd, ex), 4),
+                           "rnx_mean": {str(k): round(float(per[:, k - 1].mean()), 4) for k in ks},
+                           "rnx_std": {str(k): round(float(per[:, k - 1].std()), 4) for k in ks}}
         out["fig7"][name] = res
         m.close()
     if rank == 0:
-        print(json.dumps({"metric": "HD-KNN recall@k_hd along the iterations (feedback loop)", "data": "synthetic",
-                          "config": {"fig4": f"pixels-70k N={N}, k_hd={p['k_hd']}, {len(q)} sampled queries",
-                                     "fig7": "D=30, d=2, k_hd=32, k_ld=16, n_neg=16, perplexity 30"},
+        print(json.dumps({"metric": "AUC of R_NX(K <= k_hd) of the HD neighbour lists along the iterations "
+                                    "(feedback loop)", "data": "synthetic",
+                          "config": {"fig4": f"pixels-70k N={N}, k_hd={p['k_hd']}, {len(q)} sampled points",
+                                     "fig7": "D=30, d=2, k_hd=32, k_ld=16, n_neg=16, perplexity 30, 2000 sampled "
+                                             "points"},
                           "results": out}), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -784,6 +878,9 @@ def parse_args(argv=None):
     ap.add_argument("--every", type=int, default=50, help="--mode dynamic: iterations between insertions")
     ap.add_argument("--insert-rounds", type=int, default=64,
                     help="--mode dynamic: neighbour-of-neighbour rounds of each insertion")
+    ap.add_argument("--fresh-iters", type=int, default=50,
+                    help="--mode dynamic: iterations after an insertion in which the new points refine their HD "
+                         "lists whatever the coin (0: off)")
     ap.add_argument("--hd-mode", type=int, default=0, choices=[0, 1, 2],
                     help="--mode dynamic: 0 adaptive HD refinement, 1 every iteration, 2 never")
     ap.add_argument("--mlp-pretrain", type=int, default=0,

@@ -68,6 +68,9 @@ typedef struct {
     double Zhat;     /* running estimate of sum_{k != l} w_kl (Eq. 4)           */
     double E;        /* smoothed fraction of points with new HD neighbours       */
     uint32_t t;      /* iteration counter                                        */
+    int64_t fresh_lo;     /* insertion window (option "fresh_iters"): points     */
+    uint32_t fresh_until; /* fresh_lo .. N-1 refine while t < fresh_until;      */
+                          /* fresh_lo = N (and any fresh_until) means none      */
 } funcsne_state_t;
 
 typedef struct {
@@ -179,6 +182,13 @@ int funcsne_create(const float *X, int64_t N, int32_t D, int32_t d, int32_t k_hd
  *                    (default 0: off)
  *   "insert_rounds"  neighbour-of-neighbour rounds that build an inserted
  *                    point's HD list (0..256, default 64)
+ *   "fresh_iters"    iterations after an insertion during which the inserted
+ *                    points refine their HD lists in every iteration, also
+ *                    when the coin does not fire (an addition for points
+ *                    added on the fly; E is updated only by the coin's
+ *                    iterations). An insertion inside an open window extends
+ *                    it and keeps the earlier points in it; a removal closes
+ *                    it. 0 (default): off
  *   "hd_lanes"       lanes that read one gathered HD row in the refinement:
  *                    1, 2, 4 or 8, or 0 (default) to choose from the row
  *                    bytes. A tuning knob; it fixes the FP32 summation order,
@@ -349,6 +359,14 @@ int funcsne_profile_step(funcsne_t *h, int32_t n_iters, double *ms_per_kernel);
  * Errors: FUNCSNE_E_ARG. */
 int funcsne_debug_bounded_wait(funcsne_t *h, uint32_t polls);
 
+/* Allocation-failure injection, for testing failure detection on the host:
+ * after `after` more successful device allocations of the library (any
+ * handle), the next one fails as if the device were out of memory, once;
+ * the call that made it returns FUNCSNE_E_OOM and releases what it had
+ * allocated. after < 0 switches the injection off. Process-wide, not
+ * thread-safe against concurrent calls. Always returns FUNCSNE_OK. */
+int funcsne_debug_fail_alloc(int64_t after);
+
 /* Exact k nearest HD neighbours (FP32 distances, ties by index) of the n_q
  * query points `queries` (int32, host or device), by brute force over all
  * points: for measuring neighbour recall. idx: n_q x k, d2: n_q x k or NULL. */
@@ -368,7 +386,12 @@ int funcsne_exact_knn(const funcsne_t *h, const int32_t *queries, int64_t n_q, i
  *   X        device pointer, N rows of D FP32 features with row pitch ldx
  *            floats (ldx % 4 == 0, ldx >= D rounded up to 4, ldx <= 4096),
  *            16-byte aligned; columns D .. ceil(D/4)*4 - 1 must be zero.
- *   queries  HOST array of n_q point indices in [0, N) (read before return).
+ *   queries  HOST array of n_q point indices in [0, N). They are checked
+ *            on the host before return, then copied to the device with
+ *            cudaMemcpyAsync on `stream`: from pageable memory the copy has
+ *            finished when the call returns; from page-locked (pinned)
+ *            memory it runs when the stream reaches it, so such a buffer
+ *            must stay unchanged until then.
  *   k        neighbours per query, 1 <= k <= min(64, N - 1).
  *   idx, d2  DEVICE outputs, n_q x k int32 and FP32 (d2 may be NULL); ordered
  *            by (d2, index), the query point itself excluded.

@@ -17,6 +17,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/funcsne.h"
 #include "launch.h"
 #include "params.h"
@@ -63,6 +65,7 @@ struct funcsne {
     int32_t forces_pair = 1;  // the row-pair layout of the forces (rows of 8+ floats)
     int32_t ld_pair = 1;      // the row-pair layout of the LD refinement's distances
     int32_t hd_prefetch = 1;  // HD refinement pipelined over the points of a warp (option)
+    int32_t fresh_iters = 0;  // iterations an inserted point is refined for, whatever the coin
     int32_t hd_pf_used = 0;   // ... in use: rows read by two lanes, room for four blocks
     int32_t hd_lanes_opt = 0; // lanes per gathered HD row (0: chosen from the row bytes)
     int32_t insert_rounds = 64; // neighbour-of-neighbour rounds of an insertion
@@ -120,14 +123,32 @@ int fail(funcsne* h, int code, const char* fmt, ...) {
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);       \
     } while (0)
 
+// Allocation-failure injection (funcsne_debug_fail_alloc): allocations left
+// before one fails; -1: off.
+int64_t g_fail_alloc_after = -1;
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (g_fail_alloc_after == 0) {
+        g_fail_alloc_after = -1;
+        return cudaErrorMemoryAllocation;
+    }
+    if (g_fail_alloc_after > 0) --g_fail_alloc_after;
     return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// An NVTX range over the host side of an entry point (what a profiler's
+// timeline shows for each call; inert without one attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 void drop_graphs(funcsne* h) {
     if (h->graph1) cudaGraphExecDestroy(h->graph1);
@@ -244,9 +265,13 @@ cudaError_t launch_phase(const funcsne* h, int phase, const StepParams& p, cudaS
                 default: return hd_refine_launch_fp8(p, h->RH, p.ga, h->hd_blocks, h->hd_smem, s);
             }
         case 1: return ld_refine_launch(p, h->DP, h->RH, use_ld_pair(h), h->ld_blocks, h->ld_smem, s);
-        case 2:
+        case 2: {
+            // the insertion window's lists first (a no-op outside window-only iterations)
+            const cudaError_t e = fresh_lists_launch(p, h->update_blocks, s);
+            if (e != cudaSuccess) return e;
             if (use_forces_pair(h)) return forces_pair_launch(p, h->DP, h->RH, h->fo_blocks, h->fo_smem, s);
             return forces_launch(p, h->DP, h->RH, h->forces_cw, h->fo_blocks, h->fo_smem, s);
+        }
         default: return update_launch(update_params(h, nullptr, nullptr), h->update_blocks, s);
     }
 }
@@ -596,6 +621,10 @@ int mlp_train_now(funcsne* h, int n) {
 // Reallocate every per-point array for new_cap rows (N rows kept, the rest zero).
 int grow(funcsne* h, int64_t new_cap) {
     const int64_t N = h->N;
+    // the arrays move one by one: graphs captured with the old addresses go
+    // first, so a failure part-way (some arrays moved, h->cap unchanged,
+    // every array still holding at least cap rows) leaves a usable handle
+    drop_graphs(h);
     auto move = [&](auto** p, size_t row_elems) -> int {
         using T = std::remove_pointer_t<std::remove_reference_t<decltype(*p)>>;
         T* q = nullptr;
@@ -637,7 +666,6 @@ int grow(funcsne* h, int64_t new_cap) {
     if ((rc = move(&h->P, h->k_hd))) return rc;
     if ((rc = move(&h->beta, 1))) return rc;
     h->cap = new_cap;
-    drop_graphs(h);
     return FUNCSNE_OK;
 }
 
@@ -652,6 +680,7 @@ extern "C" {
 
 int funcsne_create(const float* X, int64_t N, int32_t D, int32_t d, int32_t k_hd, int32_t k_ld, int32_t n_neg,
                    float alpha, float perplexity, uint64_t seed, funcsne_t** out) {
+    NvtxRange nvtx_range("funcsne_create");
     if (!out) return fail(nullptr, FUNCSNE_E_ARG, "out is NULL");
     *out = nullptr;
     if (!X) return fail(nullptr, FUNCSNE_E_ARG, "X is NULL");
@@ -738,6 +767,8 @@ int funcsne_create(const float* X, int64_t N, int32_t D, int32_t d, int32_t k_hd
     DevScalars init{};
     init.E = 1.0;
     init.Zhat = 1.0;
+    init.fresh_lo = N;  // no insertion window
+    init.fresh_until = 0;
     CREATE_CUDA(cudaMemcpyAsync(h->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
     CREATE_CUDA(launch_check_finite(h->X32, static_cast<int64_t>(N) * h->xpitch, &h->sc->err, s));
     {
@@ -846,6 +877,9 @@ int funcsne_set_option(funcsne_t* h, const char* key, double v) {
         if (v < (k == "jump_parts" ? 1 : 0) || v > 1e7 || v != static_cast<int>(v))
             return fail(h, FUNCSNE_E_ARG, "%s must be an integer (jump_iters >= 0, jump_parts >= 1)", key);
         (k == "jump_iters" ? h->jump_iters : h->jump_parts) = static_cast<int32_t>(v);
+    } else if (k == "fresh_iters") {
+        if (v < 0 || v > 1e6 || v != std::floor(v)) return fail(h, FUNCSNE_E_ARG, "fresh_iters must be an integer in [0, 1e6]");
+        h->fresh_iters = static_cast<int32_t>(v);
     } else if (k == "insert_rounds") {
         if (v < 0 || v > 256 || v != static_cast<int>(v))
             return fail(h, FUNCSNE_E_ARG, "insert_rounds must be an integer in [0, 256]");
@@ -913,6 +947,7 @@ int funcsne_get_option(const funcsne_t* hc, const char* key, double* v) {
     else if (k == "hd_lanes") *v = h->hd_lanes_opt;
     else if (k == "hd_lanes_used") *v = hd_lanes(h);
     else if (k == "insert_rounds") *v = h->insert_rounds;
+    else if (k == "fresh_iters") *v = h->fresh_iters;
     else if (k == "jump_iters") *v = h->jump_iters;
     else if (k == "jump_parts") *v = h->jump_parts;
     else if (k == "perplexity") *v = h->perplexity;
@@ -976,6 +1011,7 @@ int jump_iteration(funcsne* h) {
 }
 
 int funcsne_step(funcsne_t* h, int32_t n_iters) {
+    NvtxRange nvtx_range("funcsne_step");
     if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
     if (n_iters < 0) return fail(h, FUNCSNE_E_ARG, "n_iters must be >= 0");
     while (n_iters > 0 && h->t_host < static_cast<uint32_t>(h->jump_iters)) {
@@ -1016,6 +1052,7 @@ int funcsne_step(funcsne_t* h, int32_t n_iters) {
 }
 
 int funcsne_mlp_train(funcsne_t* h, int32_t n_steps) {
+    NvtxRange nvtx_range("funcsne_mlp_train");
     if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
     if (n_steps < 0) return fail(h, FUNCSNE_E_ARG, "n_steps must be >= 0");
     return mlp_train_now(h, n_steps);
@@ -1041,6 +1078,11 @@ int funcsne_mlp_predict(const funcsne_t* hc, const float* X, int64_t n, float* Y
     cudaFree(xd);
     cudaFree(yd);
     FSNE_CUDA(h, e);
+    return FUNCSNE_OK;
+}
+
+int funcsne_debug_fail_alloc(int64_t after) {
+    g_fail_alloc_after = after < 0 ? -1 : after;
     return FUNCSNE_OK;
 }
 
@@ -1108,6 +1150,7 @@ int funcsne_sync(funcsne_t* h) {
 }
 
 int funcsne_insert(funcsne_t* h, const float* X_new, int64_t n_new, int32_t placement, int64_t* first_id) {
+    NvtxRange nvtx_range("funcsne_insert");
     if (!h || !X_new || !first_id) return fail(h, FUNCSNE_E_ARG, "NULL argument");
     if (n_new < 1) return fail(h, FUNCSNE_E_ARG, "n_new must be >= 1");
     if (placement != FUNCSNE_PLACE_MEAN && placement != FUNCSNE_PLACE_SURROGATE)
@@ -1168,6 +1211,15 @@ int funcsne_insert(funcsne_t* h, const float* X_new, int64_t n_new, int32_t plac
               (static_cast<double>(n_old) * static_cast<double>(n_old - 1));
     const double frac = static_cast<double>(n_new) / static_cast<double>(N2);
     if (frac > s.E) s.E = frac;
+    // the new points' refinement window: the next fresh_iters iterations; a
+    // window still open keeps its older points in it
+    if (h->fresh_iters > 0) {
+        if (!(s.t < s.fresh_until)) s.fresh_lo = n_old;
+        s.fresh_until = s.t + static_cast<uint32_t>(h->fresh_iters);
+        FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->fresh_lo, &s.fresh_lo, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+        FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->fresh_until, &s.fresh_until, sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                     h->stream));
+    }
     FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->Zhat, &s.Zhat, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->E, &s.E, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1217,6 +1269,7 @@ int host_ids(funcsne* h, const int64_t* ids, int64_t n, std::vector<int64_t>& ou
 }
 
 int funcsne_update_points(funcsne_t* h, const int64_t* ids, int64_t n, const float* X_rows) {
+    NvtxRange nvtx_range("funcsne_update_points");
     if (!h || !ids || !X_rows) return fail(h, FUNCSNE_E_ARG, "NULL argument");
     if (n < 1) return fail(h, FUNCSNE_E_ARG, "n must be >= 1");
     std::vector<int64_t> hid;
@@ -1250,6 +1303,7 @@ int funcsne_update_points(funcsne_t* h, const int64_t* ids, int64_t n, const flo
 }
 
 int funcsne_remove(funcsne_t* h, const int64_t* ids, int64_t n) {
+    NvtxRange nvtx_range("funcsne_remove");
     if (!h || !ids) return fail(h, FUNCSNE_E_ARG, "NULL argument");
     if (n < 1) return fail(h, FUNCSNE_E_ARG, "n must be >= 1");
     std::vector<int64_t> hid;
@@ -1315,11 +1369,18 @@ int funcsne_remove(funcsne_t* h, const int64_t* ids, int64_t n) {
     if (frac > s.E) s.E = frac;
     FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->Zhat, &s.Zhat, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->E, &s.E, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    // renumbering closes the refinement window of recent insertions
+    s.fresh_lo = Nk;
+    s.fresh_until = s.t;
+    FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->fresh_lo, &s.fresh_lo, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+    FSNE_CUDA(h, cudaMemcpyAsync(&h->sc->fresh_until, &s.fresh_until, sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                 h->stream));
     configure_step(h);
     return recalibrate(h);
 }
 
 int funcsne_get_embedding(const funcsne_t* hc, float* Y_out, int64_t cap_rows) {
+    NvtxRange nvtx_range("funcsne_get_embedding");
     funcsne* h = const_cast<funcsne*>(hc);
     if (!h || !Y_out) return fail(h, FUNCSNE_E_ARG, "NULL argument");
     const int64_t rows = cap_rows < h->N ? cap_rows : h->N;
@@ -1469,6 +1530,8 @@ int funcsne_export_state(const funcsne_t* hc, funcsne_state_t* st) {
     st->Zhat = s.Zhat;
     st->E = s.E;
     st->t = s.t;
+    st->fresh_lo = s.fresh_lo;
+    st->fresh_until = s.fresh_until;
     return FUNCSNE_OK;
 }
 
@@ -1476,6 +1539,7 @@ int funcsne_import_state(funcsne_t* h, const funcsne_state_t* st) {
     if (!h || !st) return fail(h, FUNCSNE_E_ARG, "NULL argument");
     if (!(st->Zhat > 0) || !std::isfinite(st->Zhat) || !(st->E >= 0 && st->E <= 1))
         return fail(h, FUNCSNE_E_ARG, "Zhat must be > 0 and E in [0, 1]");
+    if (st->fresh_lo < 0 || st->fresh_lo > h->N) return fail(h, FUNCSNE_E_ARG, "fresh_lo must be in [0, N]");
     DevScalars s;
     int rc = read_scalars(h, &s);
     if (rc) return rc;
@@ -1530,6 +1594,8 @@ int funcsne_import_state(funcsne_t* h, const funcsne_state_t* st) {
     s.Zhat = st->Zhat;
     s.E = st->E;
     s.t = st->t;
+    s.fresh_lo = st->fresh_lo;
+    s.fresh_until = st->fresh_until;
     h->t_host = st->t;
     s.err = 0;
     s.ticket = 0;
@@ -1561,6 +1627,7 @@ int funcsne_debug_step(funcsne_t* h, float* att, float* rep) {
 }
 
 int funcsne_profile_step(funcsne_t* h, int32_t n_iters, double* ms_per_kernel) {
+    NvtxRange nvtx_range("funcsne_profile_step");
     if (!h || !ms_per_kernel) return fail(h, FUNCSNE_E_ARG, "NULL argument");
     if (n_iters < 1) return fail(h, FUNCSNE_E_ARG, "n_iters must be >= 1");
     const int ne = kPhases + 1;
@@ -1570,7 +1637,9 @@ int funcsne_profile_step(funcsne_t* h, int32_t n_iters, double* ms_per_kernel) {
     for (int k = 0; k < n_iters && rc == FUNCSNE_OK; ++k) {
         const StepParams p = step_params(h);
         cudaError_t e = cudaEventRecord(ev[ne * k], h->stream);
+        static const char* const kPhaseNames[kPhases] = {"hd_refine", "ld_refine", "forces", "update"};
         for (int ph = 0; ph < kPhases && e == cudaSuccess; ++ph) {
+            NvtxRange phase_range(kPhaseNames[ph]);
             e = launch_phase(h, ph, p, h->stream);
             if (e == cudaSuccess) e = cudaEventRecord(ev[ne * k + ph + 1], h->stream);
         }
@@ -1594,6 +1663,7 @@ int funcsne_profile_step(funcsne_t* h, int32_t n_iters, double* ms_per_kernel) {
 }
 
 int funcsne_exact_knn(const funcsne_t* hc, const int32_t* queries, int64_t n_q, int32_t k, int32_t* idx, float* d2) {
+    NvtxRange nvtx_range("funcsne_exact_knn");
     funcsne* h = const_cast<funcsne*>(hc);
     if (!h || !queries || !idx) return fail(h, FUNCSNE_E_ARG, "NULL argument");
     if (k < 1 || k > 64 || k >= h->N) return fail(h, FUNCSNE_E_ARG, "k must be in [1, min(64, N-1)]");

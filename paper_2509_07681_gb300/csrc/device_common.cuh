@@ -637,6 +637,32 @@ __device__ __forceinline__ ApproxDist group_dist_fp8(const float* __restrict__ x
     return band_from_row_error(my_acc, my_err, gamma);
 }
 
+// ---------------------------------------------------------------- range checks
+// With FUNCSNE_CHECKED defined (the library's range-checked build), every
+// point index read from memory and then used to address a row or a list is
+// checked against [0, n): an index outside it sets kErrIndex in the device
+// error word (reported by funcsne_sync as FUNCSNE_E_RANGE) and is replaced by
+// `fallback`, a valid index, so the access stays in bounds. Never traps.
+// Without it the macros cost nothing.
+#ifdef FUNCSNE_CHECKED
+__device__ __forceinline__ uint32_t checked_index(uint32_t j, uint32_t n, uint32_t fallback, uint32_t* err) {
+    if (j < n) return j;
+    atomicOr(err, kErrIndex);
+    return fallback;
+}
+#define FSNE_IDX(j, n, fallback, err) ::fsne::checked_index((j), (n), (fallback), (err))
+// a candidate that the kernel drops when it is out of range: only reported
+#define FSNE_FLAG_RANGE(j, n, err) \
+    do {                                \
+        if (!((j) < (n))) atomicOr((err), kErrIndex); \
+    } while (0)
+#else
+#define FSNE_IDX(j, n, fallback, err) (j)
+#define FSNE_FLAG_RANGE(j, n, err) \
+    do {                                \
+    } while (0)
+#endif
+
 // ---------------------------------------------------------------- asynchronous copies
 // 16-byte global-to-shared copies that complete in the background
 // (cp.async, L2 only): issued for the next point while the current one is

@@ -50,6 +50,9 @@ extern "C" int funcsne_exact_knn_noalloc(const float* X, int64_t N, int32_t D, i
     if (k < 1 || k > 64 || k >= N) return reject(FUNCSNE_E_ARG, "exact_knn_noalloc: k must be in [1, min(64, N-1)] (k=%lld)", k);
     if (n_q < 0) return reject(FUNCSNE_E_ARG, "exact_knn_noalloc: n_q must be >= 0");
     if (n_q == 0) return FUNCSNE_OK;
+    // bounded first, so that the byte counts below cannot wrap around
+    if (n_q > static_cast<int64_t>(kScratchBytes / 4))
+        return reject(FUNCSNE_E_ARG, "exact_knn_noalloc: n_q=%lld exceeds the 4 MiB static scratch", n_q);
     const int RK = k <= 32 ? 1 : 2;
     const size_t q_bytes = (static_cast<size_t>(n_q) * 4 + 255) / 256 * 256;
     const size_t per_slice = static_cast<size_t>(n_q) * 32 * RK * sizeof(unsigned long long);

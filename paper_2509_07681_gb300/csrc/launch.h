@@ -78,6 +78,9 @@ cudaError_t ld_refine_launch(const StepParams& p, int DP, int RH, bool pair, int
 cudaError_t forces_launch(const StepParams& p, int DP, int RH, int CW, int blocks, size_t smem, cudaStream_t s);
 int ld_refine_occupancy(int DP, int RH, bool pair, size_t smem);
 int forces_occupancy(int DP, int RH, int CW, size_t smem);
+// copy of the insertion window's new HD lists into the current buffer
+// (iterations that refined only the window)
+cudaError_t fresh_lists_launch(const StepParams& p, int blocks, cudaStream_t s);
 // forces with the row-pair layout (DP = 8, 16 or 32)
 cudaError_t forces_pair_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s);
 int forces_pair_occupancy(int DP, int RH, size_t smem);

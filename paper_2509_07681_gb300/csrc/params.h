@@ -64,7 +64,17 @@ struct DevScalars {
     uint32_t err;        // error bits
     uint32_t ticket;     // last-block detection of the update kernel
     unsigned long long n_refined;  // iterations whose coin fired (cumulative)
+    // refinement window of recently inserted points: points fresh_lo .. N-1
+    // refine their HD lists in every iteration with t < fresh_until, also
+    // when the coin does not fire (fresh_lo = N: none)
+    int64_t fresh_lo;
+    uint32_t fresh_until;
 };
+
+// True when iteration t refines only the points of the insertion window.
+__host__ __device__ inline bool fresh_only(const DevScalars* s, uint32_t t, bool fire, int64_t N) {
+    return !fire && t < s->fresh_until && s->fresh_lo < N;
+}
 
 constexpr uint32_t kErrNonFinite = 1u;
 constexpr uint32_t kErrIndex = 2u;

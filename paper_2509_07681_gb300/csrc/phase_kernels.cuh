@@ -79,7 +79,11 @@ hd_refine_kernel(const StepParams p) {
 
     const DevScalars* sc = p.sc;
     const uint32_t t = sc->t;
-    if (!hd_coin(t, sc->E, p.seed, p.hd_mode, p.coin_p0, p.coin_p1)) return;  // uniform over the grid
+    // the coin refines every point; without it, only the points of the
+    // insertion window (if one is open) are refined (uniform over the grid)
+    const bool fire = hd_coin(t, sc->E, p.seed, p.hd_mode, p.coin_p0, p.coin_p1);
+    if (!fire && !fresh_only(sc, t, fire, p.N)) return;
+    const int64_t lo = fire ? 0 : sc->fresh_lo;
     const ListView L = list_view(p, sc->hd_cur, sc->ld_cur);
     const uint32_t N = static_cast<uint32_t>(p.N);
     const int k_hd = p.k_hd, k_ld = p.k_ld;
@@ -110,7 +114,7 @@ hd_refine_kernel(const StepParams p) {
         cp_async_commit();
     };
     const int64_t tw = static_cast<int64_t>(gridDim.x) * kWarpsPerBlock;
-    const int64_t g0 = static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + wib;
+    const int64_t g0 = lo + static_cast<int64_t>(blockIdx.x) * kWarpsPerBlock + wib;
     uint32_t n_hidx[RH];
     float n_hd2[RH];
     uint32_t n_lidx = 0;
@@ -154,18 +158,23 @@ hd_refine_kernel(const StepParams p) {
         for (int r = 0; r < RH; ++r)
             if (r * 32 + lane < k_hd) hset_insert(tab, hidx[r]);
         const uint32_t e0 = lane < kHdNnEnd ? map_index(w.x, k_hd) : map_index(w.x, k_ld);
+        // hv and lv are shuffled warp-wide; each lane uses (and, in the
+        // checked build, range-checks) only the one its slot reads
         const uint32_t hv = warp_get<RH>(hidx, e0);
         const uint32_t lv = __shfl_sync(kFull, lidx, static_cast<int>(e0 & 31u));
         uint32_t c;
         if (lane < kHdNnEnd)
-            c = static_cast<uint32_t>(__ldg(L.hd_idx_c + static_cast<int64_t>(hv) * k_hd + map_index(w.y, k_hd)));
+            c = static_cast<uint32_t>(__ldg(L.hd_idx_c + static_cast<int64_t>(FSNE_IDX(hv, N, i, &p.sc->err)) * k_hd +
+                                            map_index(w.y, k_hd)));
         else if (lane < kHdLdNbEnd)
             c = lv;
         else if (lane < kHdLdNnEnd)
-            c = static_cast<uint32_t>(__ldg(L.ld_idx_c + static_cast<int64_t>(lv) * k_ld + map_index(w.y, k_ld)));
+            c = static_cast<uint32_t>(__ldg(L.ld_idx_c + static_cast<int64_t>(FSNE_IDX(lv, N, i, &p.sc->err)) * k_ld +
+                                            map_index(w.y, k_ld)));
         else
             c = map_other(w.x, N, i);
         __syncwarp();
+        FSNE_FLAG_RANGE(c, N, &p.sc->err);
         bool valid = (c != i) && (c < N) && !hset_has(tab, c);
         valid &= (__match_any_sync(kFull, c) & ((1u << lane) - 1u)) == 0u;
 
@@ -446,14 +455,16 @@ ld_refine_kernel(const StepParams p) {
             const uint32_t hv = warp_get<RH>(hidx, e0);
             // in flight while the old list's rows are gathered
             const uint32_t cnn =
-                lane < kLdNnEnd
-                    ? static_cast<uint32_t>(__ldg(L.ld_idx_c + static_cast<int64_t>(lv) * k_ld + map_index(w.w, k_ld)))
-                    : 0u;
-            d_old = ld_dist_rows<DP>(yi, Y, lane < k_ld ? lidx : kNoRow, lane);
+                lane < kLdNnEnd ? static_cast<uint32_t>(__ldg(L.ld_idx_c +
+                                                              static_cast<int64_t>(FSNE_IDX(lv, N, i, &p.sc->err)) * k_ld +
+                                                              map_index(w.w, k_ld)))
+                                : 0u;
+            d_old = ld_dist_rows<DP>(yi, Y, lane < k_ld ? FSNE_IDX(lidx, N, i, &p.sc->err) : kNoRow, lane);
             hset_clear(tab, lane);
             __syncwarp();
             if (lane < k_ld) hset_insert(tab, lidx);
             const uint32_t c = lane < kLdNnEnd ? cnn : (lane < kLdHdNbEnd ? hv : map_other(w.z, N, i));
+            FSNE_FLAG_RANGE(c, N, &p.sc->err);
             __syncwarp();
             bool valid = (c != i) && (c < N) && !hset_has(tab, c);
             valid &= (__match_any_sync(kFull, c) & ((1u << lane) - 1u)) == 0u;
@@ -473,7 +484,8 @@ ld_refine_kernel(const StepParams p) {
             const uint32_t hv = warp_get<RH>(hidx, e0);
             uint32_t c;
             if (lane < kLdNnEnd)
-                c = static_cast<uint32_t>(__ldg(L.ld_idx_c + static_cast<int64_t>(lv) * k_ld + map_index(w.w, k_ld)));
+                c = static_cast<uint32_t>(__ldg(L.ld_idx_c + static_cast<int64_t>(FSNE_IDX(lv, N, i, &p.sc->err)) * k_ld +
+                                                map_index(w.w, k_ld)));
             else if (lane < kLdHdNbEnd)
                 c = hv;
             else
@@ -481,7 +493,8 @@ ld_refine_kernel(const StepParams p) {
             __syncwarp();
             bool valid = (c != i) && (c < N) && !hset_has(tab, c);
             valid &= (__match_any_sync(kFull, c) & ((1u << lane) - 1u)) == 0u;
-            d_old = group_ld_dist<DP, GL>(yi, Y, lane < k_ld ? lidx : kNoRow, lane);
+            FSNE_FLAG_RANGE(c, N, &p.sc->err);
+            d_old = group_ld_dist<DP, GL>(yi, Y, lane < k_ld ? FSNE_IDX(lidx, N, i, &p.sc->err) : kNoRow, lane);
             d_c = group_ld_dist<DP, GL>(yi, Y, valid ? c : kNoRow, lane);
             cand_c = c;
             cand_valid = valid;
@@ -557,6 +570,8 @@ forces_kernel(const StepParams p) {
     const uint32_t t = sc->t;
     const bool fire = hd_coin(t, sc->E, p.seed, p.hd_mode, p.coin_p0, p.coin_p1);
     // lists of iteration t+1: the HD buffer flips only when the coin fired
+    // (the rows of an insertion window refined alone were copied back into
+    // the current buffer by fresh_lists_kernel)
     const int32_t* __restrict__ hd_new = (sc->hd_cur ^ (fire ? 1 : 0)) ? p.hd_idx1 : p.hd_idx0;
     const int32_t* __restrict__ ld_new = sc->ld_cur ? p.ld_idx0 : p.ld_idx1;
     const float invZ = static_cast<float>(1.0 / sc->Zhat);
@@ -576,10 +591,13 @@ forces_kernel(const StepParams p) {
 #pragma unroll
         for (int r = 0; r < RH; ++r) {
             const int e = r * 32 + lane;
-            nh[r] = e < k_hd ? static_cast<uint32_t>(__ldg(hd_new + gi * k_hd + e)) : 0xffffffffu;
+            nh[r] = e < k_hd ? FSNE_IDX(static_cast<uint32_t>(__ldg(hd_new + gi * k_hd + e)), N, i, &p.sc->err)
+                             : 0xffffffffu;
             pv[r] = e < k_hd ? p.P[gi * k_hd + e] : 0.f;
         }
-        const uint32_t nl = lane < k_ld ? static_cast<uint32_t>(__ldg(ld_new + gi * k_ld + lane)) : 0xffffffffu;
+        const uint32_t nl =
+            lane < k_ld ? FSNE_IDX(static_cast<uint32_t>(__ldg(ld_new + gi * k_ld + lane)), N, i, &p.sc->err)
+                        : 0xffffffffu;
         float yi[CW];
         load_chunk<CW>(Y + gi * DP + co, yi);
         const uint4 wq = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
@@ -739,6 +757,8 @@ forces_pair_kernel(const StepParams p) {
     const uint32_t t = sc->t;
     const bool fire = hd_coin(t, sc->E, p.seed, p.hd_mode, p.coin_p0, p.coin_p1);
     // lists of iteration t+1: the HD buffer flips only when the coin fired
+    // (the rows of an insertion window refined alone were copied back into
+    // the current buffer by fresh_lists_kernel)
     const int32_t* __restrict__ hd_new = (sc->hd_cur ^ (fire ? 1 : 0)) ? p.hd_idx1 : p.hd_idx0;
     const int32_t* __restrict__ ld_new = sc->ld_cur ? p.ld_idx0 : p.ld_idx1;
     const float invZ = static_cast<float>(1.0 / sc->Zhat);
@@ -760,10 +780,13 @@ forces_pair_kernel(const StepParams p) {
 #pragma unroll
         for (int r = 0; r < RH; ++r) {
             const int e = r * 32 + lane;
-            nh[r] = e < k_hd ? static_cast<uint32_t>(__ldg(hd_new + gi * k_hd + e)) : 0xffffffffu;
+            nh[r] = e < k_hd ? FSNE_IDX(static_cast<uint32_t>(__ldg(hd_new + gi * k_hd + e)), N, i, &p.sc->err)
+                             : 0xffffffffu;
             pv[r] = e < k_hd ? p.P[gi * k_hd + e] : 0.f;
         }
-        const uint32_t nl = lane < k_ld ? static_cast<uint32_t>(__ldg(ld_new + gi * k_ld + lane)) : 0xffffffffu;
+        const uint32_t nl =
+            lane < k_ld ? FSNE_IDX(static_cast<uint32_t>(__ldg(ld_new + gi * k_ld + lane)), N, i, &p.sc->err)
+                        : 0xffffffffu;
         const float4 yi = __ldg(reinterpret_cast<const float4*>(Y + gi * DP + co));
         const uint4 wq = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
         // S_i = HD u LD lists of t+1 as a warp hash set

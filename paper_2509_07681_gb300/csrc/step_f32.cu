@@ -49,6 +49,35 @@ cudaError_t forces_launch(const StepParams& p, int DP, int RH, int CW, int block
     return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------------ insertion window
+// In an iteration whose coin did not fire but an insertion window is open,
+// hd_refine_kernel wrote the window's new HD lists (rows fresh_lo .. N-1) to
+// the other buffer. Once the LD refinement (which reads the lists of t) is
+// done, this copies them into the current buffer, where the forces and the
+// next iteration read them. Any other iteration: returns at once.
+__global__ void __launch_bounds__(256) fresh_lists_kernel(const StepParams p) {
+    const DevScalars* sc = p.sc;
+    const uint32_t t = sc->t;
+    const bool fire = hd_coin(t, sc->E, p.seed, p.hd_mode, p.coin_p0, p.coin_p1);
+    if (!fresh_only(sc, t, fire, p.N)) return;
+    const int cur = sc->hd_cur;
+    int32_t* __restrict__ idx_c = cur ? p.hd_idx1 : p.hd_idx0;
+    const int32_t* __restrict__ idx_o = cur ? p.hd_idx0 : p.hd_idx1;
+    float* __restrict__ d2_c = cur ? p.hd_d21 : p.hd_d20;
+    const float* __restrict__ d2_o = cur ? p.hd_d20 : p.hd_d21;
+    const int64_t hi = p.N * p.k_hd;
+    for (int64_t e = sc->fresh_lo * p.k_hd + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < hi;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        idx_c[e] = idx_o[e];
+        d2_c[e] = d2_o[e];
+    }
+}
+
+cudaError_t fresh_lists_launch(const StepParams& p, int blocks, cudaStream_t s) {
+    fresh_lists_kernel<<<blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t forces_pair_launch(const StepParams& p, int DP, int RH, int blocks, size_t smem, cudaStream_t s) {
 #define FSNE_CASE(dp, rh)                                                                       \
     if (DP == dp && RH == rh) {                                                                 \

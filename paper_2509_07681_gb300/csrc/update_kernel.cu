@@ -53,7 +53,9 @@ __global__ void __launch_bounds__(256) update_kernel(const UpdateParams u) {
         const DevScalars* s0 = u.sc;
         const bool fired = hd_coin(t, s0->E, u.seed, u.hd_mode, u.coin_p0, u.coin_p1);
         for (int b = threadIdx.x; b < u.n_zpart; b += 32) z += u.zpart[b];
-        if (fired)
+        // the refinement kernel ran (and wrote its counters) when the coin
+        // fired or the insertion window was refined alone
+        if (fired || fresh_only(s0, t, fired, u.N))
             for (int b = threadIdx.x; b < u.n_cnt; b += 32) {
                 nn += u.cnt[3 * b];
                 ns += u.cnt[3 * b + 1];

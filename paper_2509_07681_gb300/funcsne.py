@@ -36,7 +36,7 @@ class FuncSNEError(RuntimeError):
 class State(C.Structure):
     _fields_ = [("Y", C.c_void_p), ("V", C.c_void_p), ("hd_idx", C.c_void_p), ("hd_d2", C.c_void_p),
                 ("ld_idx", C.c_void_p), ("beta", C.c_void_p), ("P", C.c_void_p), ("Zhat", C.c_double),
-                ("E", C.c_double), ("t", C.c_uint32)]
+                ("E", C.c_double), ("t", C.c_uint32), ("fresh_lo", C.c_int64), ("fresh_until", C.c_uint32)]
 
 
 class Stats(C.Structure):
@@ -70,6 +70,7 @@ ABI_FUNCTIONS = {
     "funcsne_get_embedding": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_get_embedding_async": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_debug_bounded_wait": (C.c_int, [_h, C.c_uint32]),
+    "funcsne_debug_fail_alloc": (C.c_int, [C.c_int64]),
     "funcsne_wait_embedding": (C.c_int, [_h]),
     "funcsne_get_data": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_scale_embedding": (C.c_int, [_h, C.c_float]),
@@ -92,11 +93,15 @@ ABI_FUNCTIONS = {
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libfuncsne.so (built by ``__graft_entry__.build()``)."""
+def load(path: str | None = None):
+    """Load libfuncsne.so (built by ``__graft_entry__.build()``), or the
+    library that the environment variable FUNCSNE_LIBRARY names (for
+    example the range-checked build, libfuncsne_checked.so)."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("FUNCSNE_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise FuncSNEError(-6, f"{path} is missing: build it with paper_2509_07681_gb300.build.build()")
     lib = C.CDLL(path)
@@ -231,10 +236,11 @@ def funcsne_export_state(h, arrays):
         setattr(st, f, p)
         keep.append(k)
     _check(load().funcsne_export_state(h, C.byref(st)), h)
-    return dict(Zhat=st.Zhat, E=st.E, t=st.t)
+    return dict(Zhat=st.Zhat, E=st.E, t=st.t, fresh_lo=st.fresh_lo, fresh_until=st.fresh_until)
 
 
-def funcsne_import_state(h, arrays, Zhat, E, t):
+def funcsne_import_state(h, arrays, Zhat, E, t, fresh_lo, fresh_until=0):
+    """fresh_lo / fresh_until: the insertion window (fresh_lo = N: none)."""
     st = State()
     keep = []
     for f in ("Y", "V", "hd_idx", "hd_d2", "ld_idx", "beta", "P"):
@@ -242,6 +248,7 @@ def funcsne_import_state(h, arrays, Zhat, E, t):
         setattr(st, f, p)
         keep.append(k)
     st.Zhat, st.E, st.t = float(Zhat), float(E), int(t)
+    st.fresh_lo, st.fresh_until = int(fresh_lo), int(fresh_until)
     _check(load().funcsne_import_state(h, C.byref(st)), h)
 
 
@@ -300,6 +307,12 @@ def funcsne_mlp_debug_step(h, arrays):
         keep.append(k)
     _check(load().funcsne_mlp_debug_step(h, C.byref(st)), h)
     return dict(loss=st.loss, scale=st.scale, step=st.step, n_params=st.n_params)
+
+
+def funcsne_debug_fail_alloc(after):
+    """After `after` more successful device allocations, fail the next one
+    once (FUNCSNE_E_OOM); after < 0 switches this off. For tests."""
+    _check(load().funcsne_debug_fail_alloc(int(after)))
 
 
 def funcsne_last_error(h=None):
@@ -391,7 +404,8 @@ class FuncSNE:
     def import_state(self, st):
         arrays = {k: (_as_f32(v) if k in ("Y", "V", "beta", "P") else np.ascontiguousarray(v, np.int32))
                   for k, v in st.items() if k in ("Y", "V", "hd_idx", "ld_idx", "beta", "P") and v is not None}
-        funcsne_import_state(self.h, arrays, st["Zhat"], st["E"], st["t"])
+        funcsne_import_state(self.h, arrays, st["Zhat"], st["E"], st["t"], st.get("fresh_lo", self.N),
+                             st.get("fresh_until", 0))
 
     def debug_step(self):
         att = np.empty((self.N, self.d), np.float32)
@@ -459,7 +473,7 @@ class FuncSNE:
     CHECKPOINT_OPTIONS = ("lr", "momentum", "att_ratio", "rep_ratio", "exaggeration", "exag_iters", "hd_mode",
                           "precision", "alpha", "perplexity", "concurrent", "surrogate", "mlp_every", "mlp_lr",
                           "mlp_batch", "mlp_hidden", "forces_cw", "forces_pair", "ld_pair", "hd_lanes", "insert_rounds",
-                          "jump_iters", "jump_parts", "coin_floor", "gamma_e", "gamma_z")
+                          "jump_iters", "jump_parts", "coin_floor", "gamma_e", "gamma_z", "fresh_iters")
 
     def save(self, path):
         """Checkpoint: HD rows, the exported iteration state, the creation
@@ -468,7 +482,7 @@ class FuncSNE:
         st = self.export_state()
         opts = {k: self.get_option(k) for k in self.CHECKPOINT_OPTIONS}
         np.savez(path, X=self.data(), **{k: v for k, v in st.items() if isinstance(v, np.ndarray)},
-                 Zhat=st["Zhat"], E=st["E"], t=st["t"],
+                 Zhat=st["Zhat"], E=st["E"], t=st["t"], fresh_lo=st["fresh_lo"], fresh_until=st["fresh_until"],
                  params=np.array([self.d, self.k_hd, self.k_ld, self.n_neg], dtype=np.int64),
                  alpha0=self._alpha0, perplexity0=self._perplexity0, seed=np.uint64(self._seed),
                  opt_keys=np.array(list(opts)), opt_vals=np.array(list(opts.values()), dtype=np.float64))
@@ -489,7 +503,9 @@ class FuncSNE:
         if perp != m.get_option("perplexity"):
             m.set_option("perplexity", perp)
         m.import_state({k: z[k] for k in ("Y", "V", "hd_idx", "ld_idx", "beta", "P")} |
-                       {"Zhat": float(z["Zhat"]), "E": float(z["E"]), "t": int(z["t"])})
+                       {"Zhat": float(z["Zhat"]), "E": float(z["E"]), "t": int(z["t"]),
+                        "fresh_lo": int(z["fresh_lo"]) if "fresh_lo" in z else m.N,
+                        "fresh_until": int(z["fresh_until"]) if "fresh_until" in z else 0})
         return m
 
     def update_points(self, ids, X_rows):

@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["recall", "rnx_curve", "rnx_auc", "overlap_counts"]
+__all__ = ["recall", "rnx_curve", "rnx_auc", "rnx_points", "overlap_counts"]
 
 
 def overlap_counts(est: np.ndarray, exact: np.ndarray, K: int) -> np.ndarray:
@@ -62,3 +62,19 @@ def rnx_auc(est: np.ndarray, exact: np.ndarray, n_points: int, kmax: int | None 
     r = rnx_curve(est, exact, n_points, kmax)
     K = np.arange(1, len(r) + 1)
     return float((r / K).sum() / (1.0 / K).sum())
+
+
+def rnx_points(est: np.ndarray, exact: np.ndarray, n_points: int, kmax: int | None = None) -> np.ndarray:
+    """Per-point R_NX: row i, column K-1 holds ((N - 1) |nu_i^K n n_i^K| / K - K) / (N - 1 - K),
+    whose mean over the rows is rnx_curve. Its spread across points is the
+    band of the paper's Fig. 7."""
+    est = np.asarray(est)
+    exact = np.asarray(exact)
+    if kmax is None:
+        kmax = min(est.shape[1], exact.shape[1])
+    N = int(n_points)
+    out = np.zeros((est.shape[0], kmax))
+    for K in range(1, kmax + 1):
+        q = overlap_counts(est, exact, K) / K
+        out[:, K - 1] = ((N - 1) * q - K) / (N - 1 - K)
+    return out

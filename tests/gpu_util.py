@@ -33,7 +33,8 @@ def oracle_from_state(X, st, params, d2=True, **opts):
     o = O.OracleState(X, params["d"], params["k_hd"], params["k_ld"], params["n_neg"], params["alpha"],
                       params["perplexity"], seed=params.get("seed", 0), init=False, **opts)
     o.load(Y=st["Y"], V=st["V"], hd_idx=st["hd_idx"], ld_idx=st["ld_idx"], beta=st["beta"], P=st["P"],
-           Zhat=st["Zhat"], E=st["E"], t=st["t"], d2=d2)
+           Zhat=st["Zhat"], E=st["E"], t=st["t"], d2=d2, fresh_lo=st.get("fresh_lo"),
+           fresh_until=st.get("fresh_until"))
     return o
 
 
@@ -196,13 +197,14 @@ FORCE_RTOL = 1e-4
 
 
 def check_after_refinement(X, st, st1, att, rep, s1, params, lr, momentum=0.8, gamma_e=0.1, gamma_z=0.1,
-                           label="", **opts):
+                           label="", coin=True, **opts):
     """Everything one GPU iteration computes after its neighbour refinement,
     checked on every row against the oracle run from the GPU's lists of t+1
     (st: exported state t; st1: state t+1; att, rep: the GPU's forces of the
     iteration; s1: its stats; the HD refinement ran):
       * the flag count equals the number of changed HD lists, and E follows
-        from it;
+        from it (coin=False: an iteration that refined only the insertion
+        window, which leaves E as it was);
       * beta and P of every changed row against the oracle's warm-started
         calibration (check_calibration); unchanged rows keep theirs;
       * attraction and repulsion of every row within 1e-4 relative;
@@ -216,7 +218,10 @@ def check_after_refinement(X, st, st1, att, rep, s1, params, lr, momentum=0.8, g
     changed = np.zeros(N, bool)
     changed[cal] = True
     assert s1["last_n_new"] == len(cal)
-    assert st1["E"] == (1.0 - gamma_e) * st["E"] + gamma_e * (len(cal) / N)  # same FP64 expression
+    if coin:
+        assert st1["E"] == (1.0 - gamma_e) * st["E"] + gamma_e * (len(cal) / N)  # same FP64 expression
+    else:
+        assert st1["E"] == st["E"]
     worst = check_calibration(X64, cal, st1["hd_idx"], st1["beta"], st1["P"], beta_or, P_or,
                               params["perplexity"], D)
     np.testing.assert_array_equal(st1["P"][~changed], st["P"][~changed])

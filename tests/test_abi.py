@@ -82,6 +82,20 @@ def test_null_handle_calls_fail_cleanly(lib):
     lib.funcsne_destroy(None)
 
 
+def test_noalloc_knn_rejects_huge_query_counts_before_touching_memory(lib):
+    """n_q is bounded before any byte count is formed from it, so a count
+    whose products would wrap around 64 bits is rejected (no device call,
+    the 4-entry query buffer is never read past)."""
+    X = np.zeros((64, 4), dtype=np.float32)
+    q = np.zeros(4, dtype=np.int32)
+    idx = np.zeros((4, 8), dtype=np.int32)
+    for n_q in (2 ** 61, 2 ** 40, (4 << 20) // 4 + 1):
+        rc = lib.funcsne_exact_knn_noalloc(X.ctypes.data, 64, 4, 4, q.ctypes.data, n_q, 8, idx.ctypes.data, None,
+                                           None)
+        assert rc == -1
+        assert "static scratch" in F.funcsne_last_error(None)
+
+
 def test_header_compiles_as_c_and_cxx():
     """The boundary is a plain C header: it compiles as C99 and as C++."""
     import shutil

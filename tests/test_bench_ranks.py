@@ -78,6 +78,11 @@ def test_reference_arm_rank0_only_under_torchrun():
     assert ln["value"] > 0 and ln["unit"] == "iter/s"
     assert ln["cpu_baseline"]["kind"] == "oracle" and ln["cpu_baseline"]["value"] == ln["value"]
     assert ln["e2e"]["h2d_bytes_per_step"] == 0 and ln["e2e"]["value"] == ln["value"]
+    # the config names the sample that was timed; the full-N rate is a labelled extra
+    assert ln["config"]["N"] <= ln["config"]["sample_of_N"] == 2000
+    assert ln["cpu_baseline"]["cores"] >= 1
+    ex = ln["extrapolated_to_full_N"]
+    assert ex["N"] == 2000 and ex["value"] == pytest.approx(ln["value"] * ln["config"]["N"] / 2000, rel=1e-3)
 
 
 def test_bench_args_and_bytes():

@@ -323,3 +323,44 @@ def test_bounded_device_wait_is_reported_and_context_survives():
     m2.sync()
     assert np.isfinite(m2.embedding()).all()
     m2.close()
+
+
+def test_allocation_failure_is_reported_and_the_library_stays_usable():
+    """Failure detection without a fault: allocation failures injected on the
+    host (funcsne_debug_fail_alloc) at several points of funcsne_create and
+    of an insertion's capacity growth return FUNCSNE_E_OOM; a failed create
+    leaves nothing behind, a failed insertion leaves the handle's points and
+    state as they were, and both the handle and new handles keep working."""
+    X = synth.blobs(n=1400, dim=20, n_clusters=4, seed=61)
+    failed = 0
+    for after in (0, 1, 3, 6, 10):
+        F.funcsne_debug_fail_alloc(after)
+        try:
+            m = F.FuncSNE(X[:1000], 2, 16, 8, 8, 1.0, 8.0, seed=0)
+        except F.FuncSNEError as e:
+            assert e.code == -2, e  # FUNCSNE_E_OOM
+            failed += 1
+        else:
+            m.close()
+    F.funcsne_debug_fail_alloc(-1)
+    assert failed >= 4
+    m = F.FuncSNE(X[:1000], 2, 16, 8, 8, 1.0, 8.0, seed=0)
+    m.step(3)
+    st = m.export_state()
+    for after in (0, 4, 9):
+        F.funcsne_debug_fail_alloc(after)
+        with pytest.raises(F.FuncSNEError) as ei:
+            m.insert(X[1000:1200])
+        assert ei.value.code == -2
+        F.funcsne_debug_fail_alloc(-1)
+        assert m.N == 1000 and m.stats()["N"] == 1000
+        st1 = m.export_state()
+        for k in ("Y", "hd_idx", "ld_idx", "beta", "P"):
+            np.testing.assert_array_equal(st1[k], st[k])
+    m.step(3)
+    m.sync()
+    assert m.insert(X[1000:1200]) == 1000 and m.N == 1200
+    m.step(3)
+    m.sync()
+    assert np.isfinite(m.embedding()).all() and m.stats()["error_word"] == 0
+    m.close()

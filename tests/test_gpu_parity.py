@@ -359,3 +359,47 @@ def test_insertion_grows_repeatedly_and_keeps_stepping():
     assert hd.min() >= 0 and hd.max() < 3000
     assert np.isfinite(m.embedding()).all()
     m.close()
+
+
+@pytest.mark.parametrize("hd_mode", [2, 0])
+def test_insertion_window_matches_oracle(hd_mode):
+    """Option fresh_iters: after an insertion, the new points refine their HD
+    lists in every iteration of the window, also when the coin does not
+    fire (hd_mode 2: never; 0: the adaptive coin). Each iteration from the
+    same state as the oracle: HD and LD sets, the window's bounds, and
+    everything after the refinement on every row; the old points' HD lists
+    change only in iterations whose coin fired."""
+    X = synth.blobs(n=2600, dim=24, n_clusters=6, seed=17)
+    p = dict(d=2, k_hd=16, k_ld=8, n_neg=8, alpha=1.0, perplexity=8.0)
+    m = _make(X[:2000], p, hd_mode=1)
+    m.step(20)
+    m.set_option("hd_mode", hd_mode)
+    m.set_option("fresh_iters", 5)
+    m.set_option("insert_rounds", 2)
+    m.step(10)
+    m.insert(X[2000:])
+    st = m.export_state()
+    assert st["fresh_lo"] == 2000 and st["fresh_until"] == st["t"] + 5
+    lr = m.get_option("lr")
+    X64 = X.astype(np.float64)
+    for it in range(6):
+        o = oracle_from_state(X, st, p, hd_mode=hd_mode, fresh_iters=5)
+        att, rep = m.debug_step()
+        st1 = m.export_state()
+        s1 = m.stats()
+        out = o.step()
+        assert s1["last_coin"] == int(out["coin"])
+        bad, amb = compare_sets(st1["hd_idx"], o.hd_idx, range(2600), X64, fp32_band(24))
+        assert bad == 0 and amb <= 3
+        badl, _ = compare_sets(st1["ld_idx"], o.ld_idx, range(2600), st["Y"].astype(np.float64), fp32_band(24))
+        assert badl == 0
+        if not out["coin"]:
+            np.testing.assert_array_equal(st1["hd_idx"][:2000], st["hd_idx"][:2000])
+            if it < 5:
+                assert np.any(st1["hd_idx"][2000:] != st["hd_idx"][2000:])
+            else:  # the window has closed
+                np.testing.assert_array_equal(st1["hd_idx"], st["hd_idx"])
+        check_after_refinement(X, st, st1, att, rep, s1, p, lr, label=f"window it {it}", coin=out["coin"],
+                               hd_mode=hd_mode, fresh_iters=5)
+        st = st1
+    m.close()
