@@ -660,11 +660,13 @@ forces_kernel(const StepParams p) {
             if (lane % G == 0) z += w;
             if (on) atomic_add_chunk<CW>(p.A + static_cast<int64_t>(j) * DP + co, dy, -fa);
         }
-        // LD neighbours outside the HD list: repulsion
+        // LD neighbours outside the HD list: repulsion (an entry that is in
+        // the HD list travels as kNoRow: one shuffle a row)
+        const uint32_t nl_rep = (lane < k_ld && !ld_in_hd) ? nl : kNoRow;
         for (int b = 0; b < k_ld; b += R) {
             const int l = b + gq;
-            const uint32_t j = __shfl_sync(kFull, nl, l & 31);
-            const bool on = __shfl_sync(kFull, ld_in_hd ? 0 : 1, l & 31) && l < k_ld;
+            const uint32_t j = __shfl_sync(kFull, nl_rep, l & 31);
+            const bool on = l < k_ld && j != kNoRow;
             float dy[CW], w, winv;
             interact(j, on, dy, w, winv);
             const float fr = 4.f * w * invZ * winv;
@@ -672,19 +674,24 @@ forces_kernel(const StepParams p) {
             for (int c = 0; c < CW; ++c) rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
             if (lane % G == 0) z += w;
         }
-        // Philox-seeded negatives outside S_i, scaled by (N-1)/n_neg
-        for (int b = 0; b < p.n_neg; b += R) {
-            const int s = b + gq;
-            const uint32_t w1 = __shfl_sync(kFull, wq.y, s & 31);
-            const uint32_t w3 = __shfl_sync(kFull, wq.w, s & 31);
-            const uint32_t j = map_other(negative_word(w1, w3, static_cast<uint32_t>(s >> 5)), N, i);
-            const bool on = s < p.n_neg && !hset_has(tab, j);
-            float dy[CW], w, winv;
-            interact(j, on, dy, w, winv);
-            const float fr = p.neg_scale * 4.f * w * invZ * winv;
+        // Philox-seeded negatives outside S_i, scaled by (N-1)/n_neg: lane l
+        // draws and checks negative s0 + l of each block of 32 once (from its
+        // own Philox words), and the passes fetch them by one shuffle a row
+        for (int s0 = 0; s0 < p.n_neg; s0 += 32) {
+            const uint32_t jn = map_other(negative_word(wq.y, wq.w, static_cast<uint32_t>(s0 >> 5)), N, i);
+            const uint32_t jneg = (s0 + lane < p.n_neg && !hset_has(tab, jn)) ? jn : kNoRow;
+            const int cnt = min(32, p.n_neg - s0);
+            for (int b = 0; b < cnt; b += R) {
+                const int e = b + gq;
+                const uint32_t j = __shfl_sync(kFull, jneg, e & 31);
+                const bool on = e < cnt && j != kNoRow;
+                float dy[CW], w, winv;
+                interact(j, on, dy, w, winv);
+                const float fr = p.neg_scale * 4.f * w * invZ * winv;
 #pragma unroll
-            for (int c = 0; c < CW; ++c) rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
-            if (lane % G == 0) z = __fmaf_rn(p.neg_scale, w, z);
+                for (int c = 0; c < CW; ++c) rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
+                if (lane % G == 0) z = __fmaf_rn(p.neg_scale, w, z);
+            }
         }
         // sum over the row groups, scattered: each lane ends with C elements
         // of (A_i, R_i) restricted to its components, which it adds to A_i
