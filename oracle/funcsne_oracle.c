@@ -1256,6 +1256,53 @@ void oracle_mlp_grad_mag(int B, int D, int H, int d, const double *theta, const 
     free(on2);
 }
 
+/* Input standardisation of the placement MLP: per-feature mean and
+ * population standard deviation over the N rows present when the network is
+ * first used (1 where a feature is constant), summed in FP64. */
+void oracle_mlp_stats(int64_t N, int D, const double *X, double *mean, double *std_out)
+{
+    for (int f = 0; f < D; ++f) {
+        double s = 0.0, s2 = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            double v = X[i * D + f];
+            s += v;
+            s2 += v * v;
+        }
+        double m = s / (double)N, var = s2 / (double)N - m * m;
+        mean[f] = m;
+        std_out[f] = var > 0.0 ? sqrt(var) : 1.0;
+    }
+}
+
+/* Network inputs of the rows idx[0..B): bfloat16 of (x - mean) / std. The
+ * rounding to bfloat16 decides a code, so it is taken in the precision the
+ * device computes the value in: mean and std as binary32, then one binary32
+ * subtraction and one binary32 division, each correctly rounded. */
+void oracle_mlp_inputs(int B, int D, const double *X, const int64_t *idx, const double *mean,
+                       const double *std_in, double *out)
+{
+    for (int b = 0; b < B; ++b)
+        for (int f = 0; f < D; ++f) {
+            float x = (float)X[idx[b] * D + f];
+            float v = (x - (float)mean[f]) / (float)std_in[f];
+            out[(size_t)b * D + f] = oracle_bf16((double)v);
+        }
+}
+
+/* Training targets of the rows idx[0..B): y / s with s the root mean square
+ * of the B x d values (1 when they are all zero). Returns s. */
+double oracle_mlp_targets(int B, int d, const double *Y, const int64_t *idx, double *out)
+{
+    double t = 0.0;
+    for (int b = 0; b < B; ++b)
+        for (int c = 0; c < d; ++c) t += Y[idx[b] * d + c] * Y[idx[b] * d + c];
+    double ms = t / ((double)B * d);
+    double sc = ms > 0.0 ? sqrt(ms) : 1.0;
+    for (int b = 0; b < B; ++b)
+        for (int c = 0; c < d; ++c) out[(size_t)b * d + c] = Y[idx[b] * d + c] / sc;
+    return sc;
+}
+
 /* Forward pass only (placement): O = MLP(X) with the same roundings. */
 void oracle_mlp_forward(int B, int D, int H, int d, const double *theta, const double *X, int round, double *O)
 {

@@ -11,7 +11,7 @@ import numpy as np
 
 from .build import build_oracle
 
-__all__ = ["lib", "set_threads", "threads", "philox", "OracleState", "bf16", "mlp_size", "mlp_init", "mlp_grad", "mlp_grad_mag", "mlp_forward", "adam", "bisect", "entropy", "topk_merge", "ld_merge",
+__all__ = ["lib", "set_threads", "threads", "philox", "OracleState", "bf16", "mlp_size", "mlp_init", "mlp_grad", "mlp_grad_mag", "mlp_stats", "mlp_inputs", "mlp_targets", "mlp_forward", "adam", "bisect", "entropy", "topk_merge", "ld_merge",
            "exact_z", "kl_divergence", "exact_grad", "bruteforce_knn", "query_knn",
            "ORACLE_BISECT_TOL", "ORACLE_BISECT_MAXIT", "STREAMS", "CAND_HD", "CAND_LD"]
 
@@ -113,6 +113,12 @@ def _declare(L):
     L.oracle_mlp_grad.restype = C.c_double
     L.oracle_mlp_grad_mag.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
     L.oracle_mlp_grad_mag.restype = None
+    L.oracle_mlp_stats.argtypes = [C.c_int64, C.c_int, _dp, _dp, _dp]
+    L.oracle_mlp_stats.restype = None
+    L.oracle_mlp_inputs.argtypes = [C.c_int, C.c_int, _dp, _lp, _dp, _dp, _dp]
+    L.oracle_mlp_inputs.restype = None
+    L.oracle_mlp_targets.argtypes = [C.c_int, C.c_int, _dp, _lp, _dp]
+    L.oracle_mlp_targets.restype = C.c_double
     L.oracle_mlp_forward.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_int, _dp]
     L.oracle_mlp_forward.restype = None
     L.oracle_adam.argtypes = [C.c_int64, _dp, _dp, _dp, _dp, C.c_int, C.c_double, C.c_double, C.c_double,
@@ -274,6 +280,34 @@ def mlp_grad_mag(theta, X, T, H):
     O = np.zeros((B, d))
     lib().oracle_mlp_grad_mag(B, D, H, d, _p(theta, _dp), _p(X, _dp), _p(T, _dp), _p(g, _dp), _p(O, _dp))
     return g, O
+
+
+def mlp_stats(X):
+    """Per-feature mean and population std (1 for constant features)."""
+    X = _f64(X)
+    N, D = X.shape
+    mean, std = np.zeros(D), np.zeros(D)
+    lib().oracle_mlp_stats(N, D, _p(X, _dp), _p(mean, _dp), _p(std, _dp))
+    return mean, std
+
+
+def mlp_inputs(X, idx, mean, std):
+    """bfloat16 of (x - mean) / std for the rows idx, in binary32 arithmetic."""
+    X = _f64(X)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros((len(idx), X.shape[1]))
+    lib().oracle_mlp_inputs(len(idx), X.shape[1], _p(X, _dp), _p(idx, _lp), _p(_f64(mean), _dp),
+                            _p(_f64(std), _dp), _p(out, _dp))
+    return out
+
+
+def mlp_targets(Y, idx):
+    """(y / s for the rows idx, s = RMS of those values)."""
+    Y = _f64(Y)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros((len(idx), Y.shape[1]))
+    sc = lib().oracle_mlp_targets(len(idx), Y.shape[1], _p(Y, _dp), _p(idx, _lp), _p(out, _dp))
+    return out, sc
 
 
 def mlp_forward(theta, X, H, d, round_bf16=True):

@@ -707,6 +707,31 @@ def test_mlp_magnitudes_bound_and_equal_without_cancellation():
     assert np.mean(np.abs(g) < 0.5 * gm) > 0.1  # signed terms do cancel
 
 
+def test_mlp_standardisation_and_target_scaling():
+    """Closed forms: a feature a + b z (z with mean 0 and population variance
+    1) has mean a and std |b|; a constant feature gets std 1; standardised
+    inputs are bfloat16 values within one bfloat16 rounding of z; targets
+    have RMS 1 (exactly 1 for s computed from them) and all-zero targets keep
+    s = 1."""
+    z = np.array([-1.5, -0.5, 0.5, 1.5, 0.0, 0.0])
+    z = (z - z.mean()) / z.std()
+    X = np.stack([3.0 + 2.0 * z, -1.0 - 0.25 * z, np.full(6, 7.0)], axis=1)
+    mean, std = O.mlp_stats(X)
+    np.testing.assert_allclose(mean, [3.0, -1.0, 7.0], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(std, [2.0, 0.25, 1.0], rtol=1e-12)
+    xin = O.mlp_inputs(X, np.arange(6), mean, std)
+    np.testing.assert_array_equal(xin, O.bf16(xin))
+    np.testing.assert_allclose(xin[:, 0], z, rtol=2 ** -8, atol=1e-6)
+    np.testing.assert_allclose(xin[:, 1], -z, rtol=2 ** -8, atol=1e-6)
+    np.testing.assert_array_equal(xin[:, 2], 0.0)
+    Y = np.random.default_rng(31).standard_normal((50, 3))
+    T, sc = O.mlp_targets(Y, np.arange(10, 40))
+    assert abs(np.sqrt(np.mean(T * T)) - 1.0) < 1e-12
+    np.testing.assert_allclose(T * sc, Y[10:40], rtol=1e-14)
+    T0, s0 = O.mlp_targets(np.zeros((5, 2)), np.arange(5))
+    assert s0 == 1.0 and np.all(T0 == 0)
+
+
 def test_mlp_init_ranges():
     D, H, d = 50, 256, 8
     th = O.mlp_init(D, H, d, 0)
