@@ -223,6 +223,32 @@ __device__ __forceinline__ void warp_sort_nearly_sorted(uint64_t& k, int lane) {
     }
 }
 
+// ---------------------------------------------------------------- packed FP32 pairs
+// sm_100 and later execute two FP32 operations in one instruction (FFMA2,
+// FMUL2); each half is rounded exactly as its scalar counterpart, so a pair
+// costs one issue slot instead of two. A squared distance summed this way
+// keeps two chains (even and odd components) and adds them at the end.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 bcast2(float s) { return make_float2(s, s); }
+// x - y rounded once, as __fsub_rn(x, y): fma(y, -1, x).
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+__device__ __forceinline__ float hsum2(float2 a) { return __fadd_rn(a.x, a.y); }
+// Squared distance between the float4 u and v in two chains:
+// (d0^2 + d2^2) + (d1^2 + d3^2).
+__device__ __forceinline__ float2 sqdiff2_f4(const float4 u, const float4 v, float2 acc) {
+    const float2 d01 = sub2(make_float2(u.x, u.y), make_float2(v.x, v.y));
+    const float2 d23 = sub2(make_float2(u.z, u.w), make_float2(v.z, v.w));
+    acc = fma2(d01, d01, acc);
+    return fma2(d23, d23, acc);
+}
+// The same two chains started from the first pair: (d0^2 + d2^2, d1^2 + d3^2).
+__device__ __forceinline__ float2 sq2_f4(const float4 u, const float4 v) {
+    const float2 d01 = sub2(make_float2(u.x, u.y), make_float2(v.x, v.y));
+    const float2 d23 = sub2(make_float2(u.z, u.w), make_float2(v.z, v.w));
+    return fma2(d23, d23, mul2(d01, d01));
+}
+
 // ---------------------------------------------------------------- warp reductions
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -304,27 +330,19 @@ __device__ __forceinline__ void atomic_add_row(float* dst, const float (&v)[DP],
 }
 
 // ---------------------------------------------------------------- HD distances
-// Exact FP32 squared distance, one lane per candidate, features in order
-// f = 0..D-1 (zero padding adds nothing). xs: the own row in shared memory.
+// Exact FP32 squared distance, one lane per candidate: the squares of the
+// even and of the odd features each summed in feature order (two packed
+// chains), then the two sums added (zero padding adds nothing). Every FP32 HD
+// distance of the library is summed in this order. xs: the own row in
+// shared memory.
 __device__ __forceinline__ float dist_f32(const float* __restrict__ xs,
                                           const float* __restrict__ xc, int n4) {
     const float4* a = reinterpret_cast<const float4*>(xs);
     const float4* b = reinterpret_cast<const float4*>(xc);
-    float acc = 0.f;
+    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
-    for (int q = 0; q < n4; ++q) {
-        const float4 u = a[q];
-        const float4 v = __ldg(b + q);
-        float d = __fsub_rn(u.x, v.x);
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(u.y, v.y);
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(u.z, v.z);
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(u.w, v.w);
-        acc = __fmaf_rn(d, d, acc);
-    }
-    return acc;
+    for (int q = 0; q < n4; ++q) acc = sqdiff2_f4(a[q], __ldg(b + q), acc);
+    return hsum2(acc);
 }
 
 struct ApproxDist {
@@ -352,12 +370,12 @@ __device__ __forceinline__ ApproxDist band_from_row_error(float acc, float E, fl
 __device__ __forceinline__ void fp8x4_to_float(uint32_t w, float s, float (&o)[4]) {
     const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w & 0xffffu), __NV_E4M3);
     const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(w >> 16), __NV_E4M3);
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
-    o[0] = __fmul_rn(a.x, s);
-    o[1] = __fmul_rn(a.y, s);
-    o[2] = __fmul_rn(b.x, s);
-    o[3] = __fmul_rn(b.y, s);
+    const float2 a = mul2(__half22float2(*reinterpret_cast<const __half2*>(&lo)), bcast2(s));
+    const float2 b = mul2(__half22float2(*reinterpret_cast<const __half2*>(&hi)), bcast2(s));
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = b.x;
+    o[3] = b.y;
 }
 
 
@@ -381,21 +399,10 @@ __device__ __forceinline__ float part_f32(const float* __restrict__ xs, const fl
                                           int s, int G) {
     const float4* a = reinterpret_cast<const float4*>(xs);
     const float4* b = reinterpret_cast<const float4*>(xc);
-    float acc = 0.f;
+    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
-    for (int q = s; q < n4; q += G) {
-        const float4 u = a[q];
-        const float4 v = __ldg(b + q);
-        float d = __fsub_rn(u.x, v.x);
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(u.y, v.y);
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(u.z, v.z);
-        acc = __fmaf_rn(d, d, acc);
-        d = __fsub_rn(u.w, v.w);
-        acc = __fmaf_rn(d, d, acc);
-    }
-    return acc;
+    for (int q = s; q < n4; q += G) acc = sqdiff2_f4(a[q], __ldg(b + q), acc);
+    return hsum2(acc);
 }
 
 // The same sum as part_f32 (same order, same bits) with the loads of up to
@@ -409,7 +416,7 @@ __device__ __forceinline__ float part_f32_batched(const float* __restrict__ xs, 
                                                   int n4, int s) {
     const float4* a = reinterpret_cast<const float4*>(xs);
     const float4* b = reinterpret_cast<const float4*>(xc);
-    float acc = 0.f;
+    float2 acc = make_float2(0.f, 0.f);
     for (int q0 = s; q0 < n4; q0 += kBatch * G) {
         float4 v[kBatch];
 #pragma unroll
@@ -420,20 +427,10 @@ __device__ __forceinline__ float part_f32_batched(const float* __restrict__ xs, 
 #pragma unroll
         for (int k = 0; k < kBatch; ++k) {
             const int q = q0 + k * G;
-            if (q < n4) {
-                const float4 u = a[q];
-                float d = __fsub_rn(u.x, v[k].x);
-                acc = __fmaf_rn(d, d, acc);
-                d = __fsub_rn(u.y, v[k].y);
-                acc = __fmaf_rn(d, d, acc);
-                d = __fsub_rn(u.z, v[k].z);
-                acc = __fmaf_rn(d, d, acc);
-                d = __fsub_rn(u.w, v[k].w);
-                acc = __fmaf_rn(d, d, acc);
-            }
+            if (q < n4) acc = sqdiff2_f4(a[q], v[k], acc);
         }
     }
-    return acc;
+    return hsum2(acc);
 }
 
 // FP32 squared distance from the staged own row xs to row cv of X32, for the
@@ -506,35 +503,29 @@ __device__ __forceinline__ float group_rerank_f32(const float* __restrict__ xs, 
 }
 
 // Adds the squared differences between own-row floats 8q .. 8q + 7 and the
-// eight BF16 values of chunk q to acc, in order.
-__device__ __forceinline__ float bf16_chunk_acc(const float* __restrict__ xs, const uint4 raw, int q, float acc) {
+// eight BF16 values of chunk q to the two chains of acc (even and odd
+// features), in order. A BF16 pair widens to FP32 by a shift and a mask.
+__device__ __forceinline__ float2 bf16_pair(uint32_t w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+__device__ __forceinline__ float2 bf16_chunk_acc(const float* __restrict__ xs, const uint4 raw, int q, float2 acc) {
     const float4 x0 = reinterpret_cast<const float4*>(xs)[2 * q];
     const float4 x1 = reinterpret_cast<const float4*>(xs)[2 * q + 1];
-    float d = __fsub_rn(x0.x, __uint_as_float(raw.x << 16));
-    acc = __fmaf_rn(d, d, acc);
-    d = __fsub_rn(x0.y, __uint_as_float(raw.x & 0xffff0000u));
-    acc = __fmaf_rn(d, d, acc);
-    d = __fsub_rn(x0.z, __uint_as_float(raw.y << 16));
-    acc = __fmaf_rn(d, d, acc);
-    d = __fsub_rn(x0.w, __uint_as_float(raw.y & 0xffff0000u));
-    acc = __fmaf_rn(d, d, acc);
-    d = __fsub_rn(x1.x, __uint_as_float(raw.z << 16));
-    acc = __fmaf_rn(d, d, acc);
-    d = __fsub_rn(x1.y, __uint_as_float(raw.z & 0xffff0000u));
-    acc = __fmaf_rn(d, d, acc);
-    d = __fsub_rn(x1.z, __uint_as_float(raw.w << 16));
-    acc = __fmaf_rn(d, d, acc);
-    d = __fsub_rn(x1.w, __uint_as_float(raw.w & 0xffff0000u));
-    acc = __fmaf_rn(d, d, acc);
-    return acc;
+    float2 d = sub2(make_float2(x0.x, x0.y), bf16_pair(raw.x));
+    acc = fma2(d, d, acc);
+    d = sub2(make_float2(x0.z, x0.w), bf16_pair(raw.y));
+    acc = fma2(d, d, acc);
+    d = sub2(make_float2(x1.x, x1.y), bf16_pair(raw.z));
+    acc = fma2(d, d, acc);
+    d = sub2(make_float2(x1.z, x1.w), bf16_pair(raw.w));
+    return fma2(d, d, acc);
 }
 
 // BF16 rows by groups: the distance to the dequantised row and its band
 // (band_from_row_error), for the candidate of every lane. BF16 rows hold nq
 // chunks of 8 values, then a 16-byte chunk whose first four bytes hold the
 // row's error bound E_c >= ||x_c - x~_c||.
-// KB > 0: a lane issues the loads of KB of its chunks before using any
-// (KB = 0: two at a time).
+// A lane issues the loads of KB of its chunks before using any.
 template <int G, int KB>
 __device__ __forceinline__ ApproxDist group_dist_bf16(const float* __restrict__ xs,
                                                       const uint8_t* __restrict__ Xq, int qpitch, int nq,
@@ -546,32 +537,27 @@ __device__ __forceinline__ ApproxDist group_dist_bf16(const float* __restrict__ 
 #pragma unroll
     for (int p = 0; p < G; ++p) {
         const uint32_t cj = __shfl_sync(kFull, cv, p * R + g);
-        float acc = 0.f, nrm = 0.f;
+        float2 acc2 = make_float2(0.f, 0.f);
+        float nrm = 0.f;
         if (cj != kNoRow) {
             const uint4* b = reinterpret_cast<const uint4*>(Xq + static_cast<int64_t>(cj) * qpitch);
-            if constexpr (KB > 0) {
-                // all of a batch's chunk loads in flight before any is used
-                constexpr int kB = KB;
-                for (int q0 = s; q0 < nq; q0 += kB * G) {
-                    uint4 raw[kB];
+            // all of a batch's chunk loads in flight before any is used
+            for (int q0 = s; q0 < nq; q0 += KB * G) {
+                uint4 raw[KB];
 #pragma unroll
-                    for (int k = 0; k < kB; ++k) {
-                        const int q = q0 + k * G;
-                        raw[k] = q < nq ? __ldg(b + q) : make_uint4(0u, 0u, 0u, 0u);
-                    }
-#pragma unroll
-                    for (int k = 0; k < kB; ++k) {
-                        const int q = q0 + k * G;
-                        if (q < nq) acc = bf16_chunk_acc(xs, raw[k], q, acc);
-                    }
+                for (int k = 0; k < KB; ++k) {
+                    const int q = q0 + k * G;
+                    raw[k] = q < nq ? __ldg(b + q) : make_uint4(0u, 0u, 0u, 0u);
                 }
-            } else {
-#pragma unroll 2
-                for (int q = s; q < nq; q += G) acc = bf16_chunk_acc(xs, __ldg(b + q), q, acc);
+#pragma unroll
+                for (int k = 0; k < KB; ++k) {
+                    const int q = q0 + k * G;
+                    if (q < nq) acc2 = bf16_chunk_acc(xs, raw[k], q, acc2);
+                }
             }
             if (s == sn) nrm = __ldg(reinterpret_cast<const float*>(b + nq));
         }
-        acc = group_sum_rt(acc, G);
+        const float acc = group_sum_rt(hsum2(acc2), G);
         const int src = (lane & (R - 1)) * G;
         const float va = __shfl_sync(kFull, acc, src);
         const float vn = __shfl_sync(kFull, nrm, src + sn);
@@ -598,7 +584,8 @@ __device__ __forceinline__ ApproxDist group_dist_fp8(const float* __restrict__ x
 #pragma unroll
     for (int p = 0; p < G; ++p) {
         const uint32_t cj = __shfl_sync(kFull, cv, p * R + g);
-        float acc = 0.f, err = 0.f;
+        float2 acc2 = make_float2(0.f, 0.f);
+        float err = 0.f;
         if (cj != kNoRow) {
             const uint8_t* row = Xq + static_cast<int64_t>(cj) * qpitch;
             const float sc = __ldg(reinterpret_cast<const float*>(row + scale_off));
@@ -613,19 +600,12 @@ __device__ __forceinline__ ApproxDist group_dist_fp8(const float* __restrict__ x
                         float v[4];
                         fp8x4_to_float(w4[m], sc, v);
                         const float4 xi = reinterpret_cast<const float4*>(xs)[4 * q + m];
-                        float d = __fsub_rn(xi.x, v[0]);
-                        acc = __fmaf_rn(d, d, acc);
-                        d = __fsub_rn(xi.y, v[1]);
-                        acc = __fmaf_rn(d, d, acc);
-                        d = __fsub_rn(xi.z, v[2]);
-                        acc = __fmaf_rn(d, d, acc);
-                        d = __fsub_rn(xi.w, v[3]);
-                        acc = __fmaf_rn(d, d, acc);
+                        acc2 = sqdiff2_f4(xi, make_float4(v[0], v[1], v[2], v[3]), acc2);
                     }
                 }
             }
         }
-        acc = group_sum_rt(acc, G);
+        const float acc = group_sum_rt(hsum2(acc2), G);
         const int src = (lane & (R - 1)) * G;
         const float va = __shfl_sync(kFull, acc, src);
         const float ve = __shfl_sync(kFull, err, src);

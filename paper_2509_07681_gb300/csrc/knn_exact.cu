@@ -1,5 +1,5 @@
 // Exact k nearest neighbours by brute force (evaluation of neighbour recall,
-// not part of the iteration). FP32 distances in feature order, ties by index.
+// not part of the iteration). FP32 distances summed as in dist_f32, ties by index.
 // Pass 1: block = 8 queries (one warp each) x one slice of the points; each
 // warp keeps a sorted top-(32*RK) list and merges 32 scanned rows at a time.
 // Pass 2: one warp per query merges the slices' lists.

@@ -52,13 +52,14 @@ __device__ __forceinline__ ListView list_view(const StepParams& p, int hc, int l
 }
 
 // ------------------------------------------------------------------ HD refinement
-// Resident blocks per SM the registers are sized for: the kernel waits
-// mostly on memory; the reduced-precision variants with k_hd <= 32 fit five
-// blocks (40 warps) with little spilling, the others four. The pipelined
-// variant (PF) holds the next point's lists in registers and keeps four
-// blocks (64 registers), which it hides latency with instead.
-template <int XM, int RH, bool PF>
-constexpr int hd_refine_min_blocks() { return (XM != 0 && RH == 1 && !PF) ? 5 : 4; }
+// Resident blocks per SM the registers are sized for: four (64 registers a
+// thread) in every variant. The kernel waits mostly on memory, and the
+// registers hold the batches of row chunks in flight (group_dist_bf16) and,
+// in the pipelined variant (PF), the next point's lists. Five blocks (48
+// registers) with two chunks in flight were slower on wide reduced-precision
+// rows: 0.584 against 0.550 ms (BF16) and 0.698 against 0.643 ms (FP8) for
+// pixels-70k (784-d rows, eight lanes a row).
+constexpr int kHdRefineMinBlocks = 4;
 
 // G: lanes per gathered row, of the FP32 rows (XM = 0) or of the BF16 / FP8
 // rows (the exact re-rank then takes the FP32 rows' p.gf at run time).
@@ -68,7 +69,7 @@ constexpr int hd_refine_min_blocks() { return (XM != 0 && RH == 1 && !PF) ? 5 : 
 // which takes two memory round trips off every point's chain of dependent
 // loads.
 template <int RH, int XM, int G, bool PF>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, hd_refine_min_blocks<XM, RH, PF>())
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, kHdRefineMinBlocks)
 hd_refine_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -187,10 +188,10 @@ hd_refine_kernel(const StepParams p) {
             const float thr = warp_get<RH>(hd2, static_cast<uint32_t>(k_hd - 1));
             ApproxDist a;
             if constexpr (XM == 1)
-                // batched loads pay off with the 64 registers of the k_hd > 32
-                // variant, and in batches of 4 for rows read by lane pairs
-                a = group_dist_bf16<G, RH == 2 ? 8 : (G == 2 ? 4 : 0)>(xs, p.Xq, p.qpitch, p.nq, cv, lane,
-                                                                       p.q_gamma);
+                // a lane's row chunks in flight: 8 with the lists of the
+                // k_hd > 32 variant, 4 otherwise (eight made the 784-d rows
+                // of pixels-70k 26% slower)
+                a = group_dist_bf16<G, RH == 2 ? 8 : 4>(xs, p.Xq, p.qpitch, p.nq, cv, lane, p.q_gamma);
             else  // nq = code words for FP8
                 a = group_dist_fp8<G>(xs, p.Xq, p.qpitch, p.nq, p.qscale_off, cv, lane, p.q_gamma);
             const bool need = valid && __fsub_rd(a.d2, a.band) <= thr;
@@ -308,15 +309,17 @@ __device__ __forceinline__ void load_chunk(const float* __restrict__ src, float 
     }
 }
 
+// Adds scale * v (CW floats as CW/2 pairs) to dst with vector atomics.
 template <int CW>
-__device__ __forceinline__ void atomic_add_chunk(float* dst, const float (&v)[CW], float scale) {
+__device__ __forceinline__ void atomic_add_chunk(float* dst, const float2 (&v)[CW / 2], float scale) {
     if constexpr (CW % 4 == 0) {
 #pragma unroll
-        for (int q = 0; q < CW / 4; ++q)
-            atomicAdd(reinterpret_cast<float4*>(dst) + q,
-                      make_float4(scale * v[4 * q], scale * v[4 * q + 1], scale * v[4 * q + 2], scale * v[4 * q + 3]));
+        for (int q = 0; q < CW / 4; ++q) {
+            const float2 a = mul2(bcast2(scale), v[2 * q]), b = mul2(bcast2(scale), v[2 * q + 1]);
+            atomicAdd(reinterpret_cast<float4*>(dst) + q, make_float4(a.x, a.y, b.x, b.y));
+        }
     } else {
-        atomicAdd(reinterpret_cast<float2*>(dst), make_float2(scale * v[0], scale * v[1]));
+        atomicAdd(reinterpret_cast<float2*>(dst), mul2(bcast2(scale), v[0]));
     }
 }
 
@@ -348,13 +351,13 @@ __device__ __forceinline__ float group_ld_dist(const float (&yi)[DP / G], const 
 #pragma unroll
             for (int c = 0; c < CW; ++c) v[c] = yi[c];
         }
-        float acc = 0.f;
+        float2 acc2 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c < CW; ++c) {
-            const float d = __fsub_rn(yi[c], v[c]);
-            acc = __fmaf_rn(d, d, acc);
+        for (int c = 0; c < CW; c += 2) {
+            const float2 d = sub2(make_float2(yi[c], yi[c + 1]), make_float2(v[c], v[c + 1]));
+            acc2 = fma2(d, d, acc2);
         }
-        acc = group_sum<G>(acc);
+        const float acc = group_sum<G>(hsum2(acc2));
         const float val = __shfl_sync(kFull, acc, (lane % R) * G);
         if (lane / R == p) mine = val;
     }
@@ -401,14 +404,7 @@ __device__ __forceinline__ float ld_dist_rows(const float4 yi, const float* __re
         const uint32_t cj = __shfl_sync(kFull, cv, q * R1 + g);
         const float4 v = cj != kNoRow ? __ldg(reinterpret_cast<const float4*>(Y + static_cast<int64_t>(cj) * DP + 4 * s))
                                       : yi;
-        float d = __fsub_rn(yi.x, v.x);
-        float a = __fmul_rn(d, d);
-        d = __fsub_rn(yi.y, v.y);
-        a = __fmaf_rn(d, d, a);
-        d = __fsub_rn(yi.z, v.z);
-        a = __fmaf_rn(d, d, a);
-        d = __fsub_rn(yi.w, v.w);
-        ps[q] = __fmaf_rn(d, d, a);
+        ps[q] = hsum2(sq2_f4(yi, v));
     }
     group_reduce_scatter<G>(ps, s);
     // lane (g, s) now holds row s R1 + g; row l sits on lane (l mod R1) G + l / R1
@@ -613,18 +609,21 @@ forces_kernel(const StepParams p) {
         if (lane < k_ld) hset_insert(tab, nl);
         __syncwarp();
 
-        float att[CW], rep[CW];
+        // this lane's components as pairs (packed arithmetic)
+        constexpr int CH = CW / 2;
+        float2 yi2[CH], att[CH], rep[CH];
 #pragma unroll
-        for (int c = 0; c < CW; ++c) {
-            att[c] = 0.f;
-            rep[c] = 0.f;
+        for (int c = 0; c < CH; ++c) {
+            yi2[c] = make_float2(yi[2 * c], yi[2 * c + 1]);
+            att[c] = make_float2(0.f, 0.f);
+            rep[c] = make_float2(0.f, 0.f);
         }
         float z = 0.f;
         // One interaction per row group: w, w^{1/alpha} and this lane's
         // components of y_i - y_j. Every lane of the warp executes it (the
         // group reduction is a warp shuffle); lanes with on == false read no
         // row and contribute nothing.
-        auto interact = [&](uint32_t j, bool on, float (&dy)[CW], float& w, float& winv) {
+        auto interact = [&](uint32_t j, bool on, float2 (&dy)[CH], float& w, float& winv) {
             float yj[CW];
             if (on) {
                 load_chunk<CW>(Y + static_cast<int64_t>(j) * DP + co, yj);
@@ -632,13 +631,13 @@ forces_kernel(const StepParams p) {
 #pragma unroll
                 for (int c = 0; c < CW; ++c) yj[c] = yi[c];
             }
-            float r2 = 0.f;
+            float2 r2v = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int c = 0; c < CW; ++c) {
-                dy[c] = __fsub_rn(yi[c], yj[c]);
-                r2 = __fmaf_rn(dy[c], dy[c], r2);
+            for (int c = 0; c < CH; ++c) {
+                dy[c] = sub2(yi2[c], make_float2(yj[2 * c], yj[2 * c + 1]));
+                r2v = fma2(dy[c], dy[c], r2v);
             }
-            r2 = group_sum<G>(r2);
+            const float r2 = group_sum<G>(hsum2(r2v));
             winv = on ? __fdividef(1.f, __fmaf_rn(r2, inv_alpha, 1.f)) : 0.f;
             w = (alpha == 1.f || !on) ? winv : exp2f(alpha * __log2f(winv));
         };
@@ -648,14 +647,15 @@ forces_kernel(const StepParams p) {
             const uint32_t j = warp_get<RH>(nh, static_cast<uint32_t>(e));
             const float pe = warp_get<RH>(pv, static_cast<uint32_t>(e));
             const bool on = e < k_hd;
-            float dy[CW], w, winv;
+            float2 dy[CH];
+            float w, winv;
             interact(j, on, dy, w, winv);
             const float fa = 4.f * pe * p.inv2N * winv;
             const float fr = 4.f * w * invZ * winv;
 #pragma unroll
-            for (int c = 0; c < CW; ++c) {
-                att[c] = __fmaf_rn(fa, dy[c], att[c]);
-                rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
+            for (int c = 0; c < CH; ++c) {
+                att[c] = fma2(bcast2(fa), dy[c], att[c]);
+                rep[c] = fma2(bcast2(fr), dy[c], rep[c]);
             }
             if (lane % G == 0) z += w;
             if (on) atomic_add_chunk<CW>(p.A + static_cast<int64_t>(j) * DP + co, dy, -fa);
@@ -667,11 +667,12 @@ forces_kernel(const StepParams p) {
             const int l = b + gq;
             const uint32_t j = __shfl_sync(kFull, nl_rep, l & 31);
             const bool on = l < k_ld && j != kNoRow;
-            float dy[CW], w, winv;
+            float2 dy[CH];
+            float w, winv;
             interact(j, on, dy, w, winv);
             const float fr = 4.f * w * invZ * winv;
 #pragma unroll
-            for (int c = 0; c < CW; ++c) rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
+            for (int c = 0; c < CH; ++c) rep[c] = fma2(bcast2(fr), dy[c], rep[c]);
             if (lane % G == 0) z += w;
         }
         // Philox-seeded negatives outside S_i, scaled by (N-1)/n_neg: lane l
@@ -685,11 +686,12 @@ forces_kernel(const StepParams p) {
                 const int e = b + gq;
                 const uint32_t j = __shfl_sync(kFull, jneg, e & 31);
                 const bool on = e < cnt && j != kNoRow;
-                float dy[CW], w, winv;
+                float2 dy[CH];
+                float w, winv;
                 interact(j, on, dy, w, winv);
                 const float fr = p.neg_scale * 4.f * w * invZ * winv;
 #pragma unroll
-                for (int c = 0; c < CW; ++c) rep[c] = __fmaf_rn(fr, dy[c], rep[c]);
+                for (int c = 0; c < CH; ++c) rep[c] = fma2(bcast2(fr), dy[c], rep[c]);
                 if (lane % G == 0) z = __fmaf_rn(p.neg_scale, w, z);
             }
         }
@@ -700,9 +702,11 @@ forces_kernel(const StepParams p) {
         constexpr int V = 2 * CW;
         float v[V];
 #pragma unroll
-        for (int c = 0; c < CW; ++c) {
-            v[c] = att[c];
-            v[CW + c] = rep[c];
+        for (int c = 0; c < CH; ++c) {
+            v[2 * c] = att[c].x;
+            v[2 * c + 1] = att[c].y;
+            v[CW + 2 * c] = rep[c].x;
+            v[CW + 2 * c + 1] = rep[c].y;
         }
         int base = 0;
         bool owner = true;
@@ -807,12 +811,14 @@ forces_pair_kernel(const StepParams p) {
         __syncwarp();
         if (lane < k_ld) hset_insert(tab, nl);
 
-        float att[4] = {0.f, 0.f, 0.f, 0.f}, rep[4] = {0.f, 0.f, 0.f, 0.f};
+        // this lane's four components as two pairs (packed arithmetic)
+        float2 att[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        float2 rep[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         float z = 0.f;
         // Two rows per lane: r2, w and w^{1/alpha} of rows j[0], j[1]
         // (kNoRow: no row, contributes nothing) and this lane's components
         // of y_i - y_j. Every lane executes it (group reductions are shuffles).
-        auto interact2 = [&](const uint32_t (&j)[2], float (&dy)[2][4], float (&w)[2], float (&winv)[2]) {
+        auto interact2 = [&](const uint32_t (&j)[2], float2 (&dy)[2][2], float (&w)[2], float (&winv)[2]) {
             float4 yj[2];
 #pragma unroll
             for (int m = 0; m < 2; ++m)
@@ -821,14 +827,9 @@ forces_pair_kernel(const StepParams p) {
             float r2[2];
 #pragma unroll
             for (int m = 0; m < 2; ++m) {
-                dy[m][0] = __fsub_rn(yi.x, yj[m].x);
-                dy[m][1] = __fsub_rn(yi.y, yj[m].y);
-                dy[m][2] = __fsub_rn(yi.z, yj[m].z);
-                dy[m][3] = __fsub_rn(yi.w, yj[m].w);
-                float a = __fmul_rn(dy[m][0], dy[m][0]);
-                a = __fmaf_rn(dy[m][1], dy[m][1], a);
-                a = __fmaf_rn(dy[m][2], dy[m][2], a);
-                r2[m] = __fmaf_rn(dy[m][3], dy[m][3], a);
+                dy[m][0] = sub2(make_float2(yi.x, yi.y), make_float2(yj[m].x, yj[m].y));
+                dy[m][1] = sub2(make_float2(yi.z, yi.w), make_float2(yj[m].z, yj[m].w));
+                r2[m] = hsum2(fma2(dy[m][1], dy[m][1], mul2(dy[m][0], dy[m][0])));
             }
 #pragma unroll
             for (int q = 1; q < G; q <<= 1) {
@@ -853,21 +854,24 @@ forces_pair_kernel(const StepParams p) {
                 pe[m] = warp_get<RH>(pv, static_cast<uint32_t>(e));
                 j[m] = e < k_hd ? jj : kNoRow;
             }
-            float dy[2][4], w[2], winv[2];
+            float2 dy[2][2];
+            float w[2], winv[2];
             interact2(j, dy, w, winv);
 #pragma unroll
             for (int m = 0; m < 2; ++m) {
                 const float fa = 4.f * pe[m] * p.inv2N * winv[m];
                 const float fr = 4.f * w[m] * invZ * winv[m];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    att[c] = __fmaf_rn(fa, dy[m][c], att[c]);
-                    rep[c] = __fmaf_rn(fr, dy[m][c], rep[c]);
+                for (int c = 0; c < 2; ++c) {
+                    att[c] = fma2(bcast2(fa), dy[m][c], att[c]);
+                    rep[c] = fma2(bcast2(fr), dy[m][c], rep[c]);
                 }
                 if (leader) z += w[m];
-                if (j[m] != kNoRow)
+                if (j[m] != kNoRow) {
+                    const float2 a = mul2(bcast2(-fa), dy[m][0]), b = mul2(bcast2(-fa), dy[m][1]);
                     atomicAdd(reinterpret_cast<float4*>(p.A + static_cast<int64_t>(j[m]) * DP + co),
-                              make_float4(-fa * dy[m][0], -fa * dy[m][1], -fa * dy[m][2], -fa * dy[m][3]));
+                              make_float4(a.x, a.y, b.x, b.y));
+                }
             }
         }
         // repulsion-only rows through the queue: positions [head, tail) of
@@ -885,13 +889,14 @@ forces_pair_kernel(const StepParams p) {
                     j[m] = pos < tail ? ring[pos & (kRepRing - 1)] : kNoRow;
                     scl[m] = pos < nld ? 1.f : p.neg_scale;
                 }
-                float dy[2][4], w[2], winv[2];
+                float2 dy[2][2];
+                float w[2], winv[2];
                 interact2(j, dy, w, winv);
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
                     const float fr = scl[m] * 4.f * w[m] * invZ * winv[m];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) rep[c] = __fmaf_rn(fr, dy[m][c], rep[c]);
+                    for (int c = 0; c < 2; ++c) rep[c] = fma2(bcast2(fr), dy[m][c], rep[c]);
                     if (leader) z = __fmaf_rn(scl[m], w[m], z);
                 }
                 head = min(head + R, tail);
@@ -918,7 +923,7 @@ forces_pair_kernel(const StepParams p) {
         // sum over the row groups, scattered over the lanes that share lane
         // mod G: each lane ends with elements of (A_i, R_i) restricted to its
         // components, which it adds to A_i or stores into R_i
-        float v[8] = {att[0], att[1], att[2], att[3], rep[0], rep[1], rep[2], rep[3]};
+        float v[8] = {att[0].x, att[0].y, att[1].x, att[1].y, rep[0].x, rep[0].y, rep[1].x, rep[1].y};
         int base = 0;
         bool owner = true;
         reduce_scatter_stages<8, 8, 16, G>(v, lane, base, owner);
