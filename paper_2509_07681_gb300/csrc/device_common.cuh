@@ -110,7 +110,8 @@ __device__ __forceinline__ void cmpx_stage(uint64_t (&k)[R], int lane, int size,
                 const int e = r * 32 + lane;
                 const bool asc = (e & size) == 0;
                 const uint64_t a = k[r], b = k[r | rs];
-                const bool sw = asc ? (a > b) : (a < b);
+                // out of order for the stage's direction (equal keys may swap)
+                const bool sw = (b < a) == asc;
                 k[r] = sw ? b : a;
                 k[r | rs] = sw ? a : b;
             }
@@ -122,9 +123,11 @@ __device__ __forceinline__ void cmpx_stage(uint64_t (&k)[R], int lane, int size,
             const uint64_t o = shfl_xor64(k[r], stride);
             const bool asc = (e & size) == 0;
             const bool lower = (lane & stride) == 0;
-            const uint64_t mn = k[r] < o ? k[r] : o;
-            const uint64_t mx = k[r] < o ? o : k[r];
-            k[r] = (lower == asc) ? mn : mx;
+            // keep the minimum (lower == asc) or the maximum of the pair:
+            // take the partner's key when it is smaller or larger respectively
+            // (one 64-bit compare, one select)
+            const bool take = (o < k[r]) == (lower == asc);
+            k[r] = take ? o : k[r];
         }
     }
 }
@@ -168,11 +171,6 @@ __device__ __forceinline__ uint64_t shfl_up64(uint64_t v, int d) {
     const uint32_t hi = __shfl_up_sync(kFull, static_cast<uint32_t>(v >> 32), d);
     return (static_cast<uint64_t>(hi) << 32) | lo;
 }
-__device__ __forceinline__ uint64_t shfl_down64(uint64_t v, int d) {
-    const uint32_t lo = __shfl_down_sync(kFull, static_cast<uint32_t>(v), d);
-    const uint32_t hi = __shfl_down_sync(kFull, static_cast<uint32_t>(v >> 32), d);
-    return (static_cast<uint64_t>(hi) << 32) | lo;
-}
 
 // Inserts the candidate keys that precede thr (one per lane) into a sorted
 // warp list of 32*R keys, one at a time: each insertion finds its position by
@@ -200,25 +198,6 @@ __device__ __forceinline__ void insert_candidates(uint64_t (&lst)[R], uint64_t c
         for (int r = 0; r < R; ++r) {
             const int e = r * 32 + lane;
             lst[r] = e < pos ? lst[r] : (e == pos ? c : prev[r]);
-        }
-    }
-}
-
-// Sorts one key per lane ascending by odd-even transposition, stopping as
-// soon as the list is sorted (a list that was sorted at the previous
-// iteration usually needs no pass or one). At most 32 passes.
-__device__ __forceinline__ void warp_sort_nearly_sorted(uint64_t& k, int lane) {
-    for (int pass = 0; pass < 32; ++pass) {
-        const uint64_t nxt = shfl_down64(k, 1);
-        if (__all_sync(kFull, lane == 31 || k <= nxt)) return;
-#pragma unroll
-        for (int ph = 0; ph < 2; ++ph) {
-            // pairs (2m + ph, 2m + ph + 1)
-            const bool low = ((lane - ph) & 1) == 0;
-            const int partner = low ? lane + 1 : lane - 1;
-            const bool has = partner >= 0 && partner < 32;
-            const uint64_t o = shfl64(k, has ? partner : lane);
-            if (has) k = low ? (k < o ? k : o) : (k < o ? o : k);
         }
     }
 }

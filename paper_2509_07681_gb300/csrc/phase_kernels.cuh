@@ -28,8 +28,9 @@ namespace fsne {
 
 constexpr int kWarpsPerBlock = 8;
 // Up to this many qualifying candidates are merged by single insertions;
-// more go through the bitonic network.
-constexpr int kInsertMax = 12;
+// more go through the bitonic network (HD and LD refinement).
+constexpr int kInsertMaxHd = 12;
+constexpr int kInsertMaxLd = 8;
 
 struct ListView {
     const int32_t* __restrict__ hd_idx_c;
@@ -209,7 +210,7 @@ hd_refine_kernel(const StepParams p) {
         const uint64_t kth = warp_get64<RH>(keys, static_cast<uint32_t>(k_hd - 1));
         const int nqual = __popc(__ballot_sync(kFull, ck < kth));
         if (nqual > 0) {
-            if (nqual > kInsertMax)
+            if (nqual > kInsertMaxHd)
                 merge_candidates<RH>(keys, ck, lane);
             else
                 insert_candidates<RH>(keys, ck, kth, lane);
@@ -503,7 +504,7 @@ ld_refine_kernel(const StepParams p) {
         warp_sort<1>(lk, lane);
         const uint64_t thr = shfl64(lk[0], k_ld - 1);
         const int nqual = __popc(__ballot_sync(kFull, ck < thr));
-        if (nqual > kInsertMax)
+        if (nqual > kInsertMaxLd)
             merge_candidates<1>(lk, ck, lane);
         else if (nqual > 0)
             insert_candidates<1>(lk, ck, thr, lane);
