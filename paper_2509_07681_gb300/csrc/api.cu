@@ -196,6 +196,7 @@ StepParams step_params(const funcsne* h) {
     const float gamma = static_cast<float>((h->xs_floats + 4) * std::ldexp(1.0, -24) * 1.01);
     p.q_gamma = gamma;
     p.seed = h->seed;
+    p.pk = philox_keys(h->seed);
     p.X32 = h->X32;
     p.Xq = h->Xq;
     p.Y = h->Y;

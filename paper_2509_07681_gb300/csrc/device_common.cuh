@@ -20,25 +20,32 @@ constexpr uint64_t kSentinel = ~0ull;  // larger than every valid (d2, idx) key
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two 32x32->64-bit
 // multiplies; the 64-bit key is bumped by the Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                        uint64_t seed) {
+__device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3, uint32_t k0,
+                                             uint32_t k1) {
+    const uint32_t ha = __umulhi(kPhiloxM0, c0), la = kPhiloxM0 * c0;
+    const uint32_t hb = __umulhi(kPhiloxM1, c2), lb = kPhiloxM1 * c2;
+    c0 = hb ^ c1 ^ k0;
+    c1 = lb;
+    c2 = ha ^ c3 ^ k1;
+    c3 = la;
+}
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t seed) {
     uint32_t k0 = static_cast<uint32_t>(seed);
     uint32_t k1 = static_cast<uint32_t>(seed >> 32);
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
+            k0 += kPhiloxW0;
+            k1 += kPhiloxW1;
         }
-        const uint32_t ha = __umulhi(0xD2511F53u, c0), la = 0xD2511F53u * c0;
-        const uint32_t hb = __umulhi(0xCD9E8D57u, c2), lb = 0xCD9E8D57u * c2;
-        const uint32_t n0 = hb ^ c1 ^ k0;
-        const uint32_t n2 = ha ^ c3 ^ k1;
-        c0 = n0;
-        c1 = lb;
-        c2 = n2;
-        c3 = la;
+        philox_round(c0, c1, c2, c3, k0, k1);
     }
+    return make_uint4(c0, c1, c2, c3);
+}
+// The same block with the round keys precomputed (philox_keys).
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const PhiloxKeys& K) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) philox_round(c0, c1, c2, c3, K.k0[r], K.k1[r]);
     return make_uint4(c0, c1, c2, c3);
 }
 

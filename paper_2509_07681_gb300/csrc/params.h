@@ -90,6 +90,30 @@ inline int lanes_per_row(int bytes) {
     return 8;
 }
 
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): multipliers of the two
+// 32x32->64-bit products and the Weyl constants that bump the 64-bit key
+// between rounds.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+
+// The ten round keys of a seed (round r: seed + r Weyl constants, mod 2^32
+// per word). The iteration kernels draw one block per lane and point; they
+// take the keys from their launch parameters instead of bumping them.
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+inline PhiloxKeys philox_keys(uint64_t seed) {
+    PhiloxKeys K;
+    uint32_t a = static_cast<uint32_t>(seed), b = static_cast<uint32_t>(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = a;
+        K.k1[r] = b;
+        a += kPhiloxW0;
+        b += kPhiloxW1;
+    }
+    return K;
+}
+
 struct StepParams {
     int64_t N;
     int32_t k_hd, k_ld, n_neg;
@@ -107,6 +131,7 @@ struct StepParams {
     float alpha, inv_alpha, inv2N, neg_scale, log_perp;
     float q_gamma;          // relative FP32 rounding bound of a distance evaluation
     uint64_t seed;
+    PhiloxKeys pk;          // round keys of seed
     const float* X32;
     const uint8_t* Xq;
     float* Y;

@@ -94,7 +94,9 @@ hd_refine_kernel(const StepParams p) {
         xbuf[f] = 0.f;
         if (PF) xbuf[p.xs_floats + f] = 0.f;
     }
-    unsigned long long c_new = 0, c_scored = 0, c_rerank = 0;
+    // per-lane counts: a lane scores at most one candidate a point, so each
+    // stays below N < 2^31; widened for the block sums
+    uint32_t c_new = 0, c_scored = 0, c_rerank = 0;
 
     // the lists of point g (HD indices and distances, LD indices)
     auto load_lists = [&](int64_t g, uint32_t (&hi)[RH], float (&h2)[RH], uint32_t& li) {
@@ -145,7 +147,7 @@ hd_refine_kernel(const StepParams p) {
         } else {
             load_lists(gi, hidx, hd2, lidx);
         }
-        const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+        const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.pk);
         if constexpr (PF) {
             cp_async_wait<1>();  // this point's row has landed
         } else {
@@ -247,7 +249,7 @@ hd_refine_kernel(const StepParams p) {
         cr += __shfl_xor_sync(kFull, cr, m);
     }
     if (lane == 0) {
-        s_cnt[wib][0] = c_new;
+        s_cnt[wib][0] = static_cast<unsigned long long>(c_new);
         s_cnt[wib][1] = cs;
         s_cnt[wib][2] = cr;
     }
@@ -416,6 +418,20 @@ __device__ __forceinline__ float ld_dist_rows(const float4 yi, const float* __re
 // per row, one 16-byte load each), and the neighbour-of-neighbour index
 // loads are issued before the old list's rows are gathered, so the two
 // memory round trips overlap. Otherwise group_ld_dist with ld_lanes lanes.
+// The Philox block of a lane in the LD refinement, with the round keys from
+// the launch parameters for rows of 16 floats and bumped in the kernel
+// otherwise. With the parameter keys the compiler keeps some of them in
+// registers; measured after a 200-iteration burn-in, that paid at d = 16
+// (spectrum-1m: 0.821 to 0.790 ms) and cost at d = 8 and d = 32
+// (swissroll-200k 0.131 to 0.135 ms, lowrank-2m 2.08 to 2.18 ms).
+template <int DP>
+__device__ __forceinline__ uint4 ld_philox(uint32_t t, uint32_t i, int lane, const StepParams& p) {
+    if constexpr (DP == 16)
+        return philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.pk);
+    else
+        return philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+}
+
 template <int DP, int RH, bool PAIR>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
 ld_refine_kernel(const StepParams p) {
@@ -446,7 +462,7 @@ ld_refine_kernel(const StepParams p) {
         bool cand_valid;
         if constexpr (PAIR) {
             const float4 yi = __ldg(reinterpret_cast<const float4*>(Y + gi * DP + 4 * (lane % (DP / 4))));
-            const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+            const uint4 w = ld_philox<DP>(t, i, lane, p);
             const uint32_t e0 = lane < kLdNnEnd ? map_index(w.z, k_ld) : map_index(w.z, k_hd);
             const uint32_t lv = __shfl_sync(kFull, lidx, static_cast<int>(e0 & 31u));
             const uint32_t hv = warp_get<RH>(hidx, e0);
@@ -472,7 +488,7 @@ ld_refine_kernel(const StepParams p) {
             constexpr int GL = ld_lanes<DP>();
             float yi[DP / GL];
             load_chunk<DP / GL>(Y + gi * DP + (DP / GL) * (lane % GL), yi);
-            const uint4 w = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+            const uint4 w = ld_philox<DP>(t, i, lane, p);
             hset_clear(tab, lane);
             __syncwarp();
             if (lane < k_ld) hset_insert(tab, lidx);
@@ -597,7 +613,7 @@ forces_kernel(const StepParams p) {
                         : 0xffffffffu;
         float yi[CW];
         load_chunk<CW>(Y + gi * DP + co, yi);
-        const uint4 wq = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+        const uint4 wq = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.pk);
         // S_i = HD u LD lists of t+1 as a warp hash set
         hset_clear(tab, lane);
         __syncwarp();
@@ -800,7 +816,7 @@ forces_pair_kernel(const StepParams p) {
             lane < k_ld ? FSNE_IDX(static_cast<uint32_t>(__ldg(ld_new + gi * k_ld + lane)), N, i, &p.sc->err)
                         : 0xffffffffu;
         const float4 yi = __ldg(reinterpret_cast<const float4*>(Y + gi * DP + co));
-        const uint4 wq = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.seed);
+        const uint4 wq = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.pk);
         // S_i = HD u LD lists of t+1 as a warp hash set
         hset_clear(tab, lane);
         __syncwarp();
