@@ -464,8 +464,14 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int k) {
     return pos;
 }
 
-// The same FP32 distances (same grouping, hence the same bits) for only the
-// lanes with need == true, packed R to a pass. All lanes must call it.
+// The same FP32 distances (same grouping and summation order, hence the
+// same bits) for only the lanes with need == true, packed R to a pass. All
+// lanes must call it. NARROW: rows read by one or two lanes load all their
+// chunks at once (one round trip; spectrum-1m BF16 refinement 1.161 to 1.129
+// ms); callers whose reduced-precision rows take four or more lanes keep the
+// plain loop, which their code generation prefers (swissroll-200k 0.368 to
+// 0.356 ms).
+template <bool NARROW = true>
 __device__ __forceinline__ float group_rerank_f32(const float* __restrict__ xs, const float* __restrict__ X32,
                                                   int xpitch, int n4, uint32_t c, bool need, int lane, int G) {
     const uint32_t m = __ballot_sync(kFull, need);
@@ -478,7 +484,15 @@ __device__ __forceinline__ float group_rerank_f32(const float* __restrict__ xs, 
         const int src = (k < nn) ? nth_set_bit(m, k) : 0;
         const uint32_t cj = __shfl_sync(kFull, c, src);
         float acc = 0.f;
-        if (k < nn) acc = part_f32(xs, X32 + static_cast<int64_t>(cj) * xpitch, n4, s, G);
+        if (k < nn) {
+            const float* row = X32 + static_cast<int64_t>(cj) * xpitch;
+            if (NARROW && G == 2)
+                acc = part_f32_batched<2>(xs, row, n4, s);
+            else if (NARROW && G == 1)
+                acc = part_f32_batched<1>(xs, row, n4, s);
+            else
+                acc = part_f32(xs, row, n4, s, G);
+        }
         acc = group_sum_rt(acc, G);
         const int r = rank - base;
         const bool mine_here = need && r >= 0 && r < R;

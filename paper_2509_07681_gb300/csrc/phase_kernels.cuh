@@ -53,14 +53,16 @@ __device__ __forceinline__ ListView list_view(const StepParams& p, int hc, int l
 }
 
 // ------------------------------------------------------------------ HD refinement
-// Resident blocks per SM the registers are sized for: four (64 registers a
-// thread) in every variant. The kernel waits mostly on memory, and the
-// registers hold the batches of row chunks in flight (group_dist_bf16) and,
-// in the pipelined variant (PF), the next point's lists. Five blocks (48
-// registers) with two chunks in flight were slower on wide reduced-precision
-// rows: 0.584 against 0.550 ms (BF16) and 0.698 against 0.643 ms (FP8) for
-// pixels-70k (784-d rows, eight lanes a row).
-constexpr int kHdRefineMinBlocks = 4;
+// Resident blocks per SM the registers are sized for. The kernel waits mostly
+// on memory; the registers hold the batches of row chunks in flight
+// (group_dist_bf16) and, in the pipelined variant (PF), the next point's
+// lists. Five blocks (48 registers) pay for FP32 rows read by up to four
+// lanes with k_hd <= 32 (spectrum-1m 1.116 to 1.096 ms, swissroll-200k 0.321
+// to 0.308 ms); the reduced-precision, wide-row and k_hd = 64 variants are
+// faster with four (64 registers): five made pixels-70k BF16 0.517 to 0.575
+// ms and spectrum-1m BF16 1.169 to 1.190 ms.
+template <int XM, int RH, int G>
+constexpr int hd_refine_min_blocks() { return (XM == 0 && RH == 1 && G <= 4) ? 5 : 4; }
 
 // G: lanes per gathered row, of the FP32 rows (XM = 0) or of the BF16 / FP8
 // rows (the exact re-rank then takes the FP32 rows' p.gf at run time).
@@ -70,7 +72,7 @@ constexpr int kHdRefineMinBlocks = 4;
 // which takes two memory round trips off every point's chain of dependent
 // loads.
 template <int RH, int XM, int G, bool PF>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, kHdRefineMinBlocks)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, hd_refine_min_blocks<XM, RH, G>())
 hd_refine_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -202,7 +204,7 @@ hd_refine_kernel(const StepParams p) {
             c_rerank += need ? 1 : 0;
             // candidates that can enter: the exact FP32 distance, computed as
             // in FP32 mode (same grouping), so the lists equal FP32 mode's
-            const float d = group_rerank_f32(xs, p.X32, p.xpitch, p.n4, c, need, lane, p.gf);
+            const float d = group_rerank_f32<(G <= 2)>(xs, p.X32, p.xpitch, p.n4, c, need, lane, p.gf);
             if (need) ck = make_key(d, c);
         }
         // flag: some candidate precedes the old k-th entry
