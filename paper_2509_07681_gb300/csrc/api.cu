@@ -802,9 +802,8 @@ int funcsne_create(const float* X, int64_t N, int32_t D, int32_t d, int32_t k_hd
         CREATE_CUDA(launch_hd_finalize(f, blocks, s));
     }
     {
-        // FP64 scratch for the projection: R, mu, moments and block partials
-        const int64_t cols = D > h->DP ? D : h->DP;
-        const int64_t len = static_cast<int64_t>(D) * d + D + 2 * h->DP + 1024 * cols;
+        // scratch for the projection (launch_init_y), then the first Z estimate
+        const int64_t len = init_y_scratch_len(D, d, h->DP);
         double* scratch = nullptr;
         CREATE_CUDA(dalloc(&scratch, static_cast<size_t>(len)));
         cudaError_t e = launch_init_y(h->X32, N, D, h->xpitch, d, h->DP, seed, 0u, h->Y, scratch, len, s);
@@ -980,8 +979,7 @@ int funcsne_set_stream(funcsne_t* h, void* stream) {
 // Y = a random linear projection of the data, Philox counter (ctr, f,
 // INIT_Y, c), each LD dimension at the initial scale.
 int project_embedding(funcsne* h, uint32_t ctr) {
-    const int64_t cols = h->D > h->DP ? h->D : h->DP;
-    const int64_t len = static_cast<int64_t>(h->D) * h->d + h->D + 2 * h->DP + 1024 * cols;
+    const int64_t len = init_y_scratch_len(h->D, h->d, h->DP);
     double* scratch = nullptr;
     FSNE_CUDA(h, dalloc(&scratch, static_cast<size_t>(len)));
     cudaError_t e = launch_init_y(h->X32, h->N, h->D, h->xpitch, h->d, h->DP, h->seed, ctr, h->Y, scratch, len,

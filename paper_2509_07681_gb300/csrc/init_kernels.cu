@@ -98,32 +98,62 @@ __global__ void __launch_bounds__(256) hd_finalize_kernel(FinalizeParams f) {
     }
 }
 
-// Gaussian matrix R (D x d, FP64) from counter (ctr, f, INIT_Y, c), Box-Muller.
-__global__ void gauss_matrix_kernel(int D, int d, uint32_t ctr, uint64_t seed, double* R) {
+// Gaussian matrix R from counter (ctr, f, INIT_Y, c), Box-Muller in FP64,
+// stored as FP32 in D4 rows of DP columns (rows f >= D and columns c >= d
+// zero, so the padding of X and of Y contributes nothing).
+__global__ void gauss_matrix_kernel(int D, int D4, int d, int DP, uint32_t ctr, uint64_t seed, float* R) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= D * d) return;
-    const int fi = e / d, c = e % d;
+    if (e >= D4 * DP) return;
+    const int fi = e / DP, c = e % DP;
+    if (fi >= D || c >= d) {
+        R[e] = 0.f;
+        return;
+    }
     const uint4 w = philox(ctr, static_cast<uint32_t>(fi), kStreamInitY, static_cast<uint32_t>(c), seed);
     const double u1 = (static_cast<double>(w.x) + 0.5) * (1.0 / 4294967296.0);
     const double u2 = (static_cast<double>(w.y) + 0.5) * (1.0 / 4294967296.0);
-    R[e] = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+    R[e] = static_cast<float>(sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
 }
 
 // Column sums (FP64) of a row-major N x cols FP32 matrix with row pitch
-// `pitch`: block b sums rows [b*rows_per_block, ...) into part[b*cols + c].
-__global__ void col_sums_kernel(const float* __restrict__ M, int64_t N, int cols, int pitch,
-                                int64_t rows_per_block, const double* __restrict__ shift, int square,
-                                double* part) {
+// `pitch` (of squared deviations from `shift` when `square`): block b sums
+// rows [b * rows_per_block, ...) into part[b * cols + c]. Up to 128 columns,
+// the block's threads form blockDim / cols row lanes per column, whose sums
+// are then added in row-lane order; wider matrices take a column per thread.
+__global__ void __launch_bounds__(256) col_sums_kernel(const float* __restrict__ M, int64_t N, int cols, int pitch,
+                                                       int64_t rows_per_block, const double* __restrict__ shift,
+                                                       int square, double* part) {
+    __shared__ double s_part[256];
     const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per_block;
     const int64_t r1 = min(N, r0 + rows_per_block);
+    if (cols <= 128) {
+        const int nrl = static_cast<int>(blockDim.x) / cols;
+        const int rl = static_cast<int>(threadIdx.x) / cols, c = static_cast<int>(threadIdx.x) % cols;
+        double acc = 0.0;
+        if (rl < nrl) {
+            const double sh = shift ? shift[c] : 0.0;
+            for (int64_t r = r0 + rl; r < r1; r += nrl) {
+                const double v = static_cast<double>(M[r * pitch + c]) - sh;
+                acc += square ? v * v : v;
+            }
+        }
+        s_part[threadIdx.x] = acc;
+        __syncthreads();
+        if (static_cast<int>(threadIdx.x) < cols) {
+            double t = 0.0;
+            for (int k = 0; k < nrl; ++k) t += s_part[k * cols + threadIdx.x];
+            part[static_cast<int64_t>(blockIdx.x) * cols + threadIdx.x] = t;
+        }
+        return;
+    }
     for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-        double s = 0.0;
+        double acc = 0.0;
         const double sh = shift ? shift[c] : 0.0;
         for (int64_t r = r0; r < r1; ++r) {
             const double v = static_cast<double>(M[r * pitch + c]) - sh;
-            s += square ? v * v : v;
+            acc += square ? v * v : v;
         }
-        part[static_cast<int64_t>(blockIdx.x) * cols + c] = s;
+        part[static_cast<int64_t>(blockIdx.x) * cols + c] = acc;
     }
 }
 
@@ -136,31 +166,49 @@ __global__ void reduce_parts_kernel(const double* part, int nparts, int cols, do
     out[c] = s * scale;
 }
 
-// Y[i, c] = sum_f (x_if - mu_f) R[f, c] (FP64 accumulation), c < d; padding 0.
-__global__ void project_kernel(const float* __restrict__ X, int64_t N, int D, int xpitch,
-                               const double* __restrict__ mu, const double* __restrict__ R, int d,
-                               int DP, float* Y) {
+// Y[i, c] = sum_f (x_if - mu_f) R[f, c] in FP32, thread per point, rows read
+// 16 bytes at a time; R (FP32, zero padded) is read warp-uniformly.
+template <int DP>
+__global__ void __launch_bounds__(128) project_kernel(const float* __restrict__ X, int64_t N, int D, int n4,
+                                                      int xpitch, const double* __restrict__ mu,
+                                                      const float* __restrict__ R, float* Y) {
+    extern __shared__ float s_mu[];
+    for (int f = threadIdx.x; f < 4 * n4; f += blockDim.x) s_mu[f] = f < D ? static_cast<float>(mu[f]) : 0.f;
+    __syncthreads();
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double acc[32];
-    for (int c = 0; c < d; ++c) acc[c] = 0.0;
-    for (int f = 0; f < D; ++f) {
-        const double v = static_cast<double>(X[i * xpitch + f]) - mu[f];
-        for (int c = 0; c < d; ++c) acc[c] += v * R[f * d + c];
+    float acc[DP];
+#pragma unroll
+    for (int c = 0; c < DP; ++c) acc[c] = 0.f;
+    const float4* xr = reinterpret_cast<const float4*>(X + i * xpitch);
+    for (int q = 0; q < n4; ++q) {
+        const float4 x = __ldg(xr + q);
+        const float v[4] = {x.x - s_mu[4 * q], x.y - s_mu[4 * q + 1], x.z - s_mu[4 * q + 2], x.w - s_mu[4 * q + 3]};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float* r = R + (4 * q + k) * DP;
+#pragma unroll
+            for (int c = 0; c < DP; ++c) acc[c] = __fmaf_rn(v[k], __ldg(r + c), acc[c]);
+        }
     }
-    for (int c = 0; c < DP; ++c) Y[i * DP + c] = c < d ? static_cast<float>(acc[c]) : 0.f;
+#pragma unroll
+    for (int c = 0; c < DP; ++c) Y[i * DP + c] = acc[c];
 }
 
-// Y[:, c] *= target_std / std_c  (std from FP64 moments).
-__global__ void scale_cols_kernel(float* Y, int64_t N, int d, int DP, const double* mean,
-                                  const double* var, double target_std) {
+// Scale factors of the columns: target_std / std_c (1 for a zero variance),
+// from the FP64 moments.
+__global__ void col_scale_kernel(const double* var, int d, int DP, double target_std, float* sc) {
+    const int c = threadIdx.x;
+    if (c >= DP) return;
+    const double sd = c < d ? sqrt(var[c]) : 0.0;
+    sc[c] = static_cast<float>(sd > 0.0 ? target_std / sd : 1.0);
+}
+
+// Y[:, c] *= sc[c] (DP a power of two).
+__global__ void scale_cols_kernel(float* Y, int64_t n, int DP, const float* __restrict__ sc) {
     const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= N * DP) return;
-    const int c = static_cast<int>(e % DP);
-    if (c >= d) return;
-    const double sd = sqrt(var[c]);
-    const double s = sd > 0.0 ? target_std / sd : 1.0;
-    Y[e] = static_cast<float>(static_cast<double>(Y[e]) * s);
+    if (e >= n) return;
+    Y[e] *= __ldg(sc + (static_cast<int>(e) & (DP - 1)));
 }
 
 // Warp per point: z_i = sum_{j in S_i} w_ij + (N-1)/n_neg sum_s 1[j_s not in S_i] w_ij_s
@@ -223,35 +271,37 @@ __global__ void zinit_finish_kernel(const double* part, int n, DevScalars* sc) {
     sc->last_Z = s;
 }
 
-// Upper bound, in FP32, of sqrt(s) for an FP64 sum s of D <= 4096 exact
-// squares: the relative margins 2^-40 cover the sum's and the square
-// root's rounding.
-__device__ __forceinline__ float sqrt_bound(double s) {
-    constexpr double kUp = 1.0 + 1.0 / 1099511627776.0;
-    return __double2float_ru(sqrt(s * kUp) * kUp);
+// Upper bound of a row's rounding error norm from per-lane sums of squared
+// errors, all in FP32 with upward rounding: every square, every sum and the
+// square root round up, so the result is >= the exact norm. The warp sum is
+// a butterfly of upward additions (commutative, so every lane ends equal).
+__device__ __forceinline__ float err_norm_bound(float s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = __fadd_ru(s, __shfl_xor_sync(kFull, s, o));
+    return __fsqrt_ru(s);
 }
 
 // BF16 copy, one warp per row: round to nearest even, zero padding up to
 // `err_off`, then at byte `err_off` a bound E >= ||x - x~|| of the row's own
-// rounding error. Each difference of an FP32 value and its BF16 rounding is
-// exact in FP64, and so is its square.
+// rounding error (err_norm_bound).
 __global__ void quantize_bf16_kernel(const float* __restrict__ X, int64_t N, int D, int xpitch,
                                      int qpitch, int err_off, uint8_t* Q) {
     const int lane = threadIdx.x & 31;
     const int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= N) return;
     __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Q + i * qpitch);
-    double s = 0.0;
+    float s = 0.f;
     for (int f = lane; f < err_off / 2; f += 32) {
         const float x = f < D ? X[i * xpitch + f] : 0.f;
         const __nv_bfloat16 b = __float2bfloat16_rn(x);
         row[f] = b;
-        const double e = static_cast<double>(x) - static_cast<double>(__bfloat162float(b));
-        s += e * e;
+        // exact in FP32: both are multiples of x's FP32 ulp and differ by at
+        // most half a BF16 ulp
+        const float e = __fsub_rn(x, __bfloat162float(b));
+        s = __fadd_ru(s, __fmul_ru(e, e));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    if (lane == 0) *reinterpret_cast<float*>(Q + i * qpitch + err_off) = sqrt_bound(s);
+    const float E = err_norm_bound(s);
+    if (lane == 0) *reinterpret_cast<float*>(Q + i * qpitch + err_off) = E;
 }
 
 // FP8-E4M3 copy with per-row scale s = max|x| / 448 (s = 1 for a zero row),
@@ -271,7 +321,7 @@ __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t N, int 
     const float s = m > 0.f ? m / 448.f : 1.f;
     uint8_t* row = Q + i * qpitch;
     const int err_off = scale_off - 4;
-    double es = 0.0;
+    float es = 0.f;
     for (int w = lane; w < err_off / 4; w += 32) {
         float x[4];
         uint32_t word = 0u;
@@ -287,14 +337,14 @@ __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t N, int 
         fp8x4_to_float(word, s, v);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const double e = static_cast<double>(x[k]) - static_cast<double>(v[k]);
-            es += e * e;
+            // |x - x~| rounded up (the difference need not be exact in FP32)
+            const float e = __fsub_ru(fmaxf(x[k], v[k]), fminf(x[k], v[k]));
+            es = __fadd_ru(es, __fmul_ru(e, e));
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) es += __shfl_xor_sync(kFull, es, o);
+    const float E = err_norm_bound(es);
     if (lane == 0) {
-        *reinterpret_cast<float*>(row + err_off) = sqrt_bound(es);
+        *reinterpret_cast<float*>(row + err_off) = E;
         *reinterpret_cast<float*>(row + scale_off) = s;
     }
 }
@@ -343,14 +393,27 @@ cudaError_t launch_hd_finalize(const FinalizeParams& f, int blocks, cudaStream_t
     return cudaGetLastError();
 }
 
+// FP64 words of scratch launch_init_y needs: R (FP32, D4 x DP), mu (D), the
+// moments (2 DP), the scale factors (FP32, DP) and up to 1024 blocks of
+// column partials.
+int64_t init_y_scratch_len(int D, int d, int DP) {
+    (void)d;
+    const int64_t D4 = (D + 3) / 4 * 4;
+    const int64_t cols = D > DP ? D : DP;
+    return (D4 * DP + 1) / 2 + D + 2 * DP + (DP + 1) / 2 + 1024 * cols;
+}
+
 cudaError_t launch_init_y(const float* X32, int64_t N, int D, int xpitch, int d, int DP, uint64_t seed,
                           uint32_t ctr, float* Y, double* scratch, int64_t scratch_len, cudaStream_t s) {
-    // scratch layout: R (D*d) | mu (D) | moments (2*DP) | partials
-    double* R = scratch;
-    double* mu = R + static_cast<int64_t>(D) * d;
+    // scratch layout: R (FP32, D4 x DP) | mu (D) | mean, var (DP each) |
+    // scale factors (FP32, DP) | partials
+    const int n4 = (D + 3) / 4, D4 = 4 * n4;
+    float* R = reinterpret_cast<float*>(scratch);
+    double* mu = scratch + (static_cast<int64_t>(D4) * DP + 1) / 2;
     double* mean = mu + D;
     double* var = mean + DP;
-    double* part = var + DP;
+    float* sc = reinterpret_cast<float*>(var + DP);
+    double* part = var + DP + (DP + 1) / 2;
     const int64_t avail = scratch_len - (part - scratch);
     const int cols = D > DP ? D : DP;
     int nb = static_cast<int>(avail / cols);
@@ -358,15 +421,24 @@ cudaError_t launch_init_y(const float* X32, int64_t N, int D, int xpitch, int d,
     if (nb < 1) return cudaErrorInvalidValue;
     const int64_t rpb = (N + nb - 1) / nb;
     nb = static_cast<int>((N + rpb - 1) / rpb);
-    gauss_matrix_kernel<<<grid_for(static_cast<int64_t>(D) * d, 128), 128, 0, s>>>(D, d, ctr, seed, R);
+    gauss_matrix_kernel<<<grid_for(static_cast<int64_t>(D4) * DP, 128), 128, 0, s>>>(D, D4, d, DP, ctr, seed, R);
     col_sums_kernel<<<nb, 256, 0, s>>>(X32, N, D, xpitch, rpb, nullptr, 0, part);
     reduce_parts_kernel<<<grid_for(D, 128), 128, 0, s>>>(part, nb, D, 1.0 / static_cast<double>(N), mu);
-    project_kernel<<<grid_for(N, 128), 128, 0, s>>>(X32, N, D, xpitch, mu, R, d, DP, Y);
+    const size_t psmem = static_cast<size_t>(D4) * sizeof(float);
+    switch (DP) {
+        case 2: project_kernel<2><<<grid_for(N, 128), 128, psmem, s>>>(X32, N, D, n4, xpitch, mu, R, Y); break;
+        case 4: project_kernel<4><<<grid_for(N, 128), 128, psmem, s>>>(X32, N, D, n4, xpitch, mu, R, Y); break;
+        case 8: project_kernel<8><<<grid_for(N, 128), 128, psmem, s>>>(X32, N, D, n4, xpitch, mu, R, Y); break;
+        case 16: project_kernel<16><<<grid_for(N, 128), 128, psmem, s>>>(X32, N, D, n4, xpitch, mu, R, Y); break;
+        case 32: project_kernel<32><<<grid_for(N, 128), 128, psmem, s>>>(X32, N, D, n4, xpitch, mu, R, Y); break;
+        default: return cudaErrorInvalidValue;
+    }
     col_sums_kernel<<<nb, 256, 0, s>>>(Y, N, DP, DP, rpb, nullptr, 0, part);
     reduce_parts_kernel<<<grid_for(DP, 128), 128, 0, s>>>(part, nb, DP, 1.0 / static_cast<double>(N), mean);
     col_sums_kernel<<<nb, 256, 0, s>>>(Y, N, DP, DP, rpb, mean, 1, part);
     reduce_parts_kernel<<<grid_for(DP, 128), 128, 0, s>>>(part, nb, DP, 1.0 / static_cast<double>(N), var);
-    scale_cols_kernel<<<grid_for(N * DP, 256), 256, 0, s>>>(Y, N, d, DP, mean, var, kInitYStd);
+    col_scale_kernel<<<1, 32, 0, s>>>(var, d, DP, kInitYStd, sc);
+    scale_cols_kernel<<<grid_for(N * DP, 256), 256, 0, s>>>(Y, N * DP, DP, sc);
     return cudaGetLastError();
 }
 

@@ -89,6 +89,7 @@ cudaError_t update_launch(const UpdateParams& u, int blocks, cudaStream_t s);
 // set-up
 cudaError_t launch_init_lists(int64_t N, int k, uint32_t stream, uint64_t seed, int32_t* out, cudaStream_t s);
 cudaError_t launch_hd_finalize(const FinalizeParams& f, int blocks, cudaStream_t s);
+int64_t init_y_scratch_len(int D, int d, int DP);
 cudaError_t launch_init_y(const float* X32, int64_t N, int D, int xpitch, int d, int DP, uint64_t seed,
                           uint32_t ctr, float* Y, double* scratch, int64_t scratch_len, cudaStream_t s);
 cudaError_t launch_zinit(const ZinitParams& z, int DP, int blocks, DevScalars* sc, cudaStream_t s);
