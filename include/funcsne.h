@@ -359,6 +359,14 @@ int funcsne_profile_step(funcsne_t *h, int32_t n_iters, double *ms_per_kernel);
  * Errors: FUNCSNE_E_ARG. */
 int funcsne_debug_bounded_wait(funcsne_t *h, uint32_t polls);
 
+/* Copy into E_out (host or device, min(cap_rows, N) floats) each row's
+ * stored bound E_i >= ||x_i - x~_i|| on the error of its BF16 or FP8 copy
+ * x~_i, the bound the distance band of the reduced-precision HD refinement
+ * uses (E^2 summed from upward-rounded FP32 squares of the element errors,
+ * then an upward-rounded square root). For testing.
+ * Errors: FUNCSNE_E_ARG (NULL), FUNCSNE_E_STATE (FP32 rows: no copy). */
+int funcsne_debug_row_bounds(const funcsne_t *h, float *E_out, int64_t cap_rows);
+
 /* Allocation-failure injection, for testing failure detection on the host:
  * after `after` more successful device allocations of the library (any
  * handle), the next one fails as if the device were out of memory, once;

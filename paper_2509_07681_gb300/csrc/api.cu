@@ -1434,6 +1434,22 @@ int funcsne_get_data(const funcsne_t* hc, float* X_out, int64_t cap_rows) {
     return FUNCSNE_OK;
 }
 
+int funcsne_debug_row_bounds(const funcsne_t* hc, float* E_out, int64_t cap_rows) {
+    funcsne* h = const_cast<funcsne*>(hc);
+    if (!h || !E_out) return fail(h, FUNCSNE_E_ARG, "NULL argument");
+    if (h->precision == FUNCSNE_FP32 || !h->Xq)
+        return fail(h, FUNCSNE_E_STATE, "debug_row_bounds: no reduced-precision rows in FP32 mode");
+    const int64_t rows = cap_rows < h->N ? cap_rows : h->N;
+    // the bound sits at byte qscale_off of a BF16 row, four bytes before the
+    // scale of an FP8 row
+    const int off = h->precision == FUNCSNE_BF16 ? h->qscale_off : h->qscale_off - 4;
+    const float* src = reinterpret_cast<const float*>(h->Xq + off);
+    int rc = copy_rows<float>(h, E_out, 1, src, static_cast<size_t>(h->qpitch / 4), rows, 1);
+    if (rc) return rc;
+    FSNE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return FUNCSNE_OK;
+}
+
 int funcsne_scale_embedding(funcsne_t* h, float factor) {
     if (!h) return fail(h, FUNCSNE_E_ARG, "NULL handle");
     if (!(factor > 0.f) || !std::isfinite(factor)) return fail(h, FUNCSNE_E_ARG, "factor must be > 0 and finite");

@@ -71,6 +71,7 @@ ABI_FUNCTIONS = {
     "funcsne_get_embedding_async": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_debug_bounded_wait": (C.c_int, [_h, C.c_uint32]),
     "funcsne_debug_fail_alloc": (C.c_int, [C.c_int64]),
+    "funcsne_debug_row_bounds": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_wait_embedding": (C.c_int, [_h]),
     "funcsne_get_data": (C.c_int, [_h, _vp, C.c_int64]),
     "funcsne_scale_embedding": (C.c_int, [_h, C.c_float]),
@@ -309,6 +310,13 @@ def funcsne_mlp_debug_step(h, arrays):
     return dict(loss=st.loss, scale=st.scale, step=st.step, n_params=st.n_params)
 
 
+def funcsne_debug_row_bounds(h, out):
+    """Each row's stored bound E_i >= ||x_i - x~_i|| of its BF16 / FP8 copy."""
+    po, keep = _ptr(out)
+    _check(load().funcsne_debug_row_bounds(h, po, int(out.shape[0])), h)
+    return out
+
+
 def funcsne_debug_fail_alloc(after):
     """After `after` more successful device allocations, fail the next one
     once (FUNCSNE_E_OOM); after < 0 switches this off. For tests."""
@@ -412,6 +420,10 @@ class FuncSNE:
         rep = np.empty((self.N, self.d), np.float32)
         funcsne_debug_step(self.h, att, rep)
         return att, rep
+
+    def row_bounds(self):
+        """Each row's stored bound E_i >= ||x_i - x~_i|| of its reduced-precision copy."""
+        return funcsne_debug_row_bounds(self.h, np.empty(self.N, np.float32))
 
     def exact_knn(self, queries, k):
         q = np.ascontiguousarray(queries, dtype=np.int32)

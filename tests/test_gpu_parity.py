@@ -403,3 +403,41 @@ def test_insertion_window_matches_oracle(hd_mode):
                                hd_mode=hd_mode, fresh_iters=5)
         st = st1
     m.close()
+
+
+def _host_copy(X, fmt):
+    """The reduced-precision copy of each row as the library makes it:
+    BF16 round to nearest even; FP8-E4M3 codes of x / s (FP32 division,
+    round to nearest even, saturating at 448) times s = max|x| / 448 in FP32
+    (s = 1 for a zero row)."""
+    torch = pytest.importorskip("torch")
+    X32 = X.astype(np.float32)
+    if fmt == "bf16":
+        return O.bf16(X32.astype(np.float64))
+    m = np.abs(X32).max(1, keepdims=True)
+    s = np.where(m > 0, m / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+    q = torch.from_numpy((X32 / s).astype(np.float32)).clamp(-448, 448).to(torch.float8_e4m3fn)
+    return (q.to(torch.float32).numpy() * s).astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+def test_row_error_bounds_cover_the_quantisation_error(fmt):
+    """The bound E_i >= ||x_i - x~_i|| stored with each reduced-precision row
+    (it widens the distance band, so the exact re-rank sees every candidate
+    that can enter): never below the exact error norm of the row's copy,
+    and within 1e-4 of it. Rows of spread scales, offsets, tiny entries and
+    a zero row."""
+    rng = np.random.default_rng(81)
+    N, D = 1200, 50
+    X = rng.standard_normal((N, D)) * np.exp(rng.uniform(-12, 12, (N, 1))) + rng.uniform(-5, 5, (N, 1))
+    X[:, ::9] *= 1e-3
+    X[7] = 0.0
+    X = X.astype(np.float32)
+    p = CASES["blobs-2k"][1]
+    with F.FuncSNE(X, p["d"], p["k_hd"], p["k_ld"], p["n_neg"], p["alpha"], p["perplexity"], seed=0,
+                   precision=F.BF16 if fmt == "bf16" else F.FP8) as m:
+        E = m.row_bounds().astype(np.float64)
+    exact = np.sqrt(((X.astype(np.float64) - _host_copy(X, fmt)) ** 2).sum(1))
+    assert np.all(E >= exact)
+    assert np.all(E <= exact * (1 + 1e-4) + 1e-38)
+    assert E[7] == 0.0
