@@ -308,7 +308,7 @@ int configure_step(funcsne* h) {
     h->hd_pf_used = h->hd_prefetch && hd_lanes(h) <= 2 && hd_occ(true, smem2) >= 4 ? 1 : 0;
     h->hd_smem = h->hd_pf_used ? smem2 : smem1;
     h->ld_smem = static_cast<size_t>(8) * kHashSlots * 4;
-    h->fo_smem = static_cast<size_t>(8) * (kHashSlots + (use_forces_pair(h) ? kRepRing : 0)) * 4;
+    h->fo_smem = static_cast<size_t>(8) * (kForceHashSlots + (use_forces_pair(h) ? kRepRing : 0)) * 4;
     const int occ = hd_occ(h->hd_pf_used != 0, h->hd_smem);
     // the two refinements share the SMs when they run side by side
     const int ld_occ = ld_refine_occupancy(h->DP, h->RH, use_ld_pair(h), h->ld_smem);

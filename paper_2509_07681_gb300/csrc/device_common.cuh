@@ -662,30 +662,40 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // empty slot always exists and every probe sequence ends.
 constexpr uint32_t kHashEmpty = 0xffffffffu;
 
-__device__ __forceinline__ uint32_t hash_slot(uint32_t x) { return (x * 2654435761u) >> 24; }
-
-__device__ __forceinline__ void hset_clear(uint32_t* tab, int lane) {
-    const uint4 e = make_uint4(kHashEmpty, kHashEmpty, kHashEmpty, kHashEmpty);
-    reinterpret_cast<uint4*>(tab)[lane] = e;
-    reinterpret_cast<uint4*>(tab)[lane + 32] = e;
+// Open addressing with linear probing over S slots (a power of two, at least
+// 128): the top log2(S) bits of a Fibonacci hash pick the first slot.
+template <int S = kHashSlots>
+__device__ __forceinline__ uint32_t hash_slot(uint32_t x) {
+    static_assert(S >= 128 && (S & (S - 1)) == 0, "hash set size");
+    constexpr int kShift = 32 - __builtin_ctz(S);
+    return (x * 2654435761u) >> kShift;
 }
 
+template <int S = kHashSlots>
+__device__ __forceinline__ void hset_clear(uint32_t* tab, int lane) {
+    const uint4 e = make_uint4(kHashEmpty, kHashEmpty, kHashEmpty, kHashEmpty);
+#pragma unroll
+    for (int q = 0; q < S / 128; ++q) reinterpret_cast<uint4*>(tab)[lane + 32 * q] = e;
+}
+
+template <int S = kHashSlots>
 __device__ __forceinline__ void hset_insert(uint32_t* tab, uint32_t x) {
-    uint32_t h = hash_slot(x);
-    for (int probe = 0; probe < kHashSlots; ++probe) {
+    uint32_t h = hash_slot<S>(x);
+    for (int probe = 0; probe < S; ++probe) {
         const uint32_t prev = atomicCAS(tab + h, kHashEmpty, x);
         if (prev == kHashEmpty || prev == x) return;
-        h = (h + 1u) & (kHashSlots - 1);
+        h = (h + 1u) & (S - 1);
     }
 }
 
+template <int S = kHashSlots>
 __device__ __forceinline__ bool hset_has(const uint32_t* tab, uint32_t x) {
-    uint32_t h = hash_slot(x);
-    for (int probe = 0; probe < kHashSlots; ++probe) {
+    uint32_t h = hash_slot<S>(x);
+    for (int probe = 0; probe < S; ++probe) {
         const uint32_t v = tab[h];
         if (v == x) return true;
         if (v == kHashEmpty) return false;
-        h = (h + 1u) & (kHashSlots - 1);
+        h = (h + 1u) & (S - 1);
     }
     return false;
 }

@@ -578,7 +578,7 @@ forces_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    uint32_t* tab = reinterpret_cast<uint32_t*>(smem) + wib * kHashSlots;
+    uint32_t* tab = reinterpret_cast<uint32_t*>(smem) + wib * kForceHashSlots;
     __shared__ double s_z[kWarpsPerBlock];
 
     const DevScalars* sc = p.sc;
@@ -617,15 +617,15 @@ forces_kernel(const StepParams p) {
         load_chunk<CW>(Y + gi * DP + co, yi);
         const uint4 wq = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.pk);
         // S_i = HD u LD lists of t+1 as a warp hash set
-        hset_clear(tab, lane);
+        hset_clear<kForceHashSlots>(tab, lane);
         __syncwarp();
 #pragma unroll
         for (int r = 0; r < RH; ++r)
-            if (r * 32 + lane < k_hd) hset_insert(tab, nh[r]);
+            if (r * 32 + lane < k_hd) hset_insert<kForceHashSlots>(tab, nh[r]);
         __syncwarp();
-        const bool ld_in_hd = lane < k_ld && hset_has(tab, nl);
+        const bool ld_in_hd = lane < k_ld && hset_has<kForceHashSlots>(tab, nl);
         __syncwarp();
-        if (lane < k_ld) hset_insert(tab, nl);
+        if (lane < k_ld) hset_insert<kForceHashSlots>(tab, nl);
         __syncwarp();
 
         // this lane's components as pairs (packed arithmetic)
@@ -699,7 +699,7 @@ forces_kernel(const StepParams p) {
         // own Philox words), and the passes fetch them by one shuffle a row
         for (int s0 = 0; s0 < p.n_neg; s0 += 32) {
             const uint32_t jn = map_other(negative_word(wq.y, wq.w, static_cast<uint32_t>(s0 >> 5)), N, i);
-            const uint32_t jneg = (s0 + lane < p.n_neg && !hset_has(tab, jn)) ? jn : kNoRow;
+            const uint32_t jneg = (s0 + lane < p.n_neg && !hset_has<kForceHashSlots>(tab, jn)) ? jn : kNoRow;
             const int cnt = min(32, p.n_neg - s0);
             for (int b = 0; b < cnt; b += R) {
                 const int e = b + gq;
@@ -779,8 +779,8 @@ forces_pair_kernel(const StepParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    uint32_t* tab = reinterpret_cast<uint32_t*>(smem) + wib * (kHashSlots + kRepRing);
-    uint32_t* ring = tab + kHashSlots;
+    uint32_t* tab = reinterpret_cast<uint32_t*>(smem) + wib * (kForceHashSlots + kRepRing);
+    uint32_t* ring = tab + kForceHashSlots;
     __shared__ double s_z[kWarpsPerBlock];
 
     const DevScalars* sc = p.sc;
@@ -820,15 +820,15 @@ forces_pair_kernel(const StepParams p) {
         const float4 yi = __ldg(reinterpret_cast<const float4*>(Y + gi * DP + co));
         const uint4 wq = philox(t, i, kStreamRefine, static_cast<uint32_t>(lane), p.pk);
         // S_i = HD u LD lists of t+1 as a warp hash set
-        hset_clear(tab, lane);
+        hset_clear<kForceHashSlots>(tab, lane);
         __syncwarp();
 #pragma unroll
         for (int r = 0; r < RH; ++r)
-            if (r * 32 + lane < k_hd) hset_insert(tab, nh[r]);
+            if (r * 32 + lane < k_hd) hset_insert<kForceHashSlots>(tab, nh[r]);
         __syncwarp();
-        const bool ld_in_hd = lane < k_ld && hset_has(tab, nl);
+        const bool ld_in_hd = lane < k_ld && hset_has<kForceHashSlots>(tab, nl);
         __syncwarp();
-        if (lane < k_ld) hset_insert(tab, nl);
+        if (lane < k_ld) hset_insert<kForceHashSlots>(tab, nl);
 
         // this lane's four components as two pairs (packed arithmetic)
         float2 att[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
@@ -933,7 +933,7 @@ forces_pair_kernel(const StepParams p) {
             consume(false);
             const int sidx = s0 + lane;
             const uint32_t j = map_other(negative_word(wq.y, wq.w, static_cast<uint32_t>(s0 >> 5)), N, i);
-            const bool on = sidx < p.n_neg && !hset_has(tab, j);
+            const bool on = sidx < p.n_neg && !hset_has<kForceHashSlots>(tab, j);
             const unsigned mk = __ballot_sync(kFull, on);
             if (on) ring[(tail + __popc(mk & lt_mask)) & (kRepRing - 1)] = j;
             tail += __popc(mk);
